@@ -1,0 +1,172 @@
+"""Pins of the oracle's multigrid (Sec. 4): grid transfer, Galerkin projection of
+Toeplitz factors, the TGM iteration matrix against the recursive V-cycle, the
+two-grid contraction theorem, the smoothing-parameter bound of Lemma lemsmo,
+and the flexible GMRES solve against a dense direct solve."""
+import numpy as np
+import pytest
+
+from oracle import multigrid as mg
+from oracle.wsgd import wsgd_weights
+from oracle.operator import toeplitz_A, assemble_M, apply_M
+from oracle.krylov import fgmres
+
+rng = np.random.default_rng(11)
+
+
+def test_prolongation_is_bilinear():
+    # Remark after Lemma lemapp: P = T(p) U is (up to scale) linear interpolation
+    for n in [7, 15, 31]:
+        P = mg.prolongation_1d(n)
+        nc = (n - 1) // 2
+        xc = (2 * np.arange(nc) + 2) / (n + 1)        # coarse node j <-> fine node 2j+1 (0-based)
+        xf = np.arange(1, n + 1) / (n + 1)
+        np.testing.assert_allclose((P @ xc)[:-1], xf[:-1], atol=1e-15)
+        np.testing.assert_array_equal(P.sum(axis=0), 2.0)   # stencil 1/2, 1, 1/2
+    P = mg.prolongation_1d(8)                              # even n: K^k_n picks fine 1, 3, 5, 7
+    np.testing.assert_array_equal(np.argmax(P, axis=0), [0, 2, 4, 6])
+
+
+@pytest.mark.parametrize("n", [7, 15, 31, 63])
+def test_galerkin_of_toeplitz_is_q_coarsened_toeplitz(n):
+    # P^T T(t) P = T(t^c), t^c_k = sum_m q_m t_{2k+m}, q = (1/4, 1, 3/2, 1, 1/4), for odd n
+    P = mg.prolongation_1d(n)
+    nc = (n - 1) // 2
+    g = 1.37
+    w = wsgd_weights(g, n)
+    A = toeplitz_A(w, n)
+    t = lambda d: A[d, 0] if d >= 0 else A[0, -d]      # Toeplitz generator t_d = A[i, i-d]
+    q = {-2: 0.25, -1: 1.0, 0: 1.5, 1: 1.0, 2: 0.25}
+    tc = lambda d: sum(qm * (t(2 * d + m) if abs(2 * d + m) < n else 0.0) for m, qm in q.items())
+    Ac = P.T @ A @ P
+    ref = np.array([[tc(i - j) for j in range(nc)] for i in range(nc)])
+    np.testing.assert_allclose(Ac, ref, atol=1e-14)
+    B = P.T @ P
+    np.testing.assert_allclose(B, 1.5 * np.eye(nc) + 0.25 * (np.eye(nc, k=1) + np.eye(nc, k=-1)),
+                               atol=1e-15)
+
+
+def test_structured_galerkin_equals_exact_galerkin_for_constant_coefficients():
+    n = 31
+    wx, wy = wsgd_weights(1.6, n), wsgd_weights(1.75, n)
+    ones = np.ones((n, n))
+    cf = (1.2 * ones, 0.8 * ones, 0.5 * ones, 1.9 * ones)
+    h = mg.structured_galerkin(wx, wy, n, n, 0.3, 1.1, cf)
+    K0 = assemble_M(toeplitz_A(wx, n), toeplitz_A(wy, n), 0.3, 1.1, *cf)
+    he = mg.exact_galerkin(K0, n, n)
+    assert len(h.levels) == len(he.levels) == 3
+    for l in range(3):
+        np.testing.assert_allclose(h.levels[l].dense(), he.levels[l].dense(), atol=1e-11)
+        np.testing.assert_allclose(h.levels[l].diag(), he.levels[l].diag(), atol=1e-11)
+
+
+def test_structured_galerkin_injects_variable_coefficients():
+    n = 15
+    wx, wy = wsgd_weights(1.6, n), wsgd_weights(1.75, n)
+    cf = tuple(rng.uniform(0.5, 2, (n, n)) for _ in range(4))
+    h = mg.structured_galerkin(wx, wy, n, n, 0.3, 1.1, cf)
+    np.testing.assert_array_equal(h.levels[1].dp, cf[0][1::2, 1::2])
+    P = np.kron(mg.prolongation_1d(n), mg.prolongation_1d(n))
+    exact = P.T @ h.levels[0].dense() @ P
+    sg = h.levels[1].dense()
+    # not exact for variable coefficients, but close (smooth coefficients would be closer)
+    assert np.linalg.norm(sg - exact) / np.linalg.norm(exact) < 0.5
+
+
+def test_vcycle_two_level_equals_tgm_matrix():
+    # Sec. 4: with exact coarse solve the cycle is TGM(S, P) with one pre- and one
+    # post-smoothing step: x = (I - TGM) K^{-1} b
+    n = 15
+    wx, wy = wsgd_weights(1.7, n), wsgd_weights(1.5, n)
+    cf = tuple(rng.uniform(0.5, 2, (n, n)) for _ in range(4))
+    K0 = assemble_M(toeplitz_A(wx, n), toeplitz_A(wy, n), 0.2, 0.9, *cf)
+    h = mg.exact_galerkin(K0, n, n)
+    assert len(h.levels) == 2
+    P = np.kron(mg.prolongation_1d(n), mg.prolongation_1d(n))
+    T = mg.tgm_matrix(K0, P, 0.7, nu_pre=1, nu_post=1)
+    b = rng.standard_normal((n, n))
+    x = mg.vcycle(h, b, omega=0.7)
+    np.testing.assert_allclose(x.ravel(), (np.eye(n * n) - T) @ np.linalg.solve(K0, b.ravel()),
+                               rtol=1e-10, atol=1e-12)
+
+
+def test_tgm_contraction_below_one_and_flat():
+    # Theorem (theorem21bis): ||TGM||_A <= c < 1 independently of N, alpha, beta,
+    # for equal constant coefficients, 0 < omega < 2 a_0/||F||_inf, bilinear P
+    norms = []
+    for n in [7, 15, 31]:
+        for al, be in [(1.3, 1.7), (1.8, 1.6)]:
+            wx, wy = wsgd_weights(al, n), wsgd_weights(be, n)
+            ones = np.ones((n, n))
+            K = assemble_M(toeplitz_A(wx, n), toeplitz_A(wy, n), 0.0, 1.0, ones, ones, ones, ones)
+            P = np.kron(mg.prolongation_1d(n), mg.prolongation_1d(n))
+            T = mg.tgm_matrix(K, P, 0.7, nu_pre=0, nu_post=1)
+            ev, Q = np.linalg.eigh(K)
+            Kh = Q @ np.diag(np.sqrt(ev)) @ Q.T
+            Khi = Q @ np.diag(1 / np.sqrt(ev)) @ Q.T
+            norms.append(np.linalg.norm(Kh @ T @ Khi, 2))
+    assert max(norms) < 0.95
+    assert max(norms) - min(norms) < 0.15
+
+
+@pytest.mark.parametrize("g", [1.05, 1.3, 1.562, 1.8, 1.99])
+def test_omega_admissible(g):
+    # Lemma lemsmo: 0 < omega < 2 a_0/||F||_inf with a_0 = -2(d w1^a + (s/r) e w1^b) the
+    # zero-order Fourier coefficient of F = d q_a + (s/r) e q_b and
+    # ||q_g||_inf = (g - 1) 2^(g+1) (Prop. PaPb); both terms give the ratio (g+2)/2^g
+    w1 = wsgd_weights(g, 2)[1]
+    ratio = 2 * (-2 * w1) / ((g - 1) * 2 ** (g + 1))
+    np.testing.assert_allclose(ratio, (g + 2) / 2 ** g, rtol=1e-13)
+    assert 0.7 < ratio and 1.0 <= ratio  # damped (0.7) and classical (1.0) Jacobi admissible
+
+
+@pytest.mark.parametrize("kind", ["sg", "redisc", "p2"])
+def test_fgmres_mg_matches_direct_solve(kind):
+    from oracle.timeloop import make_preconditioner
+    n = 31
+    al, be = 1.5, 1.7
+    wx, wy = wsgd_weights(al, n, 1, -1), wsgd_weights(be, n, 1, -1)
+    X, Y = np.meshgrid(np.arange(1, n + 1) / (n + 1), np.arange(1, n + 1) / (n + 1))
+    cf = (1 + X ** al * Y, 1 + (1 - X) ** al * Y, 1 + Y ** be * X, 1 + (1 - Y) ** be * X)
+    sc = {"c": 0.35, "sigma": 1.8}
+    prec, _ = make_preconditioner(kind, al, be, wx, wy, n, n, sc, cf)
+    A = lambda Z: apply_M(Z, wx, wy, 0.35, 1.8, *cf)
+    b = rng.standard_normal((n, n))
+    x, its, rel, ok = fgmres(A, b, prec, 30, 1e-10)
+    K = assemble_M(toeplitz_A(wx, n), toeplitz_A(wy, n), 0.35, 1.8, *cf)
+    xd = np.linalg.solve(K, b.ravel())
+    assert ok and rel <= 1e-10
+    assert np.linalg.norm(b.ravel() - K @ x.ravel()) <= 1.0001e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(x.ravel() - xd) <= np.linalg.cond(K) * 1e-10 * np.linalg.norm(xd)
+    assert its < 30
+
+
+def test_fgmres_identity_and_exact_preconditioner():
+    n = 12
+    wx, wy = wsgd_weights(1.5, n), wsgd_weights(1.6, n)
+    cf = tuple(rng.uniform(0.5, 2, (n, n)) for _ in range(4))
+    K = assemble_M(toeplitz_A(wx, n), toeplitz_A(wy, n), 0.1, 1.0, *cf)
+    A = lambda Z: (K @ Z.ravel()).reshape(n, n)
+    b = rng.standard_normal((n, n))
+    x, its, rel, ok = fgmres(A, b, lambda R: np.linalg.solve(K, R.ravel()).reshape(n, n), 5, 1e-12)
+    assert ok and its == 1
+    x, its, rel, ok = fgmres(A, b, None, n * n, 1e-12)  # full GMRES: at most N steps
+    assert ok and its <= n * n
+
+
+def test_rediscretised_level_is_scheme_on_coarse_grid():
+    # Sec. 4.2: the coarse matrix re-discretises the equation on the grid of width
+    # 2h; in the scaling of Eq. (M) (times 1/r of the fine grid) level 1 must equal
+    # (r_1/r_0) M(2h) with M(2h) = (1/r_1) I + A_x + (s_1/r_1) A_y built by Eq. (M)
+    from oracle.operator import cn_scalars
+    n, al, be, dt = 15, 1.45, 1.75, 0.01
+    h = 1.0 / (n + 1)
+    wx, wy = wsgd_weights(al, n), wsgd_weights(be, n)
+    cf = tuple(rng.uniform(0.5, 2, (n, n)) for _ in range(4))
+    s0 = cn_scalars(al, be, h, h, dt)
+    hier = mg.rediscretised(al, be, wx, wy, n, n, s0["c"], s0["sigma"], cf)
+    nc = 7
+    s1 = cn_scalars(al, be, 2 * h, 2 * h, dt)
+    cfc = tuple(f[1::2, 1::2] for f in cf)
+    M1 = assemble_M(toeplitz_A(wx, nc), toeplitz_A(wy, nc), s1["c"], s1["sigma"], *cfc)
+    np.testing.assert_allclose(hier.levels[1].dense(), (s1["r"] / s0["r"]) * M1, rtol=1e-13, atol=1e-14)
+    assert hier.rscale == 0.25
