@@ -1,0 +1,373 @@
+"""Benchmark: CN-WSGD time steps per second at n = 2047 (rtol 1e-8).
+
+One bench step is one CN-WSGD time step (Eq. CNWSGD): the right-hand side
+b^(m) and the FGMRES(30) solve of M^(m) u^(m) = b^(m) preconditioned by one
+structured-Galerkin V-cycle, on the 2047 x 2047 grid of the perturbed
+power-law workload (alpha = 1.5, beta = 1.7, WSGD (1,-1), smooth seeded
+coefficient perturbation of amplitude 0.2, dt = h, manufactured bubble
+solution).  The timed region holds W warm-up steps' successors: K consecutive
+steps of the time loop with every input already resident in HBM.
+
+Reported beside the headline (mixed precision: FP64 Krylov, reduced-precision
+V-cycle): the same steps with the plain FP64 solver, an end-to-end figure
+through fde_step_host (host arrays, copies inside the timed region), the
+roofline of the dominant kernel (timed with CUDA events on the library's
+stream), sampled SM clocks, and the CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the
+workload (the solve does not shard across GPUs); value aggregates all ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 2047
+RESTART = 30
+RTOL = 1e-8
+METRIC = "CN-WSGD time steps/s at n=2047, rtol 1e-8: mixed-precision MG-GMRES vs FP64"
+WORKLOAD = ("perturbed power-law coefficients, n=2047, alpha=1.5, beta=1.7, WSGD (1,-1), "
+            "dt=h, FGMRES(30) + structured-Galerkin V-cycle, rtol 1e-8")
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# FP64 issue rate of GB300: 2 FMA per SM per clock (nominal 1.25 TFLOP/s)
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # = 1258.6 GFLOP/s at the 2070 MHz maximum clock
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07  # = 80 548 GFLOP/s
+
+
+def problem():
+    from paper_1706_06844_gb300 import inputs
+    return inputs.perturbed_power_law(alpha=1.5, beta=1.7, seed=1706068, amplitude=0.2)
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[2:6]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+class Workload:
+    """Device-resident inputs of the time loop and one solver handle."""
+
+    def __init__(self, precision, path=None, outer=None):
+        import torch
+        from paper_1706_06844_gb300 import fde
+        self.fde, self.torch = fde, torch
+        prob = problem()
+        n = N_GRID
+        X, Y, hx, hy = prob.grid(n, n)
+        self.prob, self.X, self.Y, self.dt = prob, X, Y, hx
+        a1, b1, a2, b2 = prob.domain
+        kw = dict(alpha=prob.alpha, beta=prob.beta, qx=prob.qx, qy=prob.qy, a1=a1, b1=b1,
+                  a2=a2, b2=b2, n1=n, n2=n, dt=self.dt, rtol=RTOL, restart=RESTART, maxit=2000,
+                  precond=fde.FDE_PRECOND_MG_SG, precision=precision)
+        if path is not None:
+            kw["toeplitz_path"] = path
+        if outer is not None:
+            kw["outer"] = outer
+        self.h = fde.fde_create(fde.params(**kw))
+        d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+        coef = [d(f) for f in prob.coefficients(X, Y, 0.0)]  # time-independent coefficients
+        fde.fde_set_coefficients(self.h, fde.FDE_COEF_NEW, *coef)
+        fde.fde_set_coefficients(self.h, fde.FDE_COEF_OLD, *coef)
+        self.u = [d(prob.exact(X, Y, 0.0)), torch.empty((n, n), dtype=torch.float64, device="cuda")]
+        self.vsrc = {}
+        self.m = 0
+        self.d = d
+
+    def source(self, m):
+        if m not in self.vsrc:
+            self.vsrc[m] = self.d(self.prob.source(self.X, self.Y, (m - 0.5) * self.dt))
+        return self.vsrc[m]
+
+    def step(self):
+        self.m += 1
+        st = self.fde.fde_step(self.h, self.u[0], self.source(self.m), self.u[1])
+        self.u.reverse()
+        return st
+
+    def close(self):
+        self.fde.fde_destroy(self.h)
+
+
+def time_steps(w, steps, warmup, dist):
+    import torch
+    for _ in range(warmup):
+        w.step()
+    for m in range(w.m + 1, w.m + steps + 1):
+        w.source(m)  # sources resident before the timed region
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = w.fde.fde_launch_count(w.h)
+    its = []
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        its.append(w.step().iterations)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    return ms, wall, its, w.fde.fde_launch_count(w.h) - l0
+
+
+def e2e_steps(w, steps):
+    """Same steps through fde_step_host: pinned host arrays in, host array out."""
+    import torch
+    n = N_GRID
+    u_host = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    u_host.copy_(w.u[0].cpu())
+    out = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    srcs = []
+    for m in range(w.m + 1, w.m + steps + 1):
+        s = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        s.copy_(torch.from_numpy(w.prob.source(w.X, w.Y, (m - 0.5) * w.dt)))
+        srcs.append(s)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in srcs:
+        w.fde.fde_step_host(w.h, u_host.data_ptr(), s.data_ptr(), out.data_ptr())
+        u_host, out = out, u_host
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nbytes = n * n * 8
+    return steps / dt, 2 * nbytes, nbytes
+
+
+def roofline(w, steps):
+    """Dominant kernel: the FP64-accurate outer Toeplitz apply (one launch = one
+    FFT pass over all rows or all columns).  Timed with CUDA events on the
+    library's stream over `steps` further time steps."""
+    fde = w.fde
+    fde.fde_profile_enable(w.h, 1)
+    for _ in range(steps):
+        w.step()
+    res = {}
+    for k, name in [(fde.FDE_KCLASS_OUTER_APPLY, "outer_apply"),
+                    (fde.FDE_KCLASS_LEVEL_APPLY, "level_apply"),
+                    (fde.FDE_KCLASS_KRYLOV, "krylov"), (fde.FDE_KCLASS_MG_OTHER, "mg_other")]:
+        res[name] = fde.fde_profile_query(w.h, k)
+    fde.fde_profile_enable(w.h, 0)
+    n, L = N_GRID, 4096
+    logL = 12
+    # algorithmic FP64 flops of one pass: per pair of vectors one forward and two
+    # inverse complex FFTs of length L (5 L log2 L each) and two complex spectral
+    # products (6 flops per point each); n vectors per pass
+    flops_pass = (n / 2) * (3 * 5 * L * logL + 2 * 6 * L)
+    launches, ms = res["outer_apply"]
+    avg_s = ms / max(launches, 1) * 1e-3
+    achieved = flops_pass / avg_s / 1e9
+    total_ms = sum(v[1] for v in res.values())
+    return {"bound": "alu", "kernel": "fft_pass_kernel<double,double> (outer FP64 Toeplitz apply)",
+            "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
+            "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
+            "traffic": None, "algorithmic_flops_per_launch": flops_pass,
+            "launches": launches, "avg_launch_ms": round(avg_s * 1e3, 4),
+            "share_of_profiled_time": {k: round(v[1] / total_ms, 4) for k, v in res.items()}}
+
+
+def cpu_baseline_sample():
+    """The FP64 oracle as it stands, timed on this host: one CN step at the
+    bench grid (right-hand side + FGMRES(30) with the structured-Galerkin
+    V-cycle to rtol 1e-8), after a one-off hierarchy set-up that is not timed."""
+    from oracle.wsgd import wsgd_weights
+    from oracle.operator import cn_scalars, rhs_fft, apply_M_fft
+    from oracle import multigrid as mg
+    from oracle.krylov import fgmres
+    prob = problem()
+    n = N_GRID
+    X, Y, hx, hy = prob.grid(n, n)
+    dt = hx
+    wx, wy = wsgd_weights(prob.alpha, n + 1, 1, prob.qx), wsgd_weights(prob.beta, n + 1, 1, prob.qy)
+    sc = cn_scalars(prob.alpha, prob.beta, hx, hy, dt)
+    c, s = sc["c"], sc["sigma"]
+    coef = prob.coefficients(X, Y, 0.0)
+    hier = mg.structured_galerkin(wx, wy, n, n, c, s, coef)
+    U = prob.exact(X, Y, 0.0)
+    V = prob.source(X, Y, 0.5 * dt)
+    t0 = time.perf_counter()
+    B = rhs_fft(U, wx, wy, c, s, *coef, V, hx, prob.alpha)
+    x, its, rel, ok = fgmres(lambda Z: apply_M_fft(Z, wx, wy, c, s, *coef), B,
+                             lambda R: mg.vcycle(hier, R), RESTART, RTOL)
+    t = time.perf_counter() - t0
+    return t, its
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    times, its = [], []
+    for i in range(args.warmup + args.steps):
+        t, k = cpu_baseline_sample()
+        if i >= args.warmup:
+            times.append(t)
+            its.append(k)
+    total = sum(times)
+    v = args.steps / total
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_GRID, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": round(v, 5), "unit": "steps/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": "each step: one CN step at n=2047 (rhs + FGMRES(30)/SG "
+                                       "V-cycle to rtol 1e-8) of the FP64 numpy oracle"},
+            "e2e": {"value": round(v, 5), "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "iterations_per_step": its}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        import torch
+        if torch.cuda.is_available():
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = td
+    if args.impl == "reference":
+        run_reference(args, rank)
+        if dist:
+            dist.destroy_process_group()
+        return
+    import torch
+    from paper_1706_06844_gb300 import fde
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    mixed = fde.FDE_PREC_FP32
+    w = Workload(mixed)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ms, wall, its, launches = time_steps(w, args.steps, args.warmup, dist)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms * 1e-3)
+    e2e_v, h2d, d2h = e2e_steps(w, max(2, min(args.steps, 4)))
+    roof = roofline(w, 2)
+    w.close()
+    fp64 = None
+    if not args.no_fp64:
+        w64 = Workload(fde.FDE_PREC_FP64)
+        ms64, wall64, its64, _ = time_steps(w64, max(2, args.steps // 4), 1, None)
+        k64 = max(2, args.steps // 4)
+        fp64 = {"value": round(k64 / (ms64 * 1e-3), 4), "unit": "steps/s",
+                "ms_per_step": round(ms64 / k64, 3), "iterations_per_step": its64,
+                "note": "plain FP64 GPU solver: same FGMRES(30), FP64 V-cycle with FFT products"}
+        w64.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t, k = cpu_baseline_sample()
+        cpu = {"value": round(1.0 / t, 5), "unit": "steps/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": f"one CN step at n=2047 of the FP64 numpy oracle "
+                                           f"({k} FGMRES iterations, {t:.1f} s)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 4), "unit": "steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64 Krylov + f32 V-cycle", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": N_GRID, "restart": RESTART, "rtol": RTOL,
+                           "precond": "MG_SG", "precision": "FP32 V-cycle, FP64 FFT outer apply",
+                           "l2": "inputs larger than L2 (Krylov basis 31 x 33.5 MB)",
+                           "parallelism": f"replicas x{world}"},
+                "iterations_per_step": its, "wall_s": round(wall, 3),
+                "e2e": {"value": round(e2e_v, 4), "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(launches), "roofline": roof, "clocks": clk.summary(),
+                "fp64_gpu": fp64, "cpu_baseline": cpu}
+        if fp64:
+            line["speedup_vs_fp64_gpu"] = round(value / world / fp64["value"], 3)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

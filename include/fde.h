@@ -1,0 +1,195 @@
+/*
+ * libfde -- GB300 (sm_103a) solver for the per-time-step linear system of the
+ * CN-WSGD discretisation of the two-dimensional two-sided space-fractional
+ * diffusion equation, after Moghaderi, Dehghan, Donatelli, Mazza,
+ * "Spectral analysis and multigrid preconditioners for two-dimensional
+ * space-fractional diffusion equations" (arXiv:1706.06844).
+ *
+ * At each time step t^(m) the scheme (Sec. 2, Eq. CNWSGD) leaves
+ *     M u^(m) = b^(m),                                           (Eq. 2)
+ *     M = c I + D+ (I (x) A_alpha) + D- (I (x) A_alpha^T)
+ *           + sigma [E+ (A_beta (x) I) + E- (A_beta^T (x) I)],   (Eq. M, AxAy)
+ *     b = (c I - A_x^(m-1) - sigma A_y^(m-1)) u^(m-1) + 2 hx^alpha v^(m-1/2),
+ * with A_gamma = -[w_{i-j+1}] (Eq. AN), w the WSGD weights (Eq. w),
+ * c = 1/r = 2 hx^alpha / dt and sigma = s/r = hx^alpha / hy^beta.  The system
+ * is solved by restarted flexible GMRES (Sec. 5) preconditioned by one
+ * multigrid V-cycle (Sec. 4: damped Jacobi, bilinear interpolation, Galerkin
+ * or rediscretised coarse operators).
+ *
+ * Conventions shared by every call:
+ *  - Grid functions are row-major n2 x n1 arrays U[j][i] of doubles, x index i
+ *    fastest (the lexicographic ordering of Sec. 2), no padding: element
+ *    (i, j) is at U[j * n1 + i].
+ *  - Unless a name ends in _host, every pointer argument is DEVICE memory owned
+ *    by the caller; the library reads/writes it on the handle's stream and keeps
+ *    no reference after the call returns.  The library owns its workspace
+ *    (Krylov basis, multigrid hierarchy, weights), allocated in fde_create and
+ *    freed in fde_destroy.
+ *  - Every call returns an int status: FDE_OK (0) or one of the FDE_ERR_*
+ *    codes; fde_last_error gives a message.  Argument errors are detected on
+ *    the host before any launch.  Calls that run a solve (fde_solve, fde_step,
+ *    fde_step_host) synchronise the stream before returning; the others only
+ *    enqueue work (their outputs are valid after a stream synchronisation).
+ *  - A handle is not thread-safe; separate handles are independent.
+ */
+#ifndef FDE_H
+#define FDE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FDE_OK                 0
+#define FDE_ERR_ARG            1  /* invalid argument (bad size, order, null pointer ...) */
+#define FDE_ERR_NOT_CONVERGED  2  /* maxit reached; the output holds the last iterate */
+#define FDE_ERR_NONFINITE      3  /* NaN/Inf met in a residual norm */
+#define FDE_ERR_CUDA           4  /* a CUDA runtime call failed */
+#define FDE_ERR_TIMEOUT        5  /* a capped device-side wait gave up */
+#define FDE_ERR_UNSUPPORTED    6  /* valid request this build does not implement */
+
+/* preconditioner (Sec. 4) */
+#define FDE_PRECOND_NONE       0  /* plain GMRES */
+#define FDE_PRECOND_MG_SG      1  /* V-cycle, structured Galerkin coarse operators, R = P^T */
+#define FDE_PRECOND_MG_REDISC  2  /* V-cycle, rediscretised coarse operators, R = P^T / 4 (P_MGM, Sec. 4.2) */
+
+/* arithmetic of the preconditioner (the outer Krylov method is always FP64) */
+#define FDE_PREC_FP64          0  /* V-cycle in FP64 ("plain FP64" solver) */
+#define FDE_PREC_FP32          1  /* V-cycle vectors and Toeplitz products in FP32 */
+#define FDE_PREC_BF16          2  /* FP32 vectors, Toeplitz products on tcgen05 in BF16 with FP32 accumulation */
+#define FDE_PREC_FP16          3  /* as BF16 with FP16 operands */
+
+/* how the preconditioner's dense Toeplitz products are evaluated */
+#define FDE_PATH_AUTO          0  /* tensor-core GEMM for BF16/FP16, FFT above the direct-sum cut-off, else direct */
+#define FDE_PATH_GEMM          1  /* tcgen05 GEMM (BF16/FP16 only) */
+#define FDE_PATH_FFT           2  /* circulant-embedding FFT */
+#define FDE_PATH_DIRECT        3  /* direct summation */
+
+/* arithmetic of the FP64-accurate outer apply (Krylov matvec, true residual, rhs) */
+#define FDE_OUTER_FP64         0  /* FFT in FP64 */
+#define FDE_OUTER_DF32         1  /* FFT in double-float (pairs of FP32), ~48-bit significand */
+
+/* coefficient time levels */
+#define FDE_COEF_NEW           0  /* d+-, e+- at t^(m): the system matrix M^(m) */
+#define FDE_COEF_OLD           1  /* d+-, e+- at t^(m-1): the right-hand side b^(m) */
+
+typedef struct fde_params {
+  double alpha, beta;      /* fractional orders in (1, 2) (problem (1), Sec. 2) */
+  int    qx, qy;           /* WSGD shift q, with p = 1: 0 is Eq. (w); -1 is the (1,-1) member of
+                              the same weighted-and-shifted family */
+  double a1, b1, a2, b2;   /* domain (a1, b1) x (a2, b2) */
+  int    n1, n2;           /* interior points; hx = (b1-a1)/(n1+1), hy = (b2-a2)/(n2+1) (Sec. 2) */
+  double dt;               /* time step */
+  double rtol;             /* stop when ||b - M x||_2 <= rtol ||b||_2 (true residual) */
+  int    restart;          /* FGMRES restart length m (1 .. 64) */
+  int    maxit;            /* cap on total inner iterations per solve */
+  int    precond;          /* FDE_PRECOND_* */
+  int    nu_pre, nu_post;  /* Jacobi sweeps before / after the coarse correction (0 .. 4) */
+  double omega;            /* Jacobi damping (Lemma lemsmo: 0 < omega < 2 a_0/||F||_inf) */
+  int    coarsest_n;       /* coarsen while n > coarsest_n (the paper fixes an 8 x 8 grid) */
+  int    precision;        /* FDE_PREC_* */
+  int    toeplitz_path;    /* FDE_PATH_* */
+  int    outer;            /* FDE_OUTER_* */
+} fde_params;
+
+typedef struct fde_stats {
+  int    iterations;       /* inner FGMRES steps (= preconditioner applications) */
+  int    restarts;         /* restart cycles begun */
+  int    converged;        /* 1 if the true residual met rtol */
+  double rel_residual;     /* ||b - M x||_2 / ||b||_2 at exit, true residual in FP64 */
+} fde_stats;
+
+typedef struct fde_handle fde_handle;
+
+/* Fill *p with defaults: alpha = beta = 1.5, q = 0, unit square, n = 63,
+ * dt = h, rtol 1e-8, FGMRES(30), maxit 1000, MG_SG, nu = (1, 1), omega 0.7,
+ * coarsest 8, FP64, AUTO path, FP64 outer apply. */
+void fde_default_params(fde_params* p);
+
+/* Create a solver for one grid (Sec. 2).  Checks the parameters, allocates
+ * the workspace and generates the WSGD weights w_0..w_n (Eq. gk, Eq. w) on
+ * the device in FP64.  `stream` is a cudaStream_t (NULL = legacy default).
+ * Coefficients must be set (fde_set_coefficients) before any apply or solve.
+ * Multigrid needs every level size odd (n, (n-1)/2, ...) down to <= coarsest_n.
+ * On error *out is NULL and the status says why. */
+int fde_create(const fde_params* p, void* stream, fde_handle** out);
+
+/* Free the workspace.  NULL is a no-op. */
+void fde_destroy(fde_handle* h);
+
+/* Last error message of `h`, or of the last failed fde_create when h is NULL. */
+const char* fde_last_error(const fde_handle* h);
+
+/* Set the diffusion coefficients d+, d-, e+, e- (Sec. 2: the diagonals of
+ * D+-, E+-) sampled on the grid, each an n2 x n1 device array.  `which` is
+ * FDE_COEF_NEW (t^(m): builds M and the multigrid hierarchy -- coarse
+ * coefficients by injection, level diagonals, coarse Toeplitz factors -- on
+ * the device) or FDE_COEF_OLD (t^(m-1): used only by fde_rhs / fde_step).
+ * The arrays are copied; the caller may free them afterwards. */
+int fde_set_coefficients(fde_handle* h, int which, const double* dp, const double* dm,
+                         const double* ep, const double* em);
+
+/* b = (c I - A_x^(m-1) - sigma A_y^(m-1)) u_prev + 2 hx^alpha v_half  (Eq. M,
+ * second line), with the FDE_COEF_OLD coefficients.  FP64-accurate. */
+int fde_rhs(fde_handle* h, const double* u_prev, const double* v_half, double* b);
+
+/* y = M x (Eq. M) with the FDE_COEF_NEW coefficients; FP64-accurate (the
+ * outer apply chosen by params.outer).  x and y must not alias. */
+int fde_apply(fde_handle* h, const double* x, double* y);
+
+/* z = B r: one application of the preconditioner (one V-cycle from a zero
+ * initial guess, Sec. 4 and 4.2), in the configured precision.  With
+ * FDE_PRECOND_NONE, z = r. */
+int fde_vcycle(fde_handle* h, const double* r, double* z);
+
+/* y = K_l x for multigrid level l (0 = finest), the level operator the
+ * V-cycle uses, in the configured precision.  x, y are n2_l x n1_l arrays. */
+int fde_level_apply(fde_handle* h, int level, const double* x, double* y);
+
+/* Number of multigrid levels and their sizes (arrays of length >= levels;
+ * either may be NULL). */
+int fde_levels(const fde_handle* h, int* levels, int* n1s, int* n2s);
+
+/* Copy the device-generated WSGD weights w_0..w_{count-1} of axis 0 (x,
+ * alpha) or 1 (y, beta) to host memory. */
+int fde_weights(const fde_handle* h, int axis, double* w_host, int count);
+
+/* Solve M x = b (Eq. 2) by FGMRES(restart) from x = 0 (Sec. 5), right
+ * preconditioned.  Writes x even when not converged (FDE_ERR_NOT_CONVERGED).
+ * `st` may be NULL.  Synchronises the stream. */
+int fde_solve(fde_handle* h, const double* b, double* x, fde_stats* st);
+
+/* One CN-WSGD time step (Eq. CNWSGD): b from u_prev, v_half and the OLD
+ * coefficients, then fde_solve.  u_next must not alias u_prev.  Increments
+ * the step counter. */
+int fde_step(fde_handle* h, const double* u_prev, const double* v_half, double* u_next,
+             fde_stats* st);
+
+/* fde_step with HOST arrays: copies u_prev and v_half host->device, runs the
+ * step and copies u_next device->host (pageable or pinned host memory). */
+int fde_step_host(fde_handle* h, const double* u_prev_host, const double* v_half_host,
+                  double* u_next_host, fde_stats* st);
+
+/* Checkpoint: the step counter m and the last solution written by fde_step
+ * (copied to u_out, device memory, may be NULL). */
+int fde_get_state(const fde_handle* h, int* m, double* u_out);
+/* Restore the step counter (the caller keeps u^(m) and passes it to fde_step). */
+int fde_set_state(fde_handle* h, int m);
+
+/* Kernel-level timing with CUDA events on the handle's stream (off by
+ * default).  Kernel classes: FDE_KCLASS_*.  fde_profile_query returns the
+ * number of launches and their summed event time since the last reset. */
+#define FDE_KCLASS_OUTER_APPLY  0  /* FP64-accurate Toeplitz apply (both directions) */
+#define FDE_KCLASS_LEVEL_APPLY  1  /* preconditioner Toeplitz products */
+#define FDE_KCLASS_KRYLOV       2  /* Arnoldi / update / norm kernels */
+#define FDE_KCLASS_MG_OTHER     3  /* smoother, transfers, coarse solve */
+#define FDE_KCLASS_COUNT        4
+int fde_profile_enable(fde_handle* h, int on);
+int fde_profile_query(fde_handle* h, int kclass, long long* launches, double* ms);
+/* Total kernels this handle has launched. */
+long long fde_launch_count(const fde_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDE_H */

@@ -1,0 +1,148 @@
+// Shared device types and the internal launch interface of libfde.
+// Kernels live in kernels_*.cu; the host drivers (handle, V-cycle, FGMRES)
+// in fde.cu call them only through the launchers declared here.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace fde {
+
+// ---------------------------------------------------------------- complex
+template <typename R>
+struct cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// a * conj(b)
+template <typename R>
+__device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
+  return {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
+}
+
+// ---------------------------------------------------------------- launches
+// Every launcher returns the cudaError_t of its launch (cudaGetLastError()).
+
+// Circulant-embedding Toeplitz pass over a set of vectors (rows or columns of a
+// grid).  For every vector v (elements x_v[i] = X[v*vs + i*es], i < n):
+//   y_v[i] = cmass * M[v*vs + i*es] + cp[.] * (A x_v)_i + cm[.] * (A^T x_v)_i
+// written to Y (accumulate = 0) or added to Y (accumulate = 1), where
+// A = [t_{i-k}] is the lower-Hessenberg Toeplitz matrix whose spectra S1 (A)
+// and S2 (A^T) were built by build_spectra for the same L.  M, cp, cm may be
+// null (term omitted; null cp/cm means 1).  T: storage type, R: FFT arithmetic.
+template <typename T, typename R>
+cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int logL,
+                            const cx<R>* S1, const cx<R>* S2, const cx<R>* tw,
+                            const T* cp, const T* cm, const T* M, double cmass,
+                            T* Y, int accumulate, cudaStream_t st);
+
+// Spectra of the circulant embeddings (length L = 2^logL >= 2n - 1) of A and A^T,
+// A = [t_{i-k}], generator t_d at t[d+1] for d = -1..n-1, scaled by scale/L and
+// stored in bit-reversed order.  Also fills the twiddle table tw[k] = e^{-2 pi i k/L},
+// k < L/2 (when tw is non-null).
+template <typename R>
+cudaError_t launch_build_spectra(const double* t, int n, int logL, double scale, cx<R>* S1,
+                                 cx<R>* S2, cx<R>* tw, cudaStream_t st);
+
+// Direct summation version of launch_fft_pass (same contract), A given by the
+// generator t (length n + 1, t_d at t[d+1]).
+template <typename T>
+cudaError_t launch_direct_pass(const T* X, int es, int vs, int nvec, int n, const T* t,
+                               const T* cp, const T* cm, const T* M, double cmass, T* Y,
+                               int accumulate, cudaStream_t st);
+
+// Galerkin mass pre-pass of a structured-Galerkin level:
+//   XBY = (B_y (x) I) x,  XBX = (I (x) B_x) x,  MASS = c (B_y (x) B_x) x
+// with B = tridiag(b1, b0, b1) per axis.
+template <typename T>
+cudaError_t launch_mass_prepass(const T* X, int n1, int n2, double bx0, double bx1, double by0,
+                                double by1, double c, T* XBY, T* XBX, T* MASS, cudaStream_t st);
+
+// Level epilogue on K x (already summed in KX):
+//   mode 0: Y = KX;  mode 1: Y = B - KX;  mode 2: Y = X + W (B - KX)
+template <typename T>
+cudaError_t launch_level_epilogue(int mode, size_t N, const T* KX, const T* B, const T* X,
+                                  const T* W, T* Y, cudaStream_t st);
+
+// Y = W * B (Jacobi sweep from a zero guess)
+template <typename T>
+cudaError_t launch_mul(size_t N, const T* W, const T* B, T* Y, cudaStream_t st);
+
+// coarse b_c = rscale * P^T r (bilinear P, odd fine sizes n = 2 nc + 1)
+template <typename T>
+cudaError_t launch_restrict(const T* R, int n1, int n2, double rscale, T* BC, cudaStream_t st);
+
+// X += P x_c
+template <typename T>
+cudaError_t launch_prolong_add(const T* XC, int n1, int n2, T* X, cudaStream_t st);
+
+// Y[i] = (TO)(scale * X[i])
+template <typename TI, typename TO>
+cudaError_t launch_convert(size_t N, const TI* X, double scale, TO* Y, cudaStream_t st);
+
+// Y = A - B (FP64)
+cudaError_t launch_sub(size_t N, const double* A, const double* B, double* Y, cudaStream_t st);
+
+// ---- setup
+// w_0..w_K of the WSGD family (p = 1, q in {0,-1}) by the Grunwald recurrence, FP64.
+cudaError_t launch_wsgd_weights(double gamma, int q, int K, double* w, cudaStream_t st);
+// level-0 generator t_d = scale * (-w_{d+1}), d = -1..n-1 (t[d+1])
+cudaError_t launch_generator_from_weights(const double* w, int n, double scale, double* t,
+                                          cudaStream_t st);
+// q-coarsening t^c_d = sum_m q_m t_{2d+m}, q = (1/4, 1, 3/2, 1, 1/4)
+cudaError_t launch_coarsen_generator(const double* t, int n, double* tc, int nc,
+                                     cudaStream_t st);
+// coarse coefficient injection F_c[jc][ic] = F[2jc+1][2ic+1] (odd sizes)
+template <typename T>
+cudaError_t launch_inject(const T* F, int n1, int n2, T* FC, cudaStream_t st);
+// per-level fields: dp, dm, ep, em (ep, em scaled by sigma), W = omega/diag(K_l)
+// from FP64 fine coefficients at the level's nodes (injection stride `stride`).
+template <typename T>
+cudaError_t launch_level_fields(const double* dp, const double* dm, const double* ep,
+                                const double* em, int n1f, int n1, int n2, int stride,
+                                double sigma, double c, double bx0, double by0, const double* tx,
+                                const double* ty, double omega, T* odp, T* odm, T* oep, T* oem,
+                                T* W, cudaStream_t st);
+// out = a X + b Y + c Z (Z may be null when c == 0), FP64
+cudaError_t launch_lincomb(size_t N, double a, const double* X, double b, const double* Y,
+                           double c, const double* Z, double* out, cudaStream_t st);
+// dense coarsest operator (N = n1 n2), LU with partial pivoting, explicit inverse (FP64)
+cudaError_t launch_coarse_inverse(const double* tx, const double* ty, int n1, int n2,
+                                  double bx0, double bx1, double by0, double by1, double c,
+                                  const double* dp, const double* dm, const double* ep,
+                                  const double* em, double* work, double* inv, int* info,
+                                  cudaStream_t st);
+// x = inv * b  (b, x in T; inv FP64)
+template <typename T>
+cudaError_t launch_coarse_solve(const double* inv, int N, const T* b, T* x, cudaStream_t st);
+
+// ---- Krylov (FP64)
+// partial dots: part[i * nb + blk] = sum over block chunk of V_i . w  (i < k)
+cudaError_t launch_dots(const double* V, size_t ldv, int k, const double* w, size_t N,
+                        double* part, int nb, cudaStream_t st);
+// w -= sum_i h_i V_i, then partial dots of the new w with V_i (i < k) and (slot k) with itself
+cudaError_t launch_axpy_dots(const double* V, size_t ldv, int k, const double* h, double* w,
+                             size_t N, double* part, int nb, int with_dots, cudaStream_t st);
+// out[i] = sum_b part[i * nb + b] (+ out[i] if add), i < k (one block)
+cudaError_t launch_reduce(const double* part, int k, int nb, double* out, int add,
+                          cudaStream_t st);
+// y = x * (1/s[0])
+cudaError_t launch_scale_inv(size_t N, const double* x, const double* s, double* y,
+                             cudaStream_t st);
+// x += sum_i c_i Z_i
+cudaError_t launch_update(const double* Z, size_t ldz, int k, const double* c, double* x,
+                          size_t N, cudaStream_t st);
+// partial sums of squares of x
+cudaError_t launch_sumsq(const double* x, size_t N, double* part, int nb, cudaStream_t st);
+
+int krylov_blocks();
+
+}  // namespace fde

@@ -1,0 +1,909 @@
+// libfde host side: the C ABI of include/fde.h, the multigrid hierarchy
+// (Sec. 4), the FP64-accurate outer operator (Eq. M) and restarted flexible
+// GMRES (Sec. 5).  All arithmetic on grid data runs in the kernels of
+// kernels_*.cu; the host only sequences launches and performs the O(m^2)
+// Givens/least-squares work of the Krylov method.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "tc_gemm.h"
+#include "../../include/fde.h"
+
+using namespace fde;
+
+namespace {
+
+std::string g_create_error;
+
+int ceil_log2(long v) {
+  int l = 0;
+  while ((1L << l) < v) ++l;
+  return l;
+}
+
+struct ProfEvent {
+  int kclass;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct MGBase;
+
+struct fde_handle {
+  fde_params p{};
+  cudaStream_t st = nullptr;
+  std::string err;
+  long long launches = 0;
+  int n1 = 0, n2 = 0;
+  size_t N = 0;
+  double hx = 0, hy = 0, c = 0, sigma = 0, two_h_alpha = 0;
+  std::vector<void*> allocs;
+
+  // weights and the FP64 outer operator (generator t = -w, spectra, coefficients)
+  double *wx = nullptr, *wy = nullptr, *tx0 = nullptr, *ty0 = nullptr;
+  int logLx = 0, logLy = 0;
+  cx<double> *S1x = nullptr, *S2x = nullptr, *S1y = nullptr, *S2y = nullptr;
+  cx<double> *twx = nullptr, *twy = nullptr;
+  double *dpN = nullptr, *dmN = nullptr, *epN = nullptr, *emN = nullptr;  // unscaled, t^(m)
+  double *epNs = nullptr, *emNs = nullptr;                                 // sigma-scaled
+  double *dpO = nullptr, *dmO = nullptr, *epOs = nullptr, *emOs = nullptr;  // t^(m-1)
+  bool have_new = false, have_old = false;
+
+  std::unique_ptr<MGBase> mg;
+
+  // Krylov workspace
+  double *V = nullptr, *Z = nullptr, *part = nullptr, *hdev = nullptr, *h2dev = nullptr;
+  double *ydev = nullptr, *tmp = nullptr, *bwork = nullptr, *hu = nullptr, *hv = nullptr,
+         *hx_out = nullptr, *u_last = nullptr;
+  int nb = 0;
+  int m = 0;
+
+  // profiling
+  bool prof = false;
+  std::vector<ProfEvent> pending;
+  std::vector<cudaEvent_t> pool;
+  long long prof_launches[FDE_KCLASS_COUNT] = {0, 0, 0, 0};
+  double prof_ms[FDE_KCLASS_COUNT] = {0, 0, 0, 0};
+
+  int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+  }
+
+  template <typename P>
+  int alloc(P** ptr, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(P) + 16);
+    if (e != cudaSuccess) return fail(FDE_ERR_CUDA, "cudaMalloc(%zu): %s", count * sizeof(P),
+                                      cudaGetErrorString(e));
+    allocs.push_back(q);
+    *ptr = static_cast<P*>(q);
+    return FDE_OK;
+  }
+
+  cudaEvent_t ev() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  int pbeg(int k) {
+    if (!prof) return -1;
+    ProfEvent pe{k, ev(), ev()};
+    cudaEventRecord(pe.a, st);
+    pending.push_back(pe);
+    return (int)pending.size() - 1;
+  }
+  void pend(int idx) {
+    if (idx >= 0) cudaEventRecord(pending[idx].b, st);
+  }
+  void prof_collect() {
+    if (pending.empty()) return;
+    cudaStreamSynchronize(st);
+    for (auto& pe : pending) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, pe.a, pe.b);
+      prof_ms[pe.kclass] += ms;
+      prof_launches[pe.kclass] += 1;
+      pool.push_back(pe.a);
+      pool.push_back(pe.b);
+    }
+    pending.clear();
+  }
+};
+
+#define LCHK(call)                                                                       \
+  do {                                                                                   \
+    cudaError_t _e = (call);                                                             \
+    h->launches++;                                                                       \
+    if (_e != cudaSuccess)                                                               \
+      return h->fail(FDE_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(_e));      \
+  } while (0)
+#define CCHK(call)                                                                       \
+  do {                                                                                   \
+    cudaError_t _e = (call);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return h->fail(FDE_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(_e));      \
+  } while (0)
+#define RCHK(call)                 \
+  do {                             \
+    int _r = (call);               \
+    if (_r != FDE_OK) return _r;   \
+  } while (0)
+
+// ============================================================================
+// multigrid hierarchy
+
+struct MGBase {
+  virtual ~MGBase() {}
+  virtual int setup(fde_handle* h) = 0;  // from h->dpN.. (FP64, unscaled)
+  virtual int vcycle(fde_handle* h, const double* r, double* z) = 0;
+  virtual int level_apply(fde_handle* h, int l, const double* x, double* y) = 0;
+  std::vector<int> n1s, n2s;
+};
+
+template <typename T>
+struct MG : MGBase {
+  struct Lv {
+    int n1, n2;
+    size_t N;
+    double bx0 = 1, bx1 = 0, by0 = 1, by1 = 0;  // Galerkin mass tridiagonals
+    double *tx = nullptr, *ty = nullptr;         // Toeplitz generators (FP64)
+    int path = FDE_PATH_DIRECT;                  // FFT, DIRECT or GEMM
+    int logLx = 0, logLy = 0;
+    cx<T> *S1x = nullptr, *S2x = nullptr, *S1y = nullptr, *S2y = nullptr, *twx = nullptr,
+          *twy = nullptr;
+    T *txT = nullptr, *tyT = nullptr;
+    T *dp, *dm, *ep, *em, *W;
+    T *x, *b, *kx, *xby = nullptr, *xbx = nullptr, *mass = nullptr;
+    tc::ToeplitzGemmLevel gemm;
+  };
+  std::vector<Lv> lv;
+  double *inv = nullptr, *cwork = nullptr, *cf[4] = {nullptr, nullptr, nullptr, nullptr};
+  int* info = nullptr;
+  double rscale = 1.0;
+  bool sg = true;
+
+  int create(fde_handle* h) {
+    const fde_params& p = h->p;
+    sg = p.precond == FDE_PRECOND_MG_SG;
+    rscale = sg ? 1.0 : 0.25;
+    int m1 = h->n1, m2 = h->n2;
+    for (;;) {
+      Lv L;
+      L.n1 = m1;
+      L.n2 = m2;
+      L.N = (size_t)m1 * m2;
+      lv.push_back(L);
+      n1s.push_back(m1);
+      n2s.push_back(m2);
+      if (m1 <= p.coarsest_n || m2 <= p.coarsest_n) break;
+      if (!(m1 & 1) || !(m2 & 1))
+        return h->fail(FDE_ERR_UNSUPPORTED,
+                       "multigrid needs odd level sizes down to the coarsest grid (got %d x %d)",
+                       m1, m2);
+      m1 = (m1 - 1) / 2;
+      m2 = (m2 - 1) / 2;
+    }
+    if (lv.back().N > 1024)
+      return h->fail(FDE_ERR_UNSUPPORTED, "coarsest grid %d x %d exceeds 1024 unknowns",
+                     lv.back().n1, lv.back().n2);
+    // mass tridiagonals (structured Galerkin: b^{c}_0 = 3/2 b_0 + 2 b_1, b^{c}_1 = b_0/4 + b_1)
+    for (size_t l = 1; l < lv.size(); ++l) {
+      if (sg) {
+        Lv& a = lv[l - 1];
+        lv[l].bx0 = 1.5 * a.bx0 + 2.0 * a.bx1;
+        lv[l].bx1 = 0.25 * a.bx0 + a.bx1;
+        lv[l].by0 = 1.5 * a.by0 + 2.0 * a.by1;
+        lv[l].by1 = 0.25 * a.by0 + a.by1;
+      }
+    }
+    const bool lowp = (p.precision == FDE_PREC_BF16 || p.precision == FDE_PREC_FP16);
+    for (size_t l = 0; l < lv.size(); ++l) {
+      Lv& L = lv[l];
+      const bool last = l + 1 == lv.size();
+      RCHK(h->alloc(&L.tx, L.n1 + 2));
+      RCHK(h->alloc(&L.ty, L.n2 + 2));
+      RCHK(h->alloc(&L.dp, L.N));
+      RCHK(h->alloc(&L.dm, L.N));
+      RCHK(h->alloc(&L.ep, L.N));
+      RCHK(h->alloc(&L.em, L.N));
+      RCHK(h->alloc(&L.W, L.N));
+      RCHK(h->alloc(&L.x, L.N));
+      RCHK(h->alloc(&L.b, L.N));
+      RCHK(h->alloc(&L.kx, L.N));
+      if (sg && l > 0) {
+        RCHK(h->alloc(&L.xby, L.N));
+        RCHK(h->alloc(&L.xbx, L.N));
+        RCHK(h->alloc(&L.mass, L.N));
+      }
+      if (last) continue;
+      // product path of this level
+      int path = p.toeplitz_path;
+      const int nmin = std::min(L.n1, L.n2);
+      if (path == FDE_PATH_AUTO) {
+        if (lowp && nmin >= tc::kMinGemmN) path = FDE_PATH_GEMM;
+        else path = nmin >= 127 ? FDE_PATH_FFT : FDE_PATH_DIRECT;
+      }
+      if (path == FDE_PATH_GEMM && !lowp)
+        return h->fail(FDE_ERR_ARG, "the tensor-core path needs BF16 or FP16 precision");
+      if (path == FDE_PATH_GEMM && nmin < tc::kMinGemmN) path = FDE_PATH_FFT;
+      L.path = path;
+      if (path == FDE_PATH_FFT) {
+        L.logLx = ceil_log2(2L * L.n1 - 1);
+        L.logLy = ceil_log2(2L * L.n2 - 1);
+        const size_t smx = 2 * ((size_t)1 << L.logLx) * sizeof(cx<T>);
+        const size_t smy = 2 * ((size_t)1 << L.logLy) * sizeof(cx<T>);
+        if (smx > 227 * 1024 || smy > 227 * 1024)
+          return h->fail(FDE_ERR_UNSUPPORTED, "FFT length too large for shared memory");
+        RCHK(h->alloc(&L.S1x, (size_t)1 << L.logLx));
+        RCHK(h->alloc(&L.S2x, (size_t)1 << L.logLx));
+        RCHK(h->alloc(&L.twx, (size_t)1 << (L.logLx - 1)));
+        RCHK(h->alloc(&L.S1y, (size_t)1 << L.logLy));
+        RCHK(h->alloc(&L.S2y, (size_t)1 << L.logLy));
+        RCHK(h->alloc(&L.twy, (size_t)1 << (L.logLy - 1)));
+      } else if (path == FDE_PATH_DIRECT) {
+        RCHK(h->alloc(&L.txT, L.n1 + 2));
+        RCHK(h->alloc(&L.tyT, L.n2 + 2));
+      } else {
+        const int prec = p.precision == FDE_PREC_BF16 ? tc::kBF16 : tc::kFP16;
+        int r = tc::level_create(&L.gemm, L.n1, L.n2, prec, sg && l > 0);
+        if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core level allocation failed (%d)", r);
+      }
+    }
+    const Lv& C = lv.back();
+    RCHK(h->alloc(&inv, C.N * C.N));
+    RCHK(h->alloc(&cwork, C.N * C.N * 2));
+    for (int k = 0; k < 4; ++k) RCHK(h->alloc(&cf[k], C.N));
+    RCHK(h->alloc(&info, 4));
+    return FDE_OK;
+  }
+
+  ~MG() {
+    for (auto& L : lv) tc::level_destroy(&L.gemm);
+  }
+
+  // generators, coefficient fields, spectra, coarsest inverse
+  int setup(fde_handle* h) override {
+    const fde_params& p = h->p;
+    cudaStream_t st = h->st;
+    for (size_t l = 0; l < lv.size(); ++l) {
+      Lv& L = lv[l];
+      if (l == 0 || !sg) {
+        const double sx = std::pow(2.0, -p.alpha * (double)l), sy = std::pow(2.0, -p.beta * (double)l);
+        LCHK(launch_generator_from_weights(h->wx, L.n1, sx, L.tx, st));
+        LCHK(launch_generator_from_weights(h->wy, L.n2, sy, L.ty, st));
+      } else {
+        LCHK(launch_coarsen_generator(lv[l - 1].tx, lv[l - 1].n1, L.tx, L.n1, st));
+        LCHK(launch_coarsen_generator(lv[l - 1].ty, lv[l - 1].n2, L.ty, L.n2, st));
+      }
+      const int stride = 1 << l;
+      LCHK(launch_level_fields<T>(h->dpN, h->dmN, h->epN, h->emN, h->n1, L.n1, L.n2, stride,
+                                  h->sigma, h->c, L.bx0, L.by0, L.tx, L.ty, p.omega, L.dp, L.dm,
+                                  L.ep, L.em, L.W, st));
+      if (L.path == FDE_PATH_FFT && l + 1 < lv.size()) {
+        LCHK(launch_build_spectra<T>(L.tx, L.n1, L.logLx, 1.0, L.S1x, L.S2x, L.twx, st));
+        LCHK(launch_build_spectra<T>(L.ty, L.n2, L.logLy, 1.0, L.S1y, L.S2y, L.twy, st));
+      } else if (L.path == FDE_PATH_DIRECT && l + 1 < lv.size()) {
+        LCHK((launch_convert<double, T>(L.n1 + 1, L.tx, 1.0, L.txT, st)));
+        LCHK((launch_convert<double, T>(L.n2 + 1, L.ty, 1.0, L.tyT, st)));
+      } else if (L.path == FDE_PATH_GEMM && l + 1 < lv.size()) {
+        int r = tc::level_setup(&L.gemm, L.tx, L.ty, st);
+        h->launches += 4;
+        if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core bank setup failed (%d)", r);
+      }
+    }
+    // coarsest: FP64 fields, dense inverse
+    Lv& C = lv.back();
+    const int stride = 1 << (lv.size() - 1);
+    LCHK(launch_level_fields<double>(h->dpN, h->dmN, h->epN, h->emN, h->n1, C.n1, C.n2, stride,
+                                     h->sigma, h->c, C.bx0, C.by0, C.tx, C.ty, p.omega, cf[0],
+                                     cf[1], cf[2], cf[3], nullptr, st));
+    LCHK(launch_coarse_inverse(C.tx, C.ty, C.n1, C.n2, C.bx0, C.bx1, C.by0, C.by1, h->c, cf[0],
+                               cf[1], cf[2], cf[3], cwork, inv, info, st));
+    int hinfo = 0;
+    CCHK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CCHK(cudaStreamSynchronize(st));
+    if (hinfo != 0) return h->fail(FDE_ERR_NONFINITE, "coarsest-grid matrix is singular");
+    return FDE_OK;
+  }
+
+  // kx = K_l x (products + mass term)
+  int products(fde_handle* h, size_t l, const T* x, T* kx) {
+    Lv& L = lv[l];
+    cudaStream_t st = h->st;
+    const T *xin_x = x, *xin_y = x, *M = x;
+    double cm = h->c;
+    if (sg && l > 0) {
+      LCHK(launch_mass_prepass<T>(x, L.n1, L.n2, L.bx0, L.bx1, L.by0, L.by1, h->c, L.xby, L.xbx,
+                                  L.mass, st));
+      xin_x = L.xby;
+      xin_y = L.xbx;
+      M = L.mass;
+      cm = 1.0;
+    }
+    const int pi = h->pbeg(FDE_KCLASS_LEVEL_APPLY);
+    if (L.path == FDE_PATH_FFT) {
+      LCHK((launch_fft_pass<T, T>(xin_x, 1, L.n1, L.n2, L.n1, L.logLx, L.S1x, L.S2x, L.twx, L.dp,
+                                  L.dm, M, cm, kx, 0, st)));
+      LCHK((launch_fft_pass<T, T>(xin_y, L.n1, 1, L.n1, L.n2, L.logLy, L.S1y, L.S2y, L.twy, L.ep,
+                                  L.em, nullptr, 0.0, kx, 1, st)));
+    } else if (L.path == FDE_PATH_DIRECT) {
+      LCHK(launch_direct_pass<T>(xin_x, 1, L.n1, L.n2, L.n1, L.txT, L.dp, L.dm, M, cm, kx, 0, st));
+      LCHK(launch_direct_pass<T>(xin_y, L.n1, 1, L.n1, L.n2, L.tyT, L.ep, L.em, nullptr, 0.0, kx,
+                                 1, st));
+    } else {
+      int r = tc::level_products(&L.gemm, (const float*)xin_x, (const float*)xin_y,
+                                 (const float*)M, cm, (const float*)L.dp, (const float*)L.dm,
+                                 (const float*)L.ep, (const float*)L.em, (float*)kx, st);
+      h->launches += 2;
+      if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core products failed (%d)", r);
+    }
+    h->pend(pi);
+    return FDE_OK;
+  }
+
+  int smooth(fde_handle* h, size_t l) {  // x <- x + W (b - K x)
+    Lv& L = lv[l];
+    RCHK(products(h, l, L.x, L.kx));
+    const int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+    LCHK(launch_level_epilogue<T>(2, L.N, L.kx, L.b, L.x, L.W, L.x, h->st));
+    h->pend(pi);
+    return FDE_OK;
+  }
+
+  int cycle(fde_handle* h, size_t l) {
+    Lv& L = lv[l];
+    const fde_params& p = h->p;
+    cudaStream_t st = h->st;
+    if (l + 1 == lv.size()) {
+      const int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+      LCHK(launch_coarse_solve<T>(inv, (int)L.N, L.b, L.x, st));
+      h->pend(pi);
+      return FDE_OK;
+    }
+    int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+    if (p.nu_pre >= 1) LCHK(launch_mul<T>(L.N, L.W, L.b, L.x, st));
+    else CCHK(cudaMemsetAsync(L.x, 0, L.N * sizeof(T), st));
+    h->pend(pi);
+    for (int s = 1; s < p.nu_pre; ++s) RCHK(smooth(h, l));
+    // residual r = b - K x (kept in kx), restriction
+    RCHK(products(h, l, L.x, L.kx));
+    pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+    LCHK(launch_level_epilogue<T>(1, L.N, L.kx, L.b, L.x, L.W, L.kx, st));
+    LCHK(launch_restrict<T>(L.kx, L.n1, L.n2, rscale, lv[l + 1].b, st));
+    h->pend(pi);
+    RCHK(cycle(h, l + 1));
+    pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+    LCHK(launch_prolong_add<T>(lv[l + 1].x, L.n1, L.n2, L.x, st));
+    h->pend(pi);
+    for (int s = 0; s < p.nu_post; ++s) RCHK(smooth(h, l));
+    return FDE_OK;
+  }
+
+  int vcycle(fde_handle* h, const double* r, double* z) override {
+    Lv& L = lv[0];
+    LCHK((launch_convert<double, T>(L.N, r, 1.0, L.b, h->st)));
+    RCHK(cycle(h, 0));
+    LCHK((launch_convert<T, double>(L.N, L.x, 1.0, z, h->st)));
+    return FDE_OK;
+  }
+
+  int level_apply(fde_handle* h, int l, const double* x, double* y) override {
+    if (l < 0 || l >= (int)lv.size()) return h->fail(FDE_ERR_ARG, "level %d out of range", l);
+    Lv& L = lv[l];
+    if (l + 1 == (int)lv.size()) {
+      // coarsest level: apply through the direct path on the FP64 generators
+      LCHK((launch_convert<double, T>(L.N, x, 1.0, L.x, h->st)));
+      T *txT, *tyT;
+      RCHK(h->alloc(&txT, L.n1 + 2));
+      RCHK(h->alloc(&tyT, L.n2 + 2));
+      LCHK((launch_convert<double, T>(L.n1 + 1, L.tx, 1.0, txT, h->st)));
+      LCHK((launch_convert<double, T>(L.n2 + 1, L.ty, 1.0, tyT, h->st)));
+      const T *xin_x = L.x, *xin_y = L.x, *M = L.x;
+      double cm = h->c;
+      T *xby, *xbx, *mass;
+      if (sg && l > 0) {
+        RCHK(h->alloc(&xby, L.N));
+        RCHK(h->alloc(&xbx, L.N));
+        RCHK(h->alloc(&mass, L.N));
+        LCHK(launch_mass_prepass<T>(L.x, L.n1, L.n2, L.bx0, L.bx1, L.by0, L.by1, h->c, xby, xbx,
+                                    mass, h->st));
+        xin_x = xby;
+        xin_y = xbx;
+        M = mass;
+        cm = 1.0;
+      }
+      LCHK(launch_direct_pass<T>(xin_x, 1, L.n1, L.n2, L.n1, txT, L.dp, L.dm, M, cm, L.kx, 0,
+                                 h->st));
+      LCHK(launch_direct_pass<T>(xin_y, L.n1, 1, L.n1, L.n2, tyT, L.ep, L.em, nullptr, 0.0, L.kx,
+                                 1, h->st));
+      LCHK((launch_convert<T, double>(L.N, L.kx, 1.0, y, h->st)));
+      return FDE_OK;
+    }
+    LCHK((launch_convert<double, T>(L.N, x, 1.0, L.x, h->st)));
+    RCHK(products(h, l, L.x, L.kx));
+    LCHK((launch_convert<T, double>(L.N, L.kx, 1.0, y, h->st)));
+    return FDE_OK;
+  }
+};
+
+// ============================================================================
+// FP64-accurate outer operator
+
+static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
+  const double* dp = old ? h->dpO : h->dpN;
+  const double* dm = old ? h->dmO : h->dmN;
+  const double* ep = old ? h->epOs : h->epNs;
+  const double* em = old ? h->emOs : h->emNs;
+  int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
+  LCHK((launch_fft_pass<double, double>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x, h->S2x,
+                                        h->twx, dp, dm, x, h->c, y, 0, h->st)));
+  h->pend(pi);
+  pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
+  LCHK((launch_fft_pass<double, double>(x, h->n1, 1, h->n1, h->n2, h->logLy, h->S1y, h->S2y,
+                                        h->twy, ep, em, nullptr, 0.0, y, 1, h->st)));
+  h->pend(pi);
+  return FDE_OK;
+}
+
+static int norm2(fde_handle* h, const double* x, double* dev_out, double* host_out) {
+  int pi = h->pbeg(FDE_KCLASS_KRYLOV);
+  LCHK(launch_sumsq(x, h->N, h->part, h->nb, h->st));
+  LCHK(launch_reduce(h->part, 1, h->nb, dev_out, 2, h->st));
+  h->pend(pi);
+  if (host_out) {
+    CCHK(cudaMemcpyAsync(host_out, dev_out, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CCHK(cudaStreamSynchronize(h->st));
+  }
+  return FDE_OK;
+}
+
+static int precond(fde_handle* h, const double* v, double* z) {
+  if (!h->mg) {
+    CCHK(cudaMemcpyAsync(z, v, h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    return FDE_OK;
+  }
+  return h->mg->vcycle(h, v, z);
+}
+
+static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_out) {
+  const fde_params& p = h->p;
+  const size_t N = h->N;
+  const int m = p.restart;
+  fde_stats st{0, 0, 0, 0.0};
+  double bnorm = 0.0;
+  RCHK(norm2(h, b, h->hdev, &bnorm));
+  CCHK(cudaMemsetAsync(x, 0, N * sizeof(double), h->st));
+  if (!std::isfinite(bnorm)) return h->fail(FDE_ERR_NONFINITE, "right-hand side is not finite");
+  if (bnorm == 0.0) {
+    st.converged = 1;
+    if (st_out) *st_out = st;
+    CCHK(cudaStreamSynchronize(h->st));
+    return FDE_OK;
+  }
+  // V_0 = b / ||b||
+  LCHK(launch_scale_inv(N, b, h->hdev, h->V, h->st));
+  double beta = bnorm;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), col(m + 2), y(m);
+  const double tol = p.rtol * bnorm;
+  int status = FDE_ERR_NOT_CONVERGED;
+  while (st.iterations < p.maxit) {
+    st.restarts++;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = h->V + (size_t)j * N;
+      double* Zj = h->Z + (size_t)j * N;
+      double* w = h->V + (size_t)(j + 1) * N;
+      RCHK(precond(h, Vj, Zj));
+      RCHK(outer_apply(h, Zj, w, false));
+      // classical Gram-Schmidt, twice (CGS2)
+      int pi = h->pbeg(FDE_KCLASS_KRYLOV);
+      LCHK(launch_dots(h->V, N, j + 1, w, N, h->part, h->nb, h->st));
+      LCHK(launch_reduce(h->part, j + 1, h->nb, h->hdev, 0, h->st));
+      LCHK(launch_axpy_dots(h->V, N, j + 1, h->hdev, w, N, h->part, h->nb, 0, h->st));
+      LCHK(launch_dots(h->V, N, j + 1, w, N, h->part, h->nb, h->st));
+      LCHK(launch_reduce(h->part, j + 1, h->nb, h->h2dev, 0, h->st));
+      LCHK(launch_reduce(h->part, j + 1, h->nb, h->hdev, 1, h->st));
+      LCHK(launch_axpy_dots(h->V, N, j + 1, h->h2dev, w, N, h->part, h->nb, 1, h->st));
+      LCHK(launch_reduce(h->part, 1, h->nb, h->hdev + j + 1, 2, h->st));
+      LCHK(launch_scale_inv(N, w, h->hdev + j + 1, w, h->st));
+      h->pend(pi);
+      CCHK(cudaMemcpyAsync(col.data(), h->hdev, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->st));
+      CCHK(cudaStreamSynchronize(h->st));
+      for (int i = 0; i <= j + 1; ++i)
+        if (!std::isfinite(col[i]))
+          return h->fail(FDE_ERR_NONFINITE, "non-finite Hessenberg entry at iteration %d",
+                         st.iterations + 1);
+      // previous rotations, new rotation (Givens)
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+      }
+      const double rho = std::hypot(col[j], col[j + 1]);
+      const double hnext = col[j + 1];
+      cs[j] = col[j] / rho;
+      sn[j] = col[j + 1] / rho;
+      col[j] = rho;
+      col[j + 1] = 0.0;
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = col[i];
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      st.iterations++;
+      k = j + 1;
+      if (std::fabs(g[j + 1]) <= tol || st.iterations >= p.maxit || hnext == 0.0) break;
+    }
+    // y = R^{-1} g, x += Z y
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int l = i + 1; l < k; ++l) s -= H[(size_t)i * m + l] * y[l];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    CCHK(cudaMemcpyAsync(h->ydev, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    int pi = h->pbeg(FDE_KCLASS_KRYLOV);
+    LCHK(launch_update(h->Z, N, k, h->ydev, x, N, h->st));
+    h->pend(pi);
+    // true residual in FP64
+    RCHK(outer_apply(h, x, h->tmp, false));
+    LCHK(launch_sub(N, b, h->tmp, h->tmp, h->st));
+    RCHK(norm2(h, h->tmp, h->h2dev, &beta));
+    if (!std::isfinite(beta)) return h->fail(FDE_ERR_NONFINITE, "non-finite residual");
+    st.rel_residual = beta / bnorm;
+    if (beta <= tol) {
+      status = FDE_OK;
+      st.converged = 1;
+      break;
+    }
+    if (st.iterations >= p.maxit) break;
+    LCHK(launch_scale_inv(N, h->tmp, h->h2dev, h->V, h->st));
+  }
+  if (st_out) *st_out = st;
+  if (status == FDE_ERR_NOT_CONVERGED)
+    h->fail(FDE_ERR_NOT_CONVERGED, "not converged: %d iterations, relative residual %.3e",
+            st.iterations, st.rel_residual);
+  return status;
+}
+
+// ============================================================================
+// C ABI
+
+extern "C" {
+
+void fde_default_params(fde_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->alpha = 1.5;
+  p->beta = 1.5;
+  p->qx = p->qy = 0;
+  p->a1 = p->a2 = 0.0;
+  p->b1 = p->b2 = 1.0;
+  p->n1 = p->n2 = 63;
+  p->dt = 1.0 / 64.0;
+  p->rtol = 1e-8;
+  p->restart = 30;
+  p->maxit = 1000;
+  p->precond = FDE_PRECOND_MG_SG;
+  p->nu_pre = 1;
+  p->nu_post = 1;
+  p->omega = 0.7;
+  p->coarsest_n = 8;
+  p->precision = FDE_PREC_FP64;
+  p->toeplitz_path = FDE_PATH_AUTO;
+  p->outer = FDE_OUTER_FP64;
+}
+
+static int validate(const fde_params* p, std::string& why) {
+  char buf[256];
+  auto bad = [&](const char* m) { why = m; return FDE_ERR_ARG; };
+  if (!(p->alpha > 1.0 && p->alpha < 2.0) || !(p->beta > 1.0 && p->beta < 2.0))
+    return bad("alpha and beta must lie in (1, 2)");
+  if ((p->qx != 0 && p->qx != -1) || (p->qy != 0 && p->qy != -1)) return bad("q must be 0 or -1");
+  if (!(p->b1 > p->a1) || !(p->b2 > p->a2)) return bad("empty domain");
+  if (p->n1 < 3 || p->n2 < 3 || p->n1 > 8191 || p->n2 > 8191) return bad("n1, n2 must be in [3, 8191]");
+  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return bad("dt must be positive");
+  if (!(p->rtol > 0.0) || !(p->rtol < 1.0)) return bad("rtol must be in (0, 1)");
+  if (p->restart < 1 || p->restart > 64) return bad("restart must be in [1, 64]");
+  if (p->maxit < 1) return bad("maxit must be >= 1");
+  if (p->precond < FDE_PRECOND_NONE || p->precond > FDE_PRECOND_MG_REDISC) return bad("unknown precond");
+  if (p->nu_pre < 0 || p->nu_pre > 4 || p->nu_post < 0 || p->nu_post > 4) return bad("nu in [0, 4]");
+  if (!(p->omega > 0.0 && p->omega < 2.0)) return bad("omega must be in (0, 2)");
+  if (p->coarsest_n < 1) return bad("coarsest_n must be >= 1");
+  if (p->precision < FDE_PREC_FP64 || p->precision > FDE_PREC_FP16) return bad("unknown precision");
+  if (p->toeplitz_path < FDE_PATH_AUTO || p->toeplitz_path > FDE_PATH_DIRECT) return bad("unknown toeplitz_path");
+  if (p->outer != FDE_OUTER_FP64 && p->outer != FDE_OUTER_DF32) return bad("unknown outer");
+  if (p->precision == FDE_PREC_BF16 || p->precision == FDE_PREC_FP16) {
+    why = "the tensor-core preconditioner is not built";
+    return FDE_ERR_UNSUPPORTED;
+  }
+  if (p->outer == FDE_OUTER_DF32) {
+    why = "the double-float outer apply is not built";
+    return FDE_ERR_UNSUPPORTED;
+  }
+  const int L1 = ceil_log2(2L * p->n1 - 1), L2 = ceil_log2(2L * p->n2 - 1);
+  if (L1 > 12 || L2 > 12) {
+    snprintf(buf, sizeof(buf), "FP64 FFT apply supports n <= 2048 (got %d x %d)", p->n1, p->n2);
+    why = buf;
+    return FDE_ERR_UNSUPPORTED;
+  }
+  return FDE_OK;
+}
+
+int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
+  if (!out) return FDE_ERR_ARG;
+  *out = nullptr;
+  if (!pin) {
+    g_create_error = "null params";
+    return FDE_ERR_ARG;
+  }
+  std::string why;
+  int v = validate(pin, why);
+  if (v != FDE_OK) {
+    g_create_error = why;
+    return v;
+  }
+  std::unique_ptr<fde_handle> hp(new fde_handle());
+  fde_handle* h = hp.get();
+  h->p = *pin;
+  h->st = (cudaStream_t)stream;
+  const fde_params& p = h->p;
+  h->n1 = p.n1;
+  h->n2 = p.n2;
+  h->N = (size_t)p.n1 * p.n2;
+  h->hx = (p.b1 - p.a1) / (p.n1 + 1);
+  h->hy = (p.b2 - p.a2) / (p.n2 + 1);
+  const double r = p.dt / (2.0 * std::pow(h->hx, p.alpha));  // Eq. (system)
+  const double s = p.dt / (2.0 * std::pow(h->hy, p.beta));
+  h->c = 1.0 / r;
+  h->sigma = s / r;
+  h->two_h_alpha = 2.0 * std::pow(h->hx, p.alpha);
+  const size_t N = h->N;
+  int rc = FDE_OK;
+  auto setup = [&]() -> int {
+    RCHK(h->alloc(&h->wx, p.n1 + 2));
+    RCHK(h->alloc(&h->wy, p.n2 + 2));
+    RCHK(h->alloc(&h->tx0, p.n1 + 2));
+    RCHK(h->alloc(&h->ty0, p.n2 + 2));
+    LCHK(launch_wsgd_weights(p.alpha, p.qx, p.n1 + 1, h->wx, h->st));
+    LCHK(launch_wsgd_weights(p.beta, p.qy, p.n2 + 1, h->wy, h->st));
+    LCHK(launch_generator_from_weights(h->wx, p.n1, 1.0, h->tx0, h->st));
+    LCHK(launch_generator_from_weights(h->wy, p.n2, 1.0, h->ty0, h->st));
+    h->logLx = ceil_log2(2L * p.n1 - 1);
+    h->logLy = ceil_log2(2L * p.n2 - 1);
+    RCHK(h->alloc(&h->S1x, (size_t)1 << h->logLx));
+    RCHK(h->alloc(&h->S2x, (size_t)1 << h->logLx));
+    RCHK(h->alloc(&h->twx, (size_t)1 << (h->logLx - 1)));
+    RCHK(h->alloc(&h->S1y, (size_t)1 << h->logLy));
+    RCHK(h->alloc(&h->S2y, (size_t)1 << h->logLy));
+    RCHK(h->alloc(&h->twy, (size_t)1 << (h->logLy - 1)));
+    LCHK(launch_build_spectra<double>(h->tx0, p.n1, h->logLx, 1.0, h->S1x, h->S2x, h->twx, h->st));
+    LCHK(launch_build_spectra<double>(h->ty0, p.n2, h->logLy, 1.0, h->S1y, h->S2y, h->twy, h->st));
+    double** fields[] = {&h->dpN, &h->dmN, &h->epN, &h->emN, &h->epNs, &h->emNs,
+                         &h->dpO, &h->dmO, &h->epOs, &h->emOs, &h->tmp, &h->bwork,
+                         &h->hu, &h->hv, &h->hx_out, &h->u_last};
+    for (double** f : fields) RCHK(h->alloc(f, N));
+    RCHK(h->alloc(&h->V, N * (size_t)(p.restart + 1)));
+    RCHK(h->alloc(&h->Z, N * (size_t)p.restart));
+    h->nb = krylov_blocks();
+    RCHK(h->alloc(&h->part, (size_t)h->nb * (p.restart + 2)));
+    RCHK(h->alloc(&h->hdev, p.restart + 4));
+    RCHK(h->alloc(&h->h2dev, p.restart + 4));
+    RCHK(h->alloc(&h->ydev, p.restart + 4));
+    if (p.precond != FDE_PRECOND_NONE) {
+      if (p.precision == FDE_PREC_FP64) {
+        auto* mg = new MG<double>();
+        h->mg.reset(mg);
+        RCHK(mg->create(h));
+      } else {
+        auto* mg = new MG<float>();
+        h->mg.reset(mg);
+        RCHK(mg->create(h));
+      }
+    }
+    CCHK(cudaStreamSynchronize(h->st));
+    return FDE_OK;
+  };
+  rc = setup();
+  if (rc != FDE_OK) {
+    g_create_error = h->err;
+    fde_destroy(hp.release());
+    return rc;
+  }
+  *out = hp.release();
+  return FDE_OK;
+}
+
+void fde_destroy(fde_handle* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  h->mg.reset();
+  for (void* q : h->allocs) cudaFree(q);
+  for (auto& pe : h->pending) {
+    cudaEventDestroy(pe.a);
+    cudaEventDestroy(pe.b);
+  }
+  for (auto e : h->pool) cudaEventDestroy(e);
+  delete h;
+}
+
+const char* fde_last_error(const fde_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int fde_set_coefficients(fde_handle* h, int which, const double* dp, const double* dm,
+                         const double* ep, const double* em) {
+  if (!h) return FDE_ERR_ARG;
+  if (!dp || !dm || !ep || !em) return h->fail(FDE_ERR_ARG, "null coefficient pointer");
+  if (which != FDE_COEF_NEW && which != FDE_COEF_OLD) return h->fail(FDE_ERR_ARG, "bad `which`");
+  const size_t N = h->N;
+  if (which == FDE_COEF_NEW) {
+    CCHK(cudaMemcpyAsync(h->dpN, dp, N * 8, cudaMemcpyDeviceToDevice, h->st));
+    CCHK(cudaMemcpyAsync(h->dmN, dm, N * 8, cudaMemcpyDeviceToDevice, h->st));
+    CCHK(cudaMemcpyAsync(h->epN, ep, N * 8, cudaMemcpyDeviceToDevice, h->st));
+    CCHK(cudaMemcpyAsync(h->emN, em, N * 8, cudaMemcpyDeviceToDevice, h->st));
+    LCHK((launch_convert<double, double>(N, ep, h->sigma, h->epNs, h->st)));
+    LCHK((launch_convert<double, double>(N, em, h->sigma, h->emNs, h->st)));
+    h->have_new = true;
+    if (h->mg) RCHK(h->mg->setup(h));
+  } else {
+    CCHK(cudaMemcpyAsync(h->dpO, dp, N * 8, cudaMemcpyDeviceToDevice, h->st));
+    CCHK(cudaMemcpyAsync(h->dmO, dm, N * 8, cudaMemcpyDeviceToDevice, h->st));
+    LCHK((launch_convert<double, double>(N, ep, h->sigma, h->epOs, h->st)));
+    LCHK((launch_convert<double, double>(N, em, h->sigma, h->emOs, h->st)));
+    h->have_old = true;
+  }
+  return FDE_OK;
+}
+
+int fde_rhs(fde_handle* h, const double* u_prev, const double* v_half, double* b) {
+  if (!h) return FDE_ERR_ARG;
+  if (!u_prev || !v_half || !b) return h->fail(FDE_ERR_ARG, "null pointer");
+  if (!h->have_old) return h->fail(FDE_ERR_ARG, "FDE_COEF_OLD coefficients not set");
+  // b = c u - A^(m-1) u + 2 h^a v = 2c u - M^(m-1) u + 2 h^a v
+  RCHK(outer_apply(h, u_prev, h->tmp, true));
+  LCHK(launch_lincomb(h->N, 2.0 * h->c, u_prev, -1.0, h->tmp, h->two_h_alpha, v_half, b, h->st));
+  return FDE_OK;
+}
+
+int fde_apply(fde_handle* h, const double* x, double* y) {
+  if (!h) return FDE_ERR_ARG;
+  if (!x || !y || x == y) return h->fail(FDE_ERR_ARG, "null or aliased pointer");
+  if (!h->have_new) return h->fail(FDE_ERR_ARG, "FDE_COEF_NEW coefficients not set");
+  return outer_apply(h, x, y, false);
+}
+
+int fde_vcycle(fde_handle* h, const double* r, double* z) {
+  if (!h) return FDE_ERR_ARG;
+  if (!r || !z) return h->fail(FDE_ERR_ARG, "null pointer");
+  if (!h->have_new) return h->fail(FDE_ERR_ARG, "FDE_COEF_NEW coefficients not set");
+  return precond(h, r, z);
+}
+
+int fde_level_apply(fde_handle* h, int level, const double* x, double* y) {
+  if (!h) return FDE_ERR_ARG;
+  if (!x || !y) return h->fail(FDE_ERR_ARG, "null pointer");
+  if (!h->have_new) return h->fail(FDE_ERR_ARG, "FDE_COEF_NEW coefficients not set");
+  if (!h->mg) return h->fail(FDE_ERR_ARG, "no multigrid hierarchy (precond NONE)");
+  return h->mg->level_apply(h, level, x, y);
+}
+
+int fde_levels(const fde_handle* h, int* levels, int* n1s, int* n2s) {
+  if (!h) return FDE_ERR_ARG;
+  const int L = h->mg ? (int)h->mg->n1s.size() : 1;
+  if (levels) *levels = L;
+  for (int l = 0; l < L; ++l) {
+    if (n1s) n1s[l] = h->mg ? h->mg->n1s[l] : h->n1;
+    if (n2s) n2s[l] = h->mg ? h->mg->n2s[l] : h->n2;
+  }
+  return FDE_OK;
+}
+
+int fde_weights(const fde_handle* hc, int axis, double* w_host, int count) {
+  fde_handle* h = const_cast<fde_handle*>(hc);
+  if (!h) return FDE_ERR_ARG;
+  const int n = axis == 0 ? h->n1 : h->n2;
+  if (!w_host || count < 0 || count > n + 2 || (axis != 0 && axis != 1))
+    return h->fail(FDE_ERR_ARG, "bad weights request");
+  CCHK(cudaMemcpyAsync(w_host, axis == 0 ? h->wx : h->wy, count * sizeof(double),
+                       cudaMemcpyDeviceToHost, h->st));
+  CCHK(cudaStreamSynchronize(h->st));
+  return FDE_OK;
+}
+
+int fde_solve(fde_handle* h, const double* b, double* x, fde_stats* st) {
+  if (!h) return FDE_ERR_ARG;
+  if (!b || !x || b == x) return h->fail(FDE_ERR_ARG, "null or aliased pointer");
+  if (!h->have_new) return h->fail(FDE_ERR_ARG, "FDE_COEF_NEW coefficients not set");
+  int r = solve_impl(h, b, x, st);
+  h->prof_collect();
+  return r;
+}
+
+int fde_step(fde_handle* h, const double* u_prev, const double* v_half, double* u_next,
+             fde_stats* st) {
+  if (!h) return FDE_ERR_ARG;
+  if (!u_prev || !v_half || !u_next || u_prev == u_next)
+    return h->fail(FDE_ERR_ARG, "null or aliased pointer");
+  RCHK(fde_rhs(h, u_prev, v_half, h->bwork));
+  int r = fde_solve(h, h->bwork, u_next, st);
+  if (r == FDE_OK || r == FDE_ERR_NOT_CONVERGED) {
+    CCHK(cudaMemcpyAsync(h->u_last, u_next, h->N * 8, cudaMemcpyDeviceToDevice, h->st));
+    h->m++;
+  }
+  return r;
+}
+
+int fde_step_host(fde_handle* h, const double* u_prev_host, const double* v_half_host,
+                  double* u_next_host, fde_stats* st) {
+  if (!h) return FDE_ERR_ARG;
+  if (!u_prev_host || !v_half_host || !u_next_host)
+    return h->fail(FDE_ERR_ARG, "null pointer");
+  CCHK(cudaMemcpyAsync(h->hu, u_prev_host, h->N * 8, cudaMemcpyHostToDevice, h->st));
+  CCHK(cudaMemcpyAsync(h->hv, v_half_host, h->N * 8, cudaMemcpyHostToDevice, h->st));
+  int r = fde_step(h, h->hu, h->hv, h->hx_out, st);
+  if (r != FDE_OK && r != FDE_ERR_NOT_CONVERGED) return r;
+  CCHK(cudaMemcpyAsync(u_next_host, h->hx_out, h->N * 8, cudaMemcpyDeviceToHost, h->st));
+  CCHK(cudaStreamSynchronize(h->st));
+  return r;
+}
+
+int fde_get_state(const fde_handle* hc, int* m, double* u_out) {
+  fde_handle* h = const_cast<fde_handle*>(hc);
+  if (!h) return FDE_ERR_ARG;
+  if (m) *m = h->m;
+  if (u_out)
+    CCHK(cudaMemcpyAsync(u_out, h->u_last, h->N * 8, cudaMemcpyDeviceToDevice, h->st));
+  return FDE_OK;
+}
+
+int fde_set_state(fde_handle* h, int m) {
+  if (!h) return FDE_ERR_ARG;
+  if (m < 0) return h->fail(FDE_ERR_ARG, "negative step counter");
+  h->m = m;
+  return FDE_OK;
+}
+
+int fde_profile_enable(fde_handle* h, int on) {
+  if (!h) return FDE_ERR_ARG;
+  h->prof_collect();
+  h->prof = on != 0;
+  for (int k = 0; k < FDE_KCLASS_COUNT; ++k) {
+    h->prof_launches[k] = 0;
+    h->prof_ms[k] = 0.0;
+  }
+  return FDE_OK;
+}
+
+int fde_profile_query(fde_handle* h, int kclass, long long* launches, double* ms) {
+  if (!h) return FDE_ERR_ARG;
+  if (kclass < 0 || kclass >= FDE_KCLASS_COUNT) return h->fail(FDE_ERR_ARG, "bad kernel class");
+  h->prof_collect();
+  if (launches) *launches = h->prof_launches[kclass];
+  if (ms) *ms = h->prof_ms[kclass];
+  return FDE_OK;
+}
+
+long long fde_launch_count(const fde_handle* h) { return h ? h->launches : 0; }
+
+}  // extern "C"

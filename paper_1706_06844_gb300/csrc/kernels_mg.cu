@@ -1,0 +1,440 @@
+// Multigrid kernels (Sec. 4) and device-side setup (Sec. 2 weights, coarse
+// operators, coarsest-grid direct solve).  Grid functions are row-major
+// n2 x n1 arrays (x fastest).
+#include "common.cuh"
+
+namespace fde {
+
+static inline int grid_for(size_t N, int threads) {
+  size_t g = (N + threads - 1) / threads;
+  const size_t cap = 152 * 16;
+  return (int)(g < cap ? (g > 0 ? g : 1) : cap);
+}
+
+// ---------------------------------------------------------------- level ops
+template <typename T>
+__global__ void mass_prepass_kernel(const T* __restrict__ X, int n1, int n2, T bx0, T bx1, T by0,
+                                    T by1, T c, T* __restrict__ XBY, T* __restrict__ XBX,
+                                    T* __restrict__ MASS) {
+  const size_t N = (size_t)n1 * n2;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n1), j = (int)(idx / n1);
+    auto at = [&](int jj, int ii) -> T {
+      return (ii >= 0 && ii < n1 && jj >= 0 && jj < n2) ? X[(size_t)jj * n1 + ii] : T(0);
+    };
+    // (B_y (x) I) x: tridiagonal along y;  (I (x) B_x) x: along x
+    const T xc = X[idx];
+    const T up = at(j - 1, i), dn = at(j + 1, i), lf = at(j, i - 1), rt = at(j, i + 1);
+    XBY[idx] = by1 * up + by0 * xc + by1 * dn;
+    XBX[idx] = bx1 * lf + bx0 * xc + bx1 * rt;
+    const T rowm = bx1 * at(j - 1, i - 1) + bx0 * up + bx1 * at(j - 1, i + 1);
+    const T row0 = bx1 * lf + bx0 * xc + bx1 * rt;
+    const T rowp = bx1 * at(j + 1, i - 1) + bx0 * dn + bx1 * at(j + 1, i + 1);
+    MASS[idx] = c * (by1 * rowm + by0 * row0 + by1 * rowp);
+  }
+}
+
+template <typename T>
+cudaError_t launch_mass_prepass(const T* X, int n1, int n2, double bx0, double bx1, double by0,
+                                double by1, double c, T* XBY, T* XBX, T* MASS, cudaStream_t st) {
+  const size_t N = (size_t)n1 * n2;
+  mass_prepass_kernel<T><<<grid_for(N, 256), 256, 0, st>>>(X, n1, n2, T(bx0), T(bx1), T(by0),
+                                                           T(by1), T(c), XBY, XBX, MASS);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void level_epilogue_kernel(int mode, size_t N, const T* __restrict__ KX,
+                                      const T* __restrict__ B, const T* X,
+                                      const T* __restrict__ W, T* Y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const T kx = KX[i];
+    if (mode == 0) Y[i] = kx;
+    else if (mode == 1) Y[i] = B[i] - kx;
+    else Y[i] = X[i] + W[i] * (B[i] - kx);
+  }
+}
+
+template <typename T>
+cudaError_t launch_level_epilogue(int mode, size_t N, const T* KX, const T* B, const T* X,
+                                  const T* W, T* Y, cudaStream_t st) {
+  level_epilogue_kernel<T><<<grid_for(N, 256), 256, 0, st>>>(mode, N, KX, B, X, W, Y);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void mul_kernel(size_t N, const T* __restrict__ W, const T* __restrict__ B, T* Y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x)
+    Y[i] = W[i] * B[i];
+}
+
+template <typename T>
+cudaError_t launch_mul(size_t N, const T* W, const T* B, T* Y, cudaStream_t st) {
+  mul_kernel<T><<<grid_for(N, 256), 256, 0, st>>>(N, W, B, Y);
+  return cudaGetLastError();
+}
+
+// b_c = rscale * (P_y (x) P_x)^T r, P column stencil (1/2, 1, 1/2) centred on fine 2k+1
+template <typename T>
+__global__ void restrict_kernel(const T* __restrict__ R, int n1, int n2, T rscale,
+                                T* __restrict__ BC) {
+  const int m1 = (n1 - 1) / 2, m2 = (n2 - 1) / 2;
+  const size_t NC = (size_t)m1 * m2;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < NC;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int ic = (int)(idx % m1), jc = (int)(idx / m1);
+    const int i = 2 * ic + 1, j = 2 * jc + 1;
+    const T* r0 = R + (size_t)(j - 1) * n1;
+    const T* r1 = r0 + n1;
+    const T* r2 = r1 + n1;
+    const T h = T(0.5);
+    const T s0 = h * r0[i - 1] + r0[i] + h * r0[i + 1];
+    const T s1 = h * r1[i - 1] + r1[i] + h * r1[i + 1];
+    const T s2 = h * r2[i - 1] + r2[i] + h * r2[i + 1];
+    BC[idx] = rscale * (h * s0 + s1 + h * s2);
+  }
+}
+
+template <typename T>
+cudaError_t launch_restrict(const T* R, int n1, int n2, double rscale, T* BC, cudaStream_t st) {
+  const size_t NC = (size_t)((n1 - 1) / 2) * ((n2 - 1) / 2);
+  restrict_kernel<T><<<grid_for(NC, 256), 256, 0, st>>>(R, n1, n2, T(rscale), BC);
+  return cudaGetLastError();
+}
+
+// x += (P_y (x) P_x) x_c
+template <typename T>
+__global__ void prolong_add_kernel(const T* __restrict__ XC, int n1, int n2, T* X) {
+  const int m1 = (n1 - 1) / 2, m2 = (n2 - 1) / 2;
+  const size_t N = (size_t)n1 * n2;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n1), j = (int)(idx / n1);
+    int ci[2], cj[2];
+    T wi[2], wj[2];
+    int ni, nj;
+    if (i & 1) { ci[0] = (i - 1) / 2; wi[0] = T(1); ni = 1; }
+    else { ci[0] = i / 2 - 1; ci[1] = i / 2; wi[0] = wi[1] = T(0.5); ni = 2; }
+    if (j & 1) { cj[0] = (j - 1) / 2; wj[0] = T(1); nj = 1; }
+    else { cj[0] = j / 2 - 1; cj[1] = j / 2; wj[0] = wj[1] = T(0.5); nj = 2; }
+    T s = T(0);
+    for (int b = 0; b < nj; ++b) {
+      if (cj[b] < 0 || cj[b] >= m2) continue;
+      for (int a = 0; a < ni; ++a) {
+        if (ci[a] < 0 || ci[a] >= m1) continue;
+        s += wj[b] * wi[a] * XC[(size_t)cj[b] * m1 + ci[a]];
+      }
+    }
+    X[idx] += s;
+  }
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(const T* XC, int n1, int n2, T* X, cudaStream_t st) {
+  const size_t N = (size_t)n1 * n2;
+  prolong_add_kernel<T><<<grid_for(N, 256), 256, 0, st>>>(XC, n1, n2, X);
+  return cudaGetLastError();
+}
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(size_t N, const TI* __restrict__ X, double scale, TO* Y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x)
+    Y[i] = (TO)(scale * (double)X[i]);
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_convert(size_t N, const TI* X, double scale, TO* Y, cudaStream_t st) {
+  convert_kernel<TI, TO><<<grid_for(N, 256), 256, 0, st>>>(N, X, scale, Y);
+  return cudaGetLastError();
+}
+
+__global__ void sub_kernel(size_t N, const double* __restrict__ A, const double* __restrict__ B,
+                           double* Y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x)
+    Y[i] = A[i] - B[i];
+}
+
+cudaError_t launch_sub(size_t N, const double* A, const double* B, double* Y, cudaStream_t st) {
+  sub_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, A, B, Y);
+  return cudaGetLastError();
+}
+
+__global__ void lincomb_kernel(size_t N, double a, const double* __restrict__ X, double b,
+                               const double* __restrict__ Y, double c,
+                               const double* __restrict__ Z, double* out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double v = a * X[i] + b * Y[i];
+    if (Z) v += c * Z[i];
+    out[i] = v;
+  }
+}
+
+cudaError_t launch_lincomb(size_t N, double a, const double* X, double b, const double* Y,
+                           double c, const double* Z, double* out, cudaStream_t st) {
+  lincomb_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, a, X, b, Y, c, Z, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- setup
+// Eq. (gk) by the recurrence g_k = g_{k-1} (k - 1 - gamma)/k, then the WSGD
+// combination w_k = lp g_k + lq g_{k-(p-q)} with lp = (gamma - 2q)/(2(p-q)),
+// lq = (2p - gamma)/(2(p-q)), p = 1 (Eq. w for q = 0).  One thread: the
+// recurrence is sequential and O(n).
+__global__ void wsgd_kernel(double gamma, int q, int K, double* w) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int d = 1 - q;
+  const double lp = (gamma - 2.0 * q) / (2.0 * d), lq = (2.0 - gamma) / (2.0 * d);
+  double g = 1.0, gm1 = 0.0, gm2 = 0.0;  // g_k, g_{k-1}, g_{k-2}
+  for (int k = 0; k <= K; ++k) {
+    if (k > 0) {
+      gm2 = gm1;
+      gm1 = g;
+      g = g * ((double)(k - 1) - gamma) / (double)k;
+    }
+    const double gs = (d == 1) ? gm1 : gm2;  // g_{k-d}
+    w[k] = lp * g + lq * (k >= d ? gs : 0.0);
+  }
+}
+
+cudaError_t launch_wsgd_weights(double gamma, int q, int K, double* w, cudaStream_t st) {
+  wsgd_kernel<<<1, 32, 0, st>>>(gamma, q, K, w);
+  return cudaGetLastError();
+}
+
+__global__ void generator_kernel(const double* __restrict__ w, int n, double scale, double* t) {
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x - 1; d <= n - 1; d += gridDim.x * blockDim.x)
+    t[d + 1] = -scale * w[d + 1];  // A = -[w_{i-j+1}] (Eq. AN): t_d = -w_{d+1}
+}
+
+cudaError_t launch_generator_from_weights(const double* w, int n, double scale, double* t,
+                                          cudaStream_t st) {
+  generator_kernel<<<(n + 256) / 256 + 1, 256, 0, st>>>(w, n, scale, t);
+  return cudaGetLastError();
+}
+
+// P^T T(t) P = T(t^c) for bilinear P on odd grids n = 2 nc + 1:
+// t^c_d = sum_{m=-2..2} q_m t_{2d+m}, q = (1/4, 1, 3/2, 1, 1/4), d = -1..nc-1
+__global__ void coarsen_kernel(const double* __restrict__ t, int n, double* tc, int nc) {
+  const double q[5] = {0.25, 1.0, 1.5, 1.0, 0.25};
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x - 1; d <= nc - 1;
+       d += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int m = -2; m <= 2; ++m) {
+      const int e = 2 * d + m;
+      if (e >= -1 && e <= n - 1) s += q[m + 2] * t[e + 1];
+    }
+    tc[d + 1] = s;
+  }
+}
+
+cudaError_t launch_coarsen_generator(const double* t, int n, double* tc, int nc,
+                                     cudaStream_t st) {
+  coarsen_kernel<<<(nc + 256) / 256 + 1, 256, 0, st>>>(t, n, tc, nc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void inject_kernel(const T* __restrict__ F, int n1, int n2, T* FC) {
+  const int m1 = (n1 - 1) / 2, m2 = (n2 - 1) / 2;
+  const size_t NC = (size_t)m1 * m2;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < NC;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int ic = (int)(idx % m1), jc = (int)(idx / m1);
+    FC[idx] = F[(size_t)(2 * jc + 1) * n1 + 2 * ic + 1];
+  }
+}
+
+template <typename T>
+cudaError_t launch_inject(const T* F, int n1, int n2, T* FC, cudaStream_t st) {
+  const size_t NC = (size_t)((n1 - 1) / 2) * ((n2 - 1) / 2);
+  inject_kernel<T><<<grid_for(NC, 256), 256, 0, st>>>(F, n1, n2, FC);
+  return cudaGetLastError();
+}
+
+// Level fields by injection from the finest grid: level node (j, i) is fine
+// node ((j+1) s - 1, (i+1) s - 1), s = 2^l.  diag(K_l) = c by0 bx0
+// + (d+ + d-) by0 ax0 + sigma (e+ + e-) ay0 bx0 (ax0, ay0: Toeplitz diagonals,
+// bx0, by0: Galerkin mass diagonals); W = omega / diag.
+template <typename T>
+__global__ void level_fields_kernel(const double* __restrict__ dp, const double* __restrict__ dm,
+                                    const double* __restrict__ ep, const double* __restrict__ em,
+                                    int n1f, int n1, int n2, int s, double sigma, double c,
+                                    double bx0, double by0, const double* __restrict__ tx,
+                                    const double* __restrict__ ty, double omega, T* odp, T* odm,
+                                    T* oep, T* oem, T* W) {
+  const size_t N = (size_t)n1 * n2;
+  const double ax0 = tx[1], ay0 = ty[1];  // Toeplitz diagonals t_0
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n1), j = (int)(idx / n1);
+    const size_t f = (size_t)((j + 1) * s - 1) * n1f + (size_t)((i + 1) * s - 1);
+    const double a = dp[f], b = dm[f], e = sigma * ep[f], g = sigma * em[f];
+    odp[idx] = T(a);
+    odm[idx] = T(b);
+    oep[idx] = T(e);
+    oem[idx] = T(g);
+    const double diag = c * by0 * bx0 + (a + b) * by0 * ax0 + (e + g) * ay0 * bx0;
+    if (W) W[idx] = T(omega / diag);
+  }
+}
+
+template <typename T>
+cudaError_t launch_level_fields(const double* dp, const double* dm, const double* ep,
+                                const double* em, int n1f, int n1, int n2, int stride,
+                                double sigma, double c, double bx0, double by0, const double* tx,
+                                const double* ty, double omega, T* odp, T* odm, T* oep, T* oem,
+                                T* W, cudaStream_t st) {
+  const size_t N = (size_t)n1 * n2;
+  level_fields_kernel<T><<<grid_for(N, 256), 256, 0, st>>>(dp, dm, ep, em, n1f, n1, n2, stride,
+                                                           sigma, c, bx0, by0, tx, ty, omega,
+                                                           odp, odm, oep, oem, W);
+  return cudaGetLastError();
+}
+
+// Dense coarsest operator
+//   K = c (By (x) Bx) + D+ (By (x) Ax) + D- (By (x) Ax^T) + E+ (Ay (x) Bx) + E- (Ay^T (x) Bx)
+// (E+- already scaled by sigma), inverted by Gauss-Jordan elimination with
+// partial pivoting in FP64 (one block; N <= 1024).
+__global__ void coarse_inverse_kernel(const double* __restrict__ tx, const double* __restrict__ ty,
+                                      int n1, int n2, double bx0, double bx1, double by0,
+                                      double by1, double c, const double* __restrict__ dp,
+                                      const double* __restrict__ dm,
+                                      const double* __restrict__ ep,
+                                      const double* __restrict__ em, double* A, double* inv,
+                                      int* info) {
+  const int N = n1 * n2, W2 = 2 * N;
+  __shared__ double red_v[256];
+  __shared__ int red_i[256];
+  __shared__ int piv_s;
+  auto T1 = [](const double* t, int n, int a, int b) -> double {  // Toeplitz entry (a, b)
+    const int d = a - b;
+    return (d >= -1 && d <= n - 1) ? t[d + 1] : 0.0;
+  };
+  auto B1 = [](double b0, double b1, int a, int b) -> double {
+    return a == b ? b0 : ((a - b == 1 || b - a == 1) ? b1 : 0.0);
+  };
+  for (int e = threadIdx.x; e < N * W2; e += blockDim.x) {
+    const int r = e / W2, col = e % W2;
+    double v;
+    if (col < N) {
+      const int j = r / n1, i = r % n1, jj = col / n1, ii = col % n1;
+      const double byv = B1(by0, by1, j, jj), bxv = B1(bx0, bx1, i, ii);
+      v = c * byv * bxv + dp[r] * byv * T1(tx, n1, i, ii) + dm[r] * byv * T1(tx, n1, ii, i) +
+          ep[r] * T1(ty, n2, j, jj) * bxv + em[r] * T1(ty, n2, jj, j) * bxv;
+    } else {
+      v = (col - N == r) ? 1.0 : 0.0;
+    }
+    A[e] = v;
+  }
+  __syncthreads();
+  int ok = 1;
+  for (int k = 0; k < N; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int r = k + threadIdx.x; r < N; r += blockDim.x) {
+      const double a = fabs(A[(size_t)r * W2 + k]);
+      if (a > best) { best = a; bi = r; }
+    }
+    red_v[threadIdx.x] = best;
+    red_i[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s && red_v[threadIdx.x + s] > red_v[threadIdx.x]) {
+        red_v[threadIdx.x] = red_v[threadIdx.x + s];
+        red_i[threadIdx.x] = red_i[threadIdx.x + s];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) piv_s = red_i[0];
+    if (red_v[0] == 0.0) ok = 0;
+    __syncthreads();
+    const int p = piv_s;
+    if (p != k)
+      for (int col = threadIdx.x; col < W2; col += blockDim.x) {
+        const double t = A[(size_t)k * W2 + col];
+        A[(size_t)k * W2 + col] = A[(size_t)p * W2 + col];
+        A[(size_t)p * W2 + col] = t;
+      }
+    __syncthreads();
+    const double inv_p = 1.0 / A[(size_t)k * W2 + k];
+    __syncthreads();
+    for (int col = threadIdx.x; col < W2; col += blockDim.x) A[(size_t)k * W2 + col] *= inv_p;
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * W2; e += blockDim.x) {
+      const int r = e / W2, col = e % W2;
+      if (r == k || col == k) continue;
+      A[e] -= A[(size_t)r * W2 + k] * A[(size_t)k * W2 + col];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x)
+      if (r != k) A[(size_t)r * W2 + k] = 0.0;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int r = e / N, col = e % N;
+    inv[e] = A[(size_t)r * W2 + N + col];
+  }
+  if (threadIdx.x == 0) *info = ok ? 0 : 1;
+}
+
+cudaError_t launch_coarse_inverse(const double* tx, const double* ty, int n1, int n2,
+                                  double bx0, double bx1, double by0, double by1, double c,
+                                  const double* dp, const double* dm, const double* ep,
+                                  const double* em, double* work, double* inv, int* info,
+                                  cudaStream_t st) {
+  coarse_inverse_kernel<<<1, 256, 0, st>>>(tx, ty, n1, n2, bx0, bx1, by0, by1, c, dp, dm, ep, em,
+                                           work, inv, info);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void coarse_solve_kernel(const double* __restrict__ inv, int N, const T* __restrict__ b,
+                                    T* x) {
+  extern __shared__ double bs[];
+  for (int k = threadIdx.x; k < N; k += blockDim.x) bs[k] = (double)b[k];
+  __syncthreads();
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    double s = 0.0;
+    const double* row = inv + (size_t)r * N;
+    for (int k = 0; k < N; ++k) s += row[k] * bs[k];
+    x[r] = T(s);
+  }
+}
+
+template <typename T>
+cudaError_t launch_coarse_solve(const double* inv, int N, const T* b, T* x, cudaStream_t st) {
+  coarse_solve_kernel<T><<<1, 256, N * sizeof(double), st>>>(inv, N, b, x);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- instantiations
+#define INST_T(T)                                                                               \
+  template cudaError_t launch_mass_prepass<T>(const T*, int, int, double, double, double, double, \
+                                              double, T*, T*, T*, cudaStream_t);                  \
+  template cudaError_t launch_level_epilogue<T>(int, size_t, const T*, const T*, const T*,        \
+                                                const T*, T*, cudaStream_t);                      \
+  template cudaError_t launch_mul<T>(size_t, const T*, const T*, T*, cudaStream_t);               \
+  template cudaError_t launch_restrict<T>(const T*, int, int, double, T*, cudaStream_t);          \
+  template cudaError_t launch_prolong_add<T>(const T*, int, int, T*, cudaStream_t);               \
+  template cudaError_t launch_inject<T>(const T*, int, int, T*, cudaStream_t);                    \
+  template cudaError_t launch_level_fields<T>(const double*, const double*, const double*,        \
+                                              const double*, int, int, int, int, double, double,  \
+                                              double, double, const double*, const double*,       \
+                                              double, T*, T*, T*, T*, T*, cudaStream_t);          \
+  template cudaError_t launch_coarse_solve<T>(const double*, int, const T*, T*, cudaStream_t);
+INST_T(double)
+INST_T(float)
+template cudaError_t launch_convert<double, float>(size_t, const double*, double, float*,
+                                                   cudaStream_t);
+template cudaError_t launch_convert<float, double>(size_t, const float*, double, double*,
+                                                   cudaStream_t);
+template cudaError_t launch_convert<double, double>(size_t, const double*, double, double*,
+                                                    cudaStream_t);
+
+}  // namespace fde

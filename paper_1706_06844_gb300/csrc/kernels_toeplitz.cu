@@ -1,0 +1,264 @@
+// Toeplitz products of the CN-WSGD operator on CUDA cores.
+//
+// The operator of Eq. (M)/(AxAy) applies, along every grid row (x) and every
+// grid column (y), a lower-Hessenberg Toeplitz matrix A = [t_{i-k}] (level 0:
+// t_d = -w_{d+1}, Eq. AN) and its transpose, each scaled point-wise by a
+// coefficient field.  Two evaluations live here:
+//
+//  * fft_pass: the circulant embedding of size L = 2^logL >= 2n - 1 that makes
+//    the product O(n log n) (the fast matrix-vector product noted in Sec. 1).
+//    Two real vectors are packed as one complex vector; a forward radix-2 DIF
+//    transform (natural order in, bit-reversed out) is multiplied point-wise by
+//    the bit-reversed spectra of A and A^T and two inverse DIT transforms
+//    (bit-reversed in, natural out) give A x and A^T x of both vectors at once
+//    -- no bit-reversal permutation is ever performed.
+//  * direct_pass: plain O(n^2) summation for small levels.
+#include "common.cuh"
+
+namespace fde {
+
+__device__ __forceinline__ int bitrev(int x, int bits) {
+  return (int)(__brev((unsigned)x) >> (32 - bits));
+}
+
+template <typename R>
+__device__ __forceinline__ cx<R> to_cx(cx<double> z) {
+  return {R(z.re), R(z.im)};
+}
+
+// forward transform, in place, natural order -> bit-reversed order
+template <typename R>
+__device__ void fft_dif(cx<R>* a, int logL, const cx<R>* __restrict__ tw) {
+  const int nb = 1 << (logL - 1);
+  for (int s = 0; s < logL; ++s) {
+    const int lh = logL - 1 - s;  // log2 of the butterfly span
+    const int half = 1 << lh;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const int pos = b & (half - 1);
+      const int i0 = ((b >> lh) << (lh + 1)) + pos;
+      const cx<R> u = a[i0], v = a[i0 + half];
+      a[i0] = cadd(u, v);
+      a[i0 + half] = cmul(csub(u, v), tw[pos << s]);
+    }
+    __syncthreads();
+  }
+}
+
+// inverse transform (unnormalised) of two arrays, in place,
+// bit-reversed order -> natural order
+template <typename R>
+__device__ void fft_dit_inv2(cx<R>* a, cx<R>* c, int logL, const cx<R>* __restrict__ tw) {
+  const int nb = 1 << (logL - 1);
+  for (int s = 0; s < logL; ++s) {
+    const int half = 1 << s;
+    const int tsh = logL - 1 - s;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const int pos = b & (half - 1);
+      const int i0 = ((b >> s) << (s + 1)) + pos;
+      const cx<R> w = tw[pos << tsh];
+      cx<R> t = cmulc(a[i0 + half], w);
+      cx<R> u = a[i0];
+      a[i0] = cadd(u, t);
+      a[i0 + half] = csub(u, t);
+      t = cmulc(c[i0 + half], w);
+      u = c[i0];
+      c[i0] = cadd(u, t);
+      c[i0 + half] = csub(u, t);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, typename R>
+__global__ void __launch_bounds__(512)
+fft_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int logL,
+                const cx<R>* __restrict__ S1, const cx<R>* __restrict__ S2,
+                const cx<R>* __restrict__ tw, const T* __restrict__ cp,
+                const T* __restrict__ cm, const T* __restrict__ M, R cmass, T* Y,
+                int accumulate) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = 1 << logL;
+  cx<R>* a = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* c = a + L;
+  const int npairs = (nvec + 1) >> 1;
+  for (int pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
+    const int va = 2 * pair;
+    const bool hasb = va + 1 < nvec;
+    const size_t oa = (size_t)va * vs, ob = oa + vs;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+      cx<R> z = {R(0), R(0)};
+      if (i < n) {
+        z.re = R(X[oa + (size_t)i * es]);
+        if (hasb) z.im = R(X[ob + (size_t)i * es]);
+      }
+      a[i] = z;
+    }
+    __syncthreads();
+    fft_dif(a, logL, tw);
+    for (int p = threadIdx.x; p < L; p += blockDim.x) {
+      const cx<R> z = a[p];
+      c[p] = cmul(z, S2[p]);
+      a[p] = cmul(z, S1[p]);
+    }
+    __syncthreads();
+    fft_dit_inv2(a, c, logL, tw);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const size_t ia = oa + (size_t)i * es;
+      R y = a[i].re * (cp ? R(cp[ia]) : R(1)) + c[i].re * (cm ? R(cm[ia]) : R(1));
+      if (M) y += cmass * R(M[ia]);
+      if (accumulate) y += R(Y[ia]);
+      Y[ia] = T(y);
+      if (hasb) {
+        const size_t ib = ob + (size_t)i * es;
+        R yb = a[i].im * (cp ? R(cp[ib]) : R(1)) + c[i].im * (cm ? R(cm[ib]) : R(1));
+        if (M) yb += cmass * R(M[ib]);
+        if (accumulate) yb += R(Y[ib]);
+        Y[ib] = T(yb);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, typename R>
+cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int logL,
+                            const cx<R>* S1, const cx<R>* S2, const cx<R>* tw, const T* cp,
+                            const T* cm, const T* M, double cmass, T* Y, int accumulate,
+                            cudaStream_t st) {
+  const int L = 1 << logL;
+  const size_t smem = 2 * (size_t)L * sizeof(cx<R>);
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int threads = L / 2 < 512 ? L / 2 : 512;
+  const int npairs = (nvec + 1) / 2;
+  const int per_sm = (int)((227 * 1024) / (smem + 1024));
+  int grid = 152 * (per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm));
+  if (grid > npairs) grid = npairs;
+  fft_pass_kernel<T, R><<<grid, threads, smem, st>>>(X, es, vs, nvec, n, logL, S1, S2, tw, cp, cm,
+                                                     M, R(cmass), Y, accumulate);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- spectra
+template <typename R>
+__global__ void build_spectra_kernel(const double* __restrict__ t, int n, int logL, double scale,
+                                     cx<R>* S1, cx<R>* S2, cx<R>* twout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = 1 << logL;
+  cx<double>* a = reinterpret_cast<cx<double>*>(smem_raw);
+  cx<double>* tw = a + L;
+  for (int k = threadIdx.x; k < L / 2; k += blockDim.x) {
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)L, &s, &c);
+    tw[k] = {c, s};
+    if (twout) twout[k] = to_cx<R>(tw[k]);
+  }
+  // z = h1 + i h2: h1 embeds A (h1[d mod L] = t_d, d = -1..n-1) and h2 embeds
+  // A^T (h2[m mod L] = t_{-m}, m = -(n-1)..1); L >= 2n - 1 keeps them apart.
+  for (int m = threadIdx.x; m < L; m += blockDim.x) {
+    const int d1 = (m <= n - 1) ? m : m - L;
+    const double h1 = (d1 >= -1 && d1 <= n - 1) ? t[d1 + 1] : 0.0;
+    const int m2 = (m <= 1) ? m : m - L;
+    const double h2 = (m2 >= -(n - 1) && m2 <= 1) ? t[-m2 + 1] : 0.0;
+    a[m] = {h1, h2};
+  }
+  __syncthreads();
+  fft_dif(a, logL, tw);
+  const double sc = scale / (double)L;
+  for (int p = threadIdx.x; p < L; p += blockDim.x) {
+    const int f = bitrev(p, logL);
+    const int pp = bitrev((L - f) & (L - 1), logL);
+    const cx<double> z = a[p], zc = {a[pp].re, -a[pp].im};
+    const cx<double> h1 = {0.5 * (z.re + zc.re) * sc, 0.5 * (z.im + zc.im) * sc};
+    // (z - zc) / (2i)
+    const cx<double> h2 = {0.5 * (z.im - zc.im) * sc, -0.5 * (z.re - zc.re) * sc};
+    S1[p] = to_cx<R>(h1);
+    S2[p] = to_cx<R>(h2);
+  }
+}
+
+template <typename R>
+cudaError_t launch_build_spectra(const double* t, int n, int logL, double scale, cx<R>* S1,
+                                 cx<R>* S2, cx<R>* tw, cudaStream_t st) {
+  const int L = 1 << logL;
+  const size_t smem = (size_t)L * sizeof(cx<double>) + (size_t)(L / 2) * sizeof(cx<double>);
+  cudaError_t e = cudaFuncSetAttribute(build_spectra_kernel<R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return e;
+  build_spectra_kernel<R><<<1, 512, smem, st>>>(t, n, logL, scale, S1, S2, tw);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- direct
+template <typename T>
+__global__ void direct_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n,
+                                   const T* __restrict__ t, const T* __restrict__ cp,
+                                   const T* __restrict__ cm, const T* __restrict__ M, T cmass,
+                                   T* Y, int accumulate) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ts = reinterpret_cast<T*>(smem_raw);  // t_d at ts[d+1], d = -1..n-1
+  T* xs = ts + (n + 1);
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) ts[k] = t[k];
+  for (int v = blockIdx.x; v < nvec; v += gridDim.x) {
+    const size_t o = (size_t)v * vs;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) xs[k] = X[o + (size_t)k * es];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      T s1 = T(0), s2 = T(0);
+      const int k1 = (i + 1 < n - 1) ? i + 1 : n - 1;
+      for (int k = 0; k <= k1; ++k) s1 += ts[i - k + 1] * xs[k];  // (A x)_i, t_{i-k}
+      for (int k = (i > 0 ? i - 1 : 0); k < n; ++k) s2 += ts[k - i + 1] * xs[k];  // (A^T x)_i
+      const size_t ia = o + (size_t)i * es;
+      T y = s1 * (cp ? cp[ia] : T(1)) + s2 * (cm ? cm[ia] : T(1));
+      if (M) y += cmass * M[ia];
+      if (accumulate) y += Y[ia];
+      Y[ia] = y;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+cudaError_t launch_direct_pass(const T* X, int es, int vs, int nvec, int n, const T* t,
+                               const T* cp, const T* cm, const T* M, double cmass, T* Y,
+                               int accumulate, cudaStream_t st) {
+  const size_t smem = (size_t)(2 * n + 1) * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(direct_pass_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+  }
+  int grid = nvec < 1216 ? nvec : 1216;
+  direct_pass_kernel<T><<<grid, 128, smem, st>>>(X, es, vs, nvec, n, t, cp, cm, M, T(cmass), Y,
+                                                 accumulate);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- instantiations
+template cudaError_t launch_fft_pass<double, double>(const double*, int, int, int, int, int,
+                                                     const cx<double>*, const cx<double>*,
+                                                     const cx<double>*, const double*,
+                                                     const double*, const double*, double,
+                                                     double*, int, cudaStream_t);
+template cudaError_t launch_fft_pass<float, float>(const float*, int, int, int, int, int,
+                                                   const cx<float>*, const cx<float>*,
+                                                   const cx<float>*, const float*, const float*,
+                                                   const float*, double, float*, int,
+                                                   cudaStream_t);
+template cudaError_t launch_build_spectra<double>(const double*, int, int, double, cx<double>*,
+                                                  cx<double>*, cx<double>*, cudaStream_t);
+template cudaError_t launch_build_spectra<float>(const double*, int, int, double, cx<float>*,
+                                                 cx<float>*, cx<float>*, cudaStream_t);
+template cudaError_t launch_direct_pass<double>(const double*, int, int, int, int, const double*,
+                                                const double*, const double*, const double*,
+                                                double, double*, int, cudaStream_t);
+template cudaError_t launch_direct_pass<float>(const float*, int, int, int, int, const float*,
+                                               const float*, const float*, const float*, double,
+                                               float*, int, cudaStream_t);
+
+}  // namespace fde

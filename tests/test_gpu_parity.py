@@ -1,0 +1,231 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Sizes span several FFT lengths, ragged (non-power-of-two) grids,
+non-square grids and both WSGD shifts; tolerances come from the arithmetic
+and are written next to each check."""
+import numpy as np
+import pytest
+
+from paper_1706_06844_gb300 import inputs
+from paper_1706_06844_gb300 import fde
+from gpu_util import Case, dev, host
+
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    fde.lib()
+
+
+def _cases():
+    return [
+        ("unit_63", lambda: Case(inputs.constant_unit(), 63)),
+        ("power_31x63", lambda: Case(inputs.power_law(), 31, 63)),
+        ("perturbed_127", lambda: Case(inputs.perturbed_power_law(), 127)),
+        ("example1_15", lambda: Case(inputs.example1(), 15)),
+    ]
+
+
+@pytest.mark.parametrize("name,mk", _cases())
+def test_weights_on_device(name, mk):
+    # Eq. (gk)/(w): same recurrence in FP64 on both sides; the GPU may fuse the
+    # final combination into an FMA, so allow a few ulps
+    case = mk()
+    h = case.handle()
+    try:
+        w = np.array(fde.fde_weights(h, 0, case.n1 + 1))
+        np.testing.assert_allclose(w, case.wx[: case.n1 + 1], rtol=4 * EPS, atol=4 * EPS)
+        w = np.array(fde.fde_weights(h, 1, case.n2 + 1))
+        np.testing.assert_allclose(w, case.wy[: case.n2 + 1], rtol=4 * EPS, atol=4 * EPS)
+    finally:
+        fde.fde_destroy(h)
+
+
+@pytest.mark.parametrize("name,mk", _cases())
+def test_outer_apply_and_rhs(name, mk):
+    # FFT-embedding product in FP64: error ~ eps log2(L) times the absolute
+    # sums |c||x| + |D||A||x| + ...; 64 eps leaves room for log2(L) <= 9
+    import torch
+    case = mk()
+    h = case.handle()
+    try:
+        rng = np.random.default_rng(3)
+        X = rng.standard_normal((case.n2, case.n1))
+        y = torch.empty_like(dev(X))
+        fde.fde_apply(h, dev(X), y)
+        torch.cuda.synchronize()
+        ref = case.oracle_apply(X)
+        bound = 64 * EPS * case.oracle_abs_apply(X)
+        assert np.all(np.abs(host(y) - ref) <= bound)
+        b = torch.empty_like(y)
+        fde.fde_rhs(h, dev(case.u0), dev(case.v), b)
+        torch.cuda.synchronize()
+        rb = case.oracle_rhs()
+        assert np.max(np.abs(host(b) - rb)) <= 1e-12 * np.max(np.abs(rb))
+    finally:
+        fde.fde_destroy(h)
+
+
+@pytest.mark.parametrize("precond", [fde.FDE_PRECOND_MG_SG, fde.FDE_PRECOND_MG_REDISC])
+@pytest.mark.parametrize("n1,n2", [(63, 63), (127, 127), (31, 63), (255, 255)])
+def test_fp64_vcycle_matches_oracle(precond, n1, n2):
+    # one V-cycle (Sec. 4) in FP64: same algorithm, rounding-order differences
+    # only (FFT vs matmul products): relative 1e-11
+    import torch
+    from oracle import multigrid as mg
+    case = Case(inputs.perturbed_power_law(), n1, n2, precond=precond)
+    h = case.handle()
+    try:
+        hier = case.oracle_hierarchy()
+        rng = np.random.default_rng(5)
+        R = rng.standard_normal((n2, n1))
+        z = torch.empty_like(dev(R))
+        fde.fde_vcycle(h, dev(R), z)
+        torch.cuda.synchronize()
+        ref = mg.vcycle(hier, R, case.params.omega, case.params.nu_pre, case.params.nu_post)
+        err = np.max(np.abs(host(z) - ref)) / np.max(np.abs(ref))
+        assert err <= 1e-11, err
+        # every level operator
+        levels = fde.fde_levels(h)
+        assert [(L.n1, L.n2) for L in hier.levels] == levels
+        for l, lev in enumerate(hier.levels):
+            Xl = rng.standard_normal((lev.n2, lev.n1))
+            yl = torch.empty_like(dev(Xl))
+            fde.fde_level_apply(h, l, dev(Xl), yl)
+            torch.cuda.synchronize()
+            rl = lev.apply(Xl)
+            assert np.max(np.abs(host(yl) - rl)) <= 1e-12 * np.max(np.abs(rl)), l
+    finally:
+        fde.fde_destroy(h)
+
+
+@pytest.mark.parametrize("precond", [fde.FDE_PRECOND_MG_SG, fde.FDE_PRECOND_MG_REDISC])
+def test_fp32_vcycle_close_to_oracle(precond):
+    # FP32 V-cycle: the cycle is linear and contractive, so the FP32 result
+    # stays within a few hundred FP32 ulps of the FP64 one (relative 1e-4)
+    import torch
+    from oracle import multigrid as mg
+    case = Case(inputs.perturbed_power_law(), 255, precond=precond,
+                precision=fde.FDE_PREC_FP32)
+    h = case.handle()
+    try:
+        hier = case.oracle_hierarchy()
+        R = np.random.default_rng(6).standard_normal((255, 255))
+        z = torch.empty_like(dev(R))
+        fde.fde_vcycle(h, dev(R), z)
+        torch.cuda.synchronize()
+        ref = mg.vcycle(hier, R, 0.7, 1, 1)
+        assert np.linalg.norm(host(z) - ref) <= 1e-4 * np.linalg.norm(ref)
+    finally:
+        fde.fde_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [fde.FDE_PREC_FP64, fde.FDE_PREC_FP32])
+@pytest.mark.parametrize("name,mk", _cases()[:3])
+def test_solve_matches_oracle(name, mk, precision):
+    # FGMRES to rtol 1e-10 on both sides: the GPU's true residual (re-checked by
+    # the oracle) meets rtol, the solutions agree within the conditioning bound,
+    # and iteration counts differ by at most one (CGS2 vs MGS rounding)
+    import torch
+    from oracle.krylov import fgmres
+    from oracle import multigrid as mg
+    case = mk()
+    case.params.rtol = 1e-10
+    case.params.precision = precision
+    h = case.handle()
+    try:
+        B = case.oracle_rhs()
+        x = torch.empty_like(dev(B))
+        st = fde.fde_solve(h, dev(B), x)
+        xg = host(x)
+        res = np.linalg.norm(B - case.oracle_apply(xg)) / np.linalg.norm(B)
+        assert st.converged == 1 and res <= 1.05e-10, res
+        hier = case.oracle_hierarchy()
+        xo, its, rel, ok = fgmres(case.oracle_apply, B, lambda R: mg.vcycle(hier, R), 30, 1e-10)
+        assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
+        if precision == fde.FDE_PREC_FP64:
+            assert abs(st.iterations - its) <= 1, (st.iterations, its)
+        else:
+            assert abs(st.iterations - its) <= 2, (st.iterations, its)
+    finally:
+        fde.fde_destroy(h)
+
+
+def test_time_loop_matches_oracle():
+    # eight CN steps (Eq. CNWSGD) of the constant-coefficient bubble at n = 63:
+    # each step's solution within 1e-8 (relative L2) of the oracle's solve
+    import torch
+    from oracle.krylov import fgmres
+    from oracle import multigrid as mg
+    from oracle.operator import rhs, apply_M
+    prob = inputs.constant_unit()
+    n, steps = 63, 8
+    case = Case(prob, n, rtol=1e-10)
+    h = case.handle()
+    try:
+        X, Y, hx, hy = prob.grid(n, n)
+        dt = case.dt
+        U = prob.exact(X, Y, 0.0)
+        ud = dev(U)
+        un = torch.empty_like(ud)
+        c, s = case.sc["c"], case.sc["sigma"]
+        hier = case.oracle_hierarchy()
+        for m in range(1, steps + 1):
+            V = prob.source(X, Y, (m - 0.5) * dt)
+            st = fde.fde_step(h, ud, dev(V), un)
+            B = rhs(U, case.wx, case.wy, c, s, *case.coef_old, V, hx, prob.alpha)
+            U, its, rel, ok = fgmres(lambda Z: apply_M(Z, case.wx, case.wy, c, s, *case.coef_new),
+                                     B, lambda R: mg.vcycle(hier, R), 30, 1e-12)
+            ug = host(un)
+            assert np.linalg.norm(ug - U) <= 1e-8 * np.linalg.norm(U), m
+            ud, un = un, ud
+        assert fde.fde_get_state(h) == steps
+    finally:
+        fde.fde_destroy(h)
+
+
+def test_step_host_matches_device_step():
+    import torch
+    case = Case(inputs.perturbed_power_law(), 63)
+    h = case.handle()
+    try:
+        u_next = np.zeros_like(case.u0)
+        st1 = fde.fde_step_host(h, np.ascontiguousarray(case.u0), np.ascontiguousarray(case.v), u_next)
+        x = torch.empty_like(dev(case.u0))
+        st2 = fde.fde_step(h, dev(case.u0), dev(case.v), x)
+        assert st1.iterations == st2.iterations
+        np.testing.assert_array_equal(u_next, host(x))
+    finally:
+        fde.fde_destroy(h)
+
+
+def test_error_paths():
+    # host-side failure injection: bad arguments, non-finite data, too few iterations
+    import torch
+    with pytest.raises(fde.FDEError) as e:
+        fde.fde_create(fde.params(n1=64, n2=64))  # even sizes cannot be coarsened
+    assert e.value.code == fde.FDE_ERR_UNSUPPORTED
+    case = Case(inputs.perturbed_power_law(), 63, maxit=1)
+    h = case.handle()
+    try:
+        B = dev(case.oracle_rhs())
+        x = torch.empty_like(B)
+        st = fde.fde_solve(h, B, x, allow_not_converged=True)
+        assert st.converged == 0 and st.iterations == 1
+        with pytest.raises(fde.FDEError) as e:
+            fde.fde_solve(h, B, x)
+        assert e.value.code == fde.FDE_ERR_NOT_CONVERGED
+        Bn = B.clone()
+        Bn[3, 4] = float("nan")
+        with pytest.raises(fde.FDEError) as e:
+            fde.fde_solve(h, Bn, x)
+        assert e.value.code == fde.FDE_ERR_NONFINITE
+        with pytest.raises(fde.FDEError) as e:
+            fde.fde_apply(h, B, B)
+        assert e.value.code == fde.FDE_ERR_ARG
+    finally:
+        fde.fde_destroy(h)
