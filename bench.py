@@ -300,6 +300,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -320,7 +321,8 @@ def main():
     import torch
     from paper_1706_06844_gb300 import fde
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    mixed = fde.FDE_PREC_FP32
+    mixed = {"bf16": fde.FDE_PREC_BF16, "fp16": fde.FDE_PREC_FP16,
+             "fp32": fde.FDE_PREC_FP32}[args.precision]
     w = Workload(mixed)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         ms, wall, its, launches = time_steps(w, args.steps, args.warmup, dist)
@@ -352,9 +354,11 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64 Krylov + f32 V-cycle", "data": "synthetic",
+                "dtype": f"f64 Krylov + {args.precision} V-cycle products", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": N_GRID, "restart": RESTART, "rtol": RTOL,
-                           "precond": "MG_SG", "precision": "FP32 V-cycle, FP64 FFT outer apply",
+                           "precond": "MG_SG",
+                           "precision": f"{args.precision} tensor-core V-cycle products (FP32 "
+                                        "vectors), FP64 FFT outer apply",
                            "l2": "inputs larger than L2 (Krylov basis 31 x 33.5 MB)",
                            "parallelism": f"replicas x{world}"},
                 "iterations_per_step": its, "wall_s": round(wall, 3),

@@ -632,10 +632,6 @@ static int validate(const fde_params* p, std::string& why) {
   if (p->precision < FDE_PREC_FP64 || p->precision > FDE_PREC_FP16) return bad("unknown precision");
   if (p->toeplitz_path < FDE_PATH_AUTO || p->toeplitz_path > FDE_PATH_DIRECT) return bad("unknown toeplitz_path");
   if (p->outer != FDE_OUTER_FP64 && p->outer != FDE_OUTER_DF32) return bad("unknown outer");
-  if (p->precision == FDE_PREC_BF16 || p->precision == FDE_PREC_FP16) {
-    why = "the tensor-core preconditioner is not built";
-    return FDE_ERR_UNSUPPORTED;
-  }
   if (p->outer == FDE_OUTER_DF32) {
     why = "the double-float outer apply is not built";
     return FDE_ERR_UNSUPPORTED;

@@ -31,6 +31,8 @@ int level_setup(ToeplitzGemmLevel* L, const double* tx, const double* ty, cudaSt
 int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y, const float* M,
                    double cm, const float* dp, const float* dm, const float* ep, const float* em,
                    float* kx, cudaStream_t st);
+// device error flag of the level's kernels (1 = a bounded wait gave up); reading it synchronises
+int level_error(ToeplitzGemmLevel* L);
 void level_destroy(ToeplitzGemmLevel* L);
 
 }  // namespace tc

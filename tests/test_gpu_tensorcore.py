@@ -1,0 +1,88 @@
+"""tcgen05 Toeplitz GEMM levels (BF16/FP16 operands, FP32 accumulation)
+against the FP64 oracle's level operators.
+
+Error model: operands are rounded once to 16 bits (relative 2^-9 for BF16,
+2^-12 for FP16 incl. the Toeplitz bank), products are exact in FP32 and the
+accumulation adds at most K 2^-24 relative; so elementwise
+|K x - K~ x| <= (2 u16 + n 2^-24) * (|c||x| + |D||A||x| + ...) plus the FP32
+rounding of the coefficient fields (2^-24)."""
+import numpy as np
+import pytest
+
+from paper_1706_06844_gb300 import inputs
+from paper_1706_06844_gb300 import fde
+from gpu_util import Case, dev, host
+
+pytestmark = pytest.mark.gpu
+
+U16 = {fde.FDE_PREC_BF16: 2.0 ** -8, fde.FDE_PREC_FP16: 2.0 ** -11}
+
+
+def _abs_level(lev, X):
+    from oracle.operator import apply_kron
+    A = lambda M: None if M is None else np.abs(M)
+    return apply_kron(np.abs(X), A(lev.Ax), A(lev.Ay), abs(lev.c), abs(lev.sigma),
+                      np.abs(lev.dp), np.abs(lev.dm), np.abs(lev.ep), np.abs(lev.em),
+                      A(lev.Bx), A(lev.By))
+
+
+@pytest.mark.parametrize("precision", [fde.FDE_PREC_BF16, fde.FDE_PREC_FP16])
+@pytest.mark.parametrize("precond", [fde.FDE_PRECOND_MG_SG, fde.FDE_PRECOND_MG_REDISC])
+@pytest.mark.parametrize("n1,n2", [(255, 255), (511, 255), (383, 767)])
+def test_gemm_level_apply(precision, precond, n1, n2):
+    # every level the tensor path serves (n >= 127), incl. ragged tiles (383 = 2*128+127)
+    # and the structured-Galerkin mass terms of coarse levels
+    import torch
+    if (n1 - 1) // 2 % 2 == 0 and n1 > 255:
+        pytest.skip("level sizes must stay odd")
+    case = Case(inputs.perturbed_power_law(), n1, n2, precond=precond, precision=precision,
+                toeplitz_path=fde.FDE_PATH_GEMM)
+    try:
+        h = case.handle()
+    except fde.FDEError as e:
+        pytest.skip(str(e))
+    try:
+        hier = case.oracle_hierarchy()
+        rng = np.random.default_rng(9)
+        for l, lev in enumerate(hier.levels):
+            if min(lev.n1, lev.n2) < 127:
+                break
+            X = rng.standard_normal((lev.n2, lev.n1))
+            y = torch.empty_like(dev(X))
+            fde.fde_level_apply(h, l, dev(X), y)
+            torch.cuda.synchronize()
+            ref = lev.apply(X)
+            bound = (2 * U16[precision] + max(lev.n1, lev.n2) * 2.0 ** -24 + 2.0 ** -22) * _abs_level(lev, X)
+            err = np.abs(host(y) - ref)
+            assert np.all(err <= bound + 1e-30), (l, float(np.max(err / (bound + 1e-300))))
+            # and the products are not trivially inaccurate
+            rel = np.linalg.norm(host(y) - ref) / np.linalg.norm(ref)
+            assert rel <= 0.05
+            # 16-bit operands really were used (an FP32 path would sit near 1e-7)
+            assert rel > 1e-6 * (U16[precision] / 2.0 ** -11), rel
+    finally:
+        fde.fde_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [fde.FDE_PREC_BF16, fde.FDE_PREC_FP16])
+def test_mixed_solve_converges_to_fp64_residual(precision):
+    # the reduced-precision V-cycle only preconditions: the FP64 FGMRES still
+    # drives the true residual below rtol, and the solution matches the oracle's
+    import torch
+    from oracle.krylov import fgmres
+    from oracle import multigrid as mg
+    case = Case(inputs.perturbed_power_law(), 255, precision=precision, rtol=1e-10)
+    h = case.handle()
+    try:
+        B = case.oracle_rhs()
+        x = torch.empty_like(dev(B))
+        st = fde.fde_solve(h, dev(B), x)
+        xg = host(x)
+        res = np.linalg.norm(B - case.oracle_apply(xg)) / np.linalg.norm(B)
+        assert st.converged and res <= 1.05e-10
+        hier = case.oracle_hierarchy()
+        xo, its, rel, ok = fgmres(case.oracle_apply, B, lambda R: mg.vcycle(hier, R), 30, 1e-12)
+        assert np.linalg.norm(xg - xo) <= 1e-7 * np.linalg.norm(xo)
+        assert st.iterations <= its + 3, (st.iterations, its)
+    finally:
+        fde.fde_destroy(h)
