@@ -292,8 +292,40 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def kernel_micro(kind, reps):
+    """One kernel class in isolation at the bench grid, for profiler captures:
+    gemm / fft32 = level-0 V-cycle products (BF16 tcgen05 GEMM / FP32 FFT),
+    fft64 / fftdf = the outer apply (FP64 / double-float FFT)."""
+    import torch
+    from paper_1706_06844_gb300 import fde
+    prec = {"gemm": fde.FDE_PREC_BF16, "fft32": fde.FDE_PREC_FP32, "fft64": fde.FDE_PREC_FP64,
+            "fftdf": fde.FDE_PREC_FP64}[kind]
+    path = {"gemm": fde.FDE_PATH_GEMM, "fft32": fde.FDE_PATH_FFT}.get(kind)
+    outer = fde.FDE_OUTER_DF32 if kind == "fftdf" else None
+    w = Workload(prec, path=path, outer=outer)
+    x = torch.randn((N_GRID, N_GRID), dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    call = ((lambda: fde.fde_level_apply(w.h, 0, x, y)) if kind in ("gemm", "fft32")
+            else (lambda: fde.fde_apply(w.h, x, y)))
+    for _ in range(2):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": kind, "n": N_GRID, "reps": reps,
+                      "ms_per_call": round(e0.elapsed_time(e1) / reps, 4)}))
+    w.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel", default=None, choices=["gemm", "fft32", "fft64", "fftdf"],
+                    help="time one kernel class alone (for profiler captures)")
+    ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=3)
@@ -302,6 +334,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     args = ap.parse_args()
+    if args.kernel:
+        kernel_micro(args.kernel, args.reps)
+        return
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -8,6 +8,8 @@
 
 namespace fde {
 
+struct df;  // double-float value (df32.cuh)
+
 // ---------------------------------------------------------------- complex
 template <typename R>
 struct cx {
@@ -38,16 +40,17 @@ __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
 // A = [t_{i-k}] is the lower-Hessenberg Toeplitz matrix whose spectra S1 (A)
 // and S2 (A^T) were built by build_spectra for the same L.  M, cp, cm may be
 // null (term omitted; null cp/cm means 1).  T: storage type, R: FFT arithmetic.
-template <typename T, typename R>
+// C: storage type of the coefficient fields (T, or df for the double-float path).
+template <typename T, typename R, typename C>
 cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int logL,
                             const cx<R>* S1, const cx<R>* S2, const cx<R>* tw,
-                            const T* cp, const T* cm, const T* M, double cmass,
+                            const C* cp, const C* cm, const T* M, double cmass,
                             T* Y, int accumulate, cudaStream_t st);
 
 // Spectra of the circulant embeddings (length L = 2^logL >= 2n - 1) of A and A^T,
 // A = [t_{i-k}], generator t_d at t[d+1] for d = -1..n-1, scaled by scale/L and
-// stored in bit-reversed order.  Also fills the twiddle table tw[k] = e^{-2 pi i k/L},
-// k < L/2 (when tw is non-null).
+// stored in bit-reversed order.  Also fills (when tw is non-null) the twiddle
+// table of length L - 1: tw[half - 1 + pos] = e^{-2 pi i pos/(2 half)}.
 template <typename R>
 cudaError_t launch_build_spectra(const double* t, int n, int logL, double scale, cx<R>* S1,
                                  cx<R>* S2, cx<R>* tw, cudaStream_t st);
@@ -88,6 +91,8 @@ cudaError_t launch_prolong_add(const T* XC, int n1, int n2, T* X, cudaStream_t s
 template <typename TI, typename TO>
 cudaError_t launch_convert(size_t N, const TI* X, double scale, TO* Y, cudaStream_t st);
 
+// double -> double-float copy of a field, scaled: Y = scale * X
+cudaError_t launch_to_df(size_t N, const double* X, double scale, df* Y, cudaStream_t st);
 // Y = A - B (FP64)
 cudaError_t launch_sub(size_t N, const double* A, const double* B, double* Y, cudaStream_t st);
 

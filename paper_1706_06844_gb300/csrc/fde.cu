@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "df32.cuh"
 #include "tc_gemm.h"
 #include "../../include/fde.h"
 
@@ -55,6 +56,10 @@ struct fde_handle {
   double *dpN = nullptr, *dmN = nullptr, *epN = nullptr, *emN = nullptr;  // unscaled, t^(m)
   double *epNs = nullptr, *emNs = nullptr;                                 // sigma-scaled
   double *dpO = nullptr, *dmO = nullptr, *epOs = nullptr, *emOs = nullptr;  // t^(m-1)
+  // double-float copies for the df32 outer apply: {dp, dm, sigma ep, sigma em}
+  cx<df> *S1xd = nullptr, *S2xd = nullptr, *S1yd = nullptr, *S2yd = nullptr, *twxd = nullptr,
+         *twyd = nullptr;
+  df *cfN[4] = {nullptr, nullptr, nullptr, nullptr}, *cfO[4] = {nullptr, nullptr, nullptr, nullptr};
   bool have_new = false, have_old = false;
 
   std::unique_ptr<MGBase> mg;
@@ -255,10 +260,10 @@ struct MG : MGBase {
           return h->fail(FDE_ERR_UNSUPPORTED, "FFT length too large for shared memory");
         RCHK(h->alloc(&L.S1x, (size_t)1 << L.logLx));
         RCHK(h->alloc(&L.S2x, (size_t)1 << L.logLx));
-        RCHK(h->alloc(&L.twx, (size_t)1 << (L.logLx - 1)));
+        RCHK(h->alloc(&L.twx, (size_t)1 << L.logLx));
         RCHK(h->alloc(&L.S1y, (size_t)1 << L.logLy));
         RCHK(h->alloc(&L.S2y, (size_t)1 << L.logLy));
-        RCHK(h->alloc(&L.twy, (size_t)1 << (L.logLy - 1)));
+        RCHK(h->alloc(&L.twy, (size_t)1 << L.logLy));
       } else if (path == FDE_PATH_DIRECT) {
         RCHK(h->alloc(&L.txT, L.n1 + 2));
         RCHK(h->alloc(&L.tyT, L.n2 + 2));
@@ -341,9 +346,9 @@ struct MG : MGBase {
     }
     const int pi = h->pbeg(FDE_KCLASS_LEVEL_APPLY);
     if (L.path == FDE_PATH_FFT) {
-      LCHK((launch_fft_pass<T, T>(xin_x, 1, L.n1, L.n2, L.n1, L.logLx, L.S1x, L.S2x, L.twx, L.dp,
+      LCHK((launch_fft_pass<T, T, T>(xin_x, 1, L.n1, L.n2, L.n1, L.logLx, L.S1x, L.S2x, L.twx, L.dp,
                                   L.dm, M, cm, kx, 0, st)));
-      LCHK((launch_fft_pass<T, T>(xin_y, L.n1, 1, L.n1, L.n2, L.logLy, L.S1y, L.S2y, L.twy, L.ep,
+      LCHK((launch_fft_pass<T, T, T>(xin_y, L.n1, 1, L.n1, L.n2, L.logLy, L.S1y, L.S2y, L.twy, L.ep,
                                   L.em, nullptr, 0.0, kx, 1, st)));
     } else if (L.path == FDE_PATH_DIRECT) {
       LCHK(launch_direct_pass<T>(xin_x, 1, L.n1, L.n2, L.n1, L.txT, L.dp, L.dm, M, cm, kx, 0, st));
@@ -449,16 +454,28 @@ struct MG : MGBase {
 // FP64-accurate outer operator
 
 static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
+  if (h->p.outer == FDE_OUTER_DF32) {
+    df* const* cf = old ? h->cfO : h->cfN;
+    int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
+    LCHK((launch_fft_pass<double, df, df>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1xd, h->S2xd,
+                                          h->twxd, cf[0], cf[1], x, h->c, y, 0, h->st)));
+    h->pend(pi);
+    pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
+    LCHK((launch_fft_pass<double, df, df>(x, h->n1, 1, h->n1, h->n2, h->logLy, h->S1yd, h->S2yd,
+                                          h->twyd, cf[2], cf[3], nullptr, 0.0, y, 1, h->st)));
+    h->pend(pi);
+    return FDE_OK;
+  }
   const double* dp = old ? h->dpO : h->dpN;
   const double* dm = old ? h->dmO : h->dmN;
   const double* ep = old ? h->epOs : h->epNs;
   const double* em = old ? h->emOs : h->emNs;
   int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
-  LCHK((launch_fft_pass<double, double>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x, h->S2x,
+  LCHK((launch_fft_pass<double, double, double>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x, h->S2x,
                                         h->twx, dp, dm, x, h->c, y, 0, h->st)));
   h->pend(pi);
   pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
-  LCHK((launch_fft_pass<double, double>(x, h->n1, 1, h->n1, h->n2, h->logLy, h->S1y, h->S2y,
+  LCHK((launch_fft_pass<double, double, double>(x, h->n1, 1, h->n1, h->n2, h->logLy, h->S1y, h->S2y,
                                         h->twy, ep, em, nullptr, 0.0, y, 1, h->st)));
   h->pend(pi);
   return FDE_OK;
@@ -632,10 +649,6 @@ static int validate(const fde_params* p, std::string& why) {
   if (p->precision < FDE_PREC_FP64 || p->precision > FDE_PREC_FP16) return bad("unknown precision");
   if (p->toeplitz_path < FDE_PATH_AUTO || p->toeplitz_path > FDE_PATH_DIRECT) return bad("unknown toeplitz_path");
   if (p->outer != FDE_OUTER_FP64 && p->outer != FDE_OUTER_DF32) return bad("unknown outer");
-  if (p->outer == FDE_OUTER_DF32) {
-    why = "the double-float outer apply is not built";
-    return FDE_ERR_UNSUPPORTED;
-  }
   const int L1 = ceil_log2(2L * p->n1 - 1), L2 = ceil_log2(2L * p->n2 - 1);
   if (L1 > 12 || L2 > 12) {
     snprintf(buf, sizeof(buf), "FP64 FFT apply supports n <= 2048 (got %d x %d)", p->n1, p->n2);
@@ -688,12 +701,26 @@ int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
     h->logLy = ceil_log2(2L * p.n2 - 1);
     RCHK(h->alloc(&h->S1x, (size_t)1 << h->logLx));
     RCHK(h->alloc(&h->S2x, (size_t)1 << h->logLx));
-    RCHK(h->alloc(&h->twx, (size_t)1 << (h->logLx - 1)));
+    RCHK(h->alloc(&h->twx, (size_t)1 << h->logLx));
     RCHK(h->alloc(&h->S1y, (size_t)1 << h->logLy));
     RCHK(h->alloc(&h->S2y, (size_t)1 << h->logLy));
-    RCHK(h->alloc(&h->twy, (size_t)1 << (h->logLy - 1)));
+    RCHK(h->alloc(&h->twy, (size_t)1 << h->logLy));
     LCHK(launch_build_spectra<double>(h->tx0, p.n1, h->logLx, 1.0, h->S1x, h->S2x, h->twx, h->st));
     LCHK(launch_build_spectra<double>(h->ty0, p.n2, h->logLy, 1.0, h->S1y, h->S2y, h->twy, h->st));
+    if (p.outer == FDE_OUTER_DF32) {
+      RCHK(h->alloc(&h->S1xd, (size_t)1 << h->logLx));
+      RCHK(h->alloc(&h->S2xd, (size_t)1 << h->logLx));
+      RCHK(h->alloc(&h->twxd, (size_t)1 << h->logLx));
+      RCHK(h->alloc(&h->S1yd, (size_t)1 << h->logLy));
+      RCHK(h->alloc(&h->S2yd, (size_t)1 << h->logLy));
+      RCHK(h->alloc(&h->twyd, (size_t)1 << h->logLy));
+      LCHK(launch_build_spectra<df>(h->tx0, p.n1, h->logLx, 1.0, h->S1xd, h->S2xd, h->twxd, h->st));
+      LCHK(launch_build_spectra<df>(h->ty0, p.n2, h->logLy, 1.0, h->S1yd, h->S2yd, h->twyd, h->st));
+      for (int k = 0; k < 4; ++k) {
+        RCHK(h->alloc(&h->cfN[k], N));
+        RCHK(h->alloc(&h->cfO[k], N));
+      }
+    }
     double** fields[] = {&h->dpN, &h->dmN, &h->epN, &h->emN, &h->epNs, &h->emNs,
                          &h->dpO, &h->dmO, &h->epOs, &h->emOs, &h->tmp, &h->bwork,
                          &h->hu, &h->hv, &h->hx_out, &h->u_last};
@@ -760,6 +787,12 @@ int fde_set_coefficients(fde_handle* h, int which, const double* dp, const doubl
     CCHK(cudaMemcpyAsync(h->emN, em, N * 8, cudaMemcpyDeviceToDevice, h->st));
     LCHK((launch_convert<double, double>(N, ep, h->sigma, h->epNs, h->st)));
     LCHK((launch_convert<double, double>(N, em, h->sigma, h->emNs, h->st)));
+    if (h->p.outer == FDE_OUTER_DF32) {
+      LCHK(launch_to_df(N, dp, 1.0, h->cfN[0], h->st));
+      LCHK(launch_to_df(N, dm, 1.0, h->cfN[1], h->st));
+      LCHK(launch_to_df(N, ep, h->sigma, h->cfN[2], h->st));
+      LCHK(launch_to_df(N, em, h->sigma, h->cfN[3], h->st));
+    }
     h->have_new = true;
     if (h->mg) RCHK(h->mg->setup(h));
   } else {
@@ -767,6 +800,12 @@ int fde_set_coefficients(fde_handle* h, int which, const double* dp, const doubl
     CCHK(cudaMemcpyAsync(h->dmO, dm, N * 8, cudaMemcpyDeviceToDevice, h->st));
     LCHK((launch_convert<double, double>(N, ep, h->sigma, h->epOs, h->st)));
     LCHK((launch_convert<double, double>(N, em, h->sigma, h->emOs, h->st)));
+    if (h->p.outer == FDE_OUTER_DF32) {
+      LCHK(launch_to_df(N, dp, 1.0, h->cfO[0], h->st));
+      LCHK(launch_to_df(N, dm, 1.0, h->cfO[1], h->st));
+      LCHK(launch_to_df(N, ep, h->sigma, h->cfO[2], h->st));
+      LCHK(launch_to_df(N, em, h->sigma, h->cfO[3], h->st));
+    }
     h->have_old = true;
   }
   return FDE_OK;

@@ -2,6 +2,7 @@
 // operators, coarsest-grid direct solve).  Grid functions are row-major
 // n2 x n1 arrays (x fastest).
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace fde {
 
@@ -149,6 +150,20 @@ __global__ void convert_kernel(size_t N, const TI* __restrict__ X, double scale,
 template <typename TI, typename TO>
 cudaError_t launch_convert(size_t N, const TI* X, double scale, TO* Y, cudaStream_t st) {
   convert_kernel<TI, TO><<<grid_for(N, 256), 256, 0, st>>>(N, X, scale, Y);
+  return cudaGetLastError();
+}
+
+__global__ void to_df_kernel(size_t N, const double* __restrict__ X, double scale, df* Y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double v = scale * X[i];
+    const float h = __double2float_rn(v);
+    Y[i] = fast_two_sum(h, __double2float_rn(v - (double)h));
+  }
+}
+
+cudaError_t launch_to_df(size_t N, const double* X, double scale, df* Y, cudaStream_t st) {
+  to_df_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, X, scale, Y);
   return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@
 //    -- no bit-reversal permutation is ever performed.
 //  * direct_pass: plain O(n^2) summation for small levels.
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace fde {
 
@@ -25,59 +26,116 @@ template <typename R>
 __device__ __forceinline__ cx<R> to_cx(cx<double> z) {
   return {R(z.re), R(z.im)};
 }
+template <typename R, typename C>
+__device__ __forceinline__ R coef(const C* p, size_t i) {
+  return p ? R(p[i]) : R(1);
+}
+template <>
+__device__ __forceinline__ df coef<df, df>(const df* p, size_t i) {
+  return p ? p[i] : df(1.f, 0.f);
+}
 
-// forward transform, in place, natural order -> bit-reversed order
+// Twiddle table layout: for a butterfly of span `half` (sub-transform length
+// 2 half) the factors omega_{2 half}^pos, pos < half, are stored contiguously
+// at T[half - 1 + pos] (L - 1 entries in all), so the threads of a warp,
+// which handle consecutive `pos`, read consecutive words.
+
+// forward transform, in place, natural order -> bit-reversed order.
+// Radix-2^2: two radix-2 decimation-in-frequency stages per pass through
+// shared memory (one extra radix-2 stage first when log2 L is odd).
 template <typename R>
 __device__ void fft_dif(cx<R>* a, int logL, const cx<R>* __restrict__ tw) {
-  const int nb = 1 << (logL - 1);
-  for (int s = 0; s < logL; ++s) {
-    const int lh = logL - 1 - s;  // log2 of the butterfly span
-    const int half = 1 << lh;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const int pos = b & (half - 1);
-      const int i0 = ((b >> lh) << (lh + 1)) + pos;
-      const cx<R> u = a[i0], v = a[i0 + half];
-      a[i0] = cadd(u, v);
-      a[i0 + half] = cmul(csub(u, v), tw[pos << s]);
+  const int L = 1 << logL;
+  int s = 0;
+  if (logL & 1) {  // span L/2
+    const int half = L >> 1;
+    for (int b = threadIdx.x; b < half; b += blockDim.x) {
+      const cx<R> u = a[b], v = a[b + half];
+      a[b] = cadd(u, v);
+      a[b + half] = cmul(csub(u, v), tw[half - 1 + b]);
+    }
+    __syncthreads();
+    s = 1;
+  }
+  for (; s < logL; s += 2) {
+    const int h1 = L >> (s + 1), h2 = h1 >> 1;  // spans of the two stages
+    const int lh2 = logL - s - 2;
+    for (int g = threadIdx.x; g < (L >> 2); g += blockDim.x) {
+      const int pos = g & (h2 - 1);
+      const int i0 = ((g >> lh2) << (lh2 + 2)) + pos;
+      cx<R> a0 = a[i0], a1 = a[i0 + h2], a2 = a[i0 + h1], a3 = a[i0 + h1 + h2];
+      const cx<R> w1a = tw[h1 - 1 + pos], w1b = tw[h1 - 1 + pos + h2], w2 = tw[h2 - 1 + pos];
+      cx<R> b0 = cadd(a0, a2), b2 = cmul(csub(a0, a2), w1a);
+      cx<R> b1 = cadd(a1, a3), b3 = cmul(csub(a1, a3), w1b);
+      a[i0] = cadd(b0, b1);
+      a[i0 + h2] = cmul(csub(b0, b1), w2);
+      a[i0 + h1] = cadd(b2, b3);
+      a[i0 + h1 + h2] = cmul(csub(b2, b3), w2);
     }
     __syncthreads();
   }
 }
 
 // inverse transform (unnormalised) of two arrays, in place,
-// bit-reversed order -> natural order
+// bit-reversed order -> natural order; radix-2^2 decimation in time (one
+// extra radix-2 stage last when log2 L is odd)
+template <typename R>
+__device__ __forceinline__ void dit4(cx<R>* a, int i0, int h, cx<R> w1, cx<R> w2, cx<R> w3) {
+  const cx<R> a0 = a[i0], a1 = a[i0 + h], a2 = a[i0 + 2 * h], a3 = a[i0 + 3 * h];
+  cx<R> t = cmulc(a1, w1);
+  const cx<R> b0 = cadd(a0, t), b1 = csub(a0, t);
+  t = cmulc(a3, w1);
+  const cx<R> b2 = cadd(a2, t), b3 = csub(a2, t);
+  t = cmulc(b2, w2);
+  a[i0] = cadd(b0, t);
+  a[i0 + 2 * h] = csub(b0, t);
+  t = cmulc(b3, w3);
+  a[i0 + h] = cadd(b1, t);
+  a[i0 + 3 * h] = csub(b1, t);
+}
+
 template <typename R>
 __device__ void fft_dit_inv2(cx<R>* a, cx<R>* c, int logL, const cx<R>* __restrict__ tw) {
-  const int nb = 1 << (logL - 1);
-  for (int s = 0; s < logL; ++s) {
-    const int half = 1 << s;
-    const int tsh = logL - 1 - s;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const int pos = b & (half - 1);
-      const int i0 = ((b >> s) << (s + 1)) + pos;
-      const cx<R> w = tw[pos << tsh];
-      cx<R> t = cmulc(a[i0 + half], w);
-      cx<R> u = a[i0];
-      a[i0] = cadd(u, t);
-      a[i0 + half] = csub(u, t);
-      t = cmulc(c[i0 + half], w);
-      u = c[i0];
-      c[i0] = cadd(u, t);
-      c[i0 + half] = csub(u, t);
+  const int L = 1 << logL;
+  int s = 0;
+  for (; s + 1 < logL; s += 2) {
+    const int h = 1 << s;  // spans h and 2h
+    for (int g = threadIdx.x; g < (L >> 2); g += blockDim.x) {
+      const int pos = g & (h - 1);
+      const int i0 = ((g >> s) << (s + 2)) + pos;
+      const cx<R> w1 = tw[h - 1 + pos], w2 = tw[2 * h - 1 + pos], w3 = tw[2 * h - 1 + pos + h];
+      dit4(a, i0, h, w1, w2, w3);
+      dit4(c, i0, h, w1, w2, w3);
+    }
+    __syncthreads();
+  }
+  if (s < logL) {  // last radix-2 stage, span L/2
+    const int half = L >> 1;
+    for (int b = threadIdx.x; b < half; b += blockDim.x) {
+      const cx<R> w = tw[half - 1 + b];
+      cx<R> t = cmulc(a[b + half], w);
+      cx<R> u = a[b];
+      a[b] = cadd(u, t);
+      a[b + half] = csub(u, t);
+      t = cmulc(c[b + half], w);
+      u = c[b];
+      c[b] = cadd(u, t);
+      c[b + half] = csub(u, t);
     }
     __syncthreads();
   }
 }
 
-template <typename T, typename R>
+template <typename T, typename R, typename C>
 __global__ void __launch_bounds__(512)
 fft_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int logL,
                 const cx<R>* __restrict__ S1, const cx<R>* __restrict__ S2,
-                const cx<R>* __restrict__ tw, const T* __restrict__ cp,
-                const T* __restrict__ cm, const T* __restrict__ M, R cmass, T* Y,
+                const cx<R>* __restrict__ tw, const C* __restrict__ cp,
+                const C* __restrict__ cm, const T* __restrict__ M, double cmass_d, T* Y,
                 int accumulate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 1 << logL;
+  const R cmass = R(cmass_d);
   cx<R>* a = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* c = a + L;
   const int npairs = (nvec + 1) >> 1;
@@ -87,7 +145,7 @@ fft_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int lo
     const size_t oa = (size_t)va * vs, ob = oa + vs;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
       cx<R> z = {R(0), R(0)};
-      if (i < n) {
+      if (i < n) {  // x_v[i] packed as re (vector va) + i im (vector va + 1)
         z.re = R(X[oa + (size_t)i * es]);
         if (hasb) z.im = R(X[ob + (size_t)i * es]);
       }
@@ -104,13 +162,13 @@ fft_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int lo
     fft_dit_inv2(a, c, logL, tw);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const size_t ia = oa + (size_t)i * es;
-      R y = a[i].re * (cp ? R(cp[ia]) : R(1)) + c[i].re * (cm ? R(cm[ia]) : R(1));
+      R y = a[i].re * coef<R, C>(cp, ia) + c[i].re * coef<R, C>(cm, ia);
       if (M) y += cmass * R(M[ia]);
       if (accumulate) y += R(Y[ia]);
       Y[ia] = T(y);
       if (hasb) {
         const size_t ib = ob + (size_t)i * es;
-        R yb = a[i].im * (cp ? R(cp[ib]) : R(1)) + c[i].im * (cm ? R(cm[ib]) : R(1));
+        R yb = a[i].im * coef<R, C>(cp, ib) + c[i].im * coef<R, C>(cm, ib);
         if (M) yb += cmass * R(M[ib]);
         if (accumulate) yb += R(Y[ib]);
         Y[ib] = T(yb);
@@ -120,16 +178,16 @@ fft_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int lo
   }
 }
 
-template <typename T, typename R>
+template <typename T, typename R, typename C>
 cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int logL,
-                            const cx<R>* S1, const cx<R>* S2, const cx<R>* tw, const T* cp,
-                            const T* cm, const T* M, double cmass, T* Y, int accumulate,
+                            const cx<R>* S1, const cx<R>* S2, const cx<R>* tw, const C* cp,
+                            const C* cm, const T* M, double cmass, T* Y, int accumulate,
                             cudaStream_t st) {
   const int L = 1 << logL;
   const size_t smem = 2 * (size_t)L * sizeof(cx<R>);
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, R>,
+    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, R, C>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
@@ -139,8 +197,8 @@ cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int log
   const int per_sm = (int)((227 * 1024) / (smem + 1024));
   int grid = 152 * (per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm));
   if (grid > npairs) grid = npairs;
-  fft_pass_kernel<T, R><<<grid, threads, smem, st>>>(X, es, vs, nvec, n, logL, S1, S2, tw, cp, cm,
-                                                     M, R(cmass), Y, accumulate);
+  fft_pass_kernel<T, R, C><<<grid, threads, smem, st>>>(X, es, vs, nvec, n, logL, S1, S2, tw, cp,
+                                                        cm, M, cmass, Y, accumulate);
   return cudaGetLastError();
 }
 
@@ -152,9 +210,12 @@ __global__ void build_spectra_kernel(const double* __restrict__ t, int n, int lo
   const int L = 1 << logL;
   cx<double>* a = reinterpret_cast<cx<double>*>(smem_raw);
   cx<double>* tw = a + L;
-  for (int k = threadIdx.x; k < L / 2; k += blockDim.x) {
+  // tw[half - 1 + pos] = exp(-2 pi i pos / (2 half)), half = 1, 2, 4, ..., L/2
+  for (int k = threadIdx.x; k < L - 1; k += blockDim.x) {
+    const int lh = 31 - __clz(k + 1);  // half = 2^lh <= k + 1 < 2 half
+    const int half = 1 << lh, pos = k + 1 - half;
     double s, c;
-    sincospi(-2.0 * (double)k / (double)L, &s, &c);
+    sincospi(-(double)pos / (double)half, &s, &c);
     tw[k] = {c, s};
     if (twout) twout[k] = to_cx<R>(tw[k]);
   }
@@ -186,7 +247,7 @@ template <typename R>
 cudaError_t launch_build_spectra(const double* t, int n, int logL, double scale, cx<R>* S1,
                                  cx<R>* S2, cx<R>* tw, cudaStream_t st) {
   const int L = 1 << logL;
-  const size_t smem = (size_t)L * sizeof(cx<double>) + (size_t)(L / 2) * sizeof(cx<double>);
+  const size_t smem = (size_t)(2 * L) * sizeof(cx<double>);
   cudaError_t e = cudaFuncSetAttribute(build_spectra_kernel<R>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
@@ -240,16 +301,22 @@ cudaError_t launch_direct_pass(const T* X, int es, int vs, int nvec, int n, cons
 }
 
 // ---------------------------------------------------------------- instantiations
-template cudaError_t launch_fft_pass<double, double>(const double*, int, int, int, int, int,
-                                                     const cx<double>*, const cx<double>*,
-                                                     const cx<double>*, const double*,
-                                                     const double*, const double*, double,
-                                                     double*, int, cudaStream_t);
-template cudaError_t launch_fft_pass<float, float>(const float*, int, int, int, int, int,
-                                                   const cx<float>*, const cx<float>*,
-                                                   const cx<float>*, const float*, const float*,
-                                                   const float*, double, float*, int,
-                                                   cudaStream_t);
+template cudaError_t launch_fft_pass<double, double, double>(
+    const double*, int, int, int, int, int, const cx<double>*, const cx<double>*,
+    const cx<double>*, const double*, const double*, const double*, double, double*, int,
+    cudaStream_t);
+template cudaError_t launch_fft_pass<float, float, float>(const float*, int, int, int, int, int,
+                                                          const cx<float>*, const cx<float>*,
+                                                          const cx<float>*, const float*,
+                                                          const float*, const float*, double,
+                                                          float*, int, cudaStream_t);
+template cudaError_t launch_fft_pass<double, df, df>(const double*, int, int, int, int, int,
+                                                     const cx<df>*, const cx<df>*,
+                                                     const cx<df>*, const df*, const df*,
+                                                     const double*, double, double*, int,
+                                                     cudaStream_t);
+template cudaError_t launch_build_spectra<df>(const double*, int, int, double, cx<df>*, cx<df>*,
+                                              cx<df>*, cudaStream_t);
 template cudaError_t launch_build_spectra<double>(const double*, int, int, double, cx<double>*,
                                                   cx<double>*, cx<double>*, cudaStream_t);
 template cudaError_t launch_build_spectra<float>(const double*, int, int, double, cx<float>*,

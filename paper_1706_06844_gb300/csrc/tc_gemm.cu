@@ -129,6 +129,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -300,34 +316,53 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapXa,
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int g = warp & 3;  // TMEM lane group this warp may access
-    const int r = g * 32 + lane;
-    const int row = j0 + r;
-    const bool ok = mbar_wait(smem_u32(accbar), 0, abort_flag);
+    // Warp w may read TMEM lanes 32 (w % 4) .. +31, i.e. output rows
+    // 32 g .. 32 g + 31.  Per 32-column chunk the four accumulators go through
+    // a padded per-warp staging area (the operand buffers are idle once the
+    // accumulator barrier has fired) so that afterwards lane = column and every
+    // global load/store of the epilogue is one 128-byte row segment.
+    const int g = warp & 3;
+    // one lane per warp waits for the accumulators (backing off between polls so
+    // the waiting warps do not compete with TMA completions on the barrier unit)
+    int okw = 1;
+    if (lane == 0) {
+      const uint64_t t0 = global_ns();
+      while (!mbar_try(smem_u32(accbar), 0)) {
+        if (*abort_flag) { okw = 0; break; }
+        if (global_ns() - t0 > 1000000000ull) { *abort_flag = 1; okw = 0; break; }
+        __nanosleep(256);
+      }
+    }
+    const bool ok = __shfl_sync(0xffffffffu, okw, 0) != 0;
     fence_after();
     if (ok && !*abort_flag) {
+      float* stg = reinterpret_cast<float*>(tilesA) + (warp - 2) * (4 * 32 * 33);
       const uint32_t tl = tmem + ((uint32_t)(g * 32) << 16);
-      for (int cb = 0; cb < BN; cb += 16) {
-        float a0[16], a1[16], a2[16], a3[16];
-        tmem_ld16(tl + 0 * BN + cb, a0);
-        tmem_ld16(tl + 1 * BN + cb, a1);
-        tmem_ld16(tl + 2 * BN + cb, a2);
-        tmem_ld16(tl + 3 * BN + cb, a3);
-        tmem_wait_ld();
-        if (row < kp.n2) {
-          const size_t rb = (size_t)row * kp.n1;
+      for (int cb = 0; cb < BN; cb += 32) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int col = i0 + cb + q;
-            if (col < kp.n1) {
-              const size_t idx = rb + col;
-              float v = kp.inv_scale * (kp.dp[idx] * a0[q] + kp.dm[idx] * a1[q] +
-                                        kp.ep[idx] * a2[q] + kp.em[idx] * a3[q]);
-              if (kp.M) v += kp.cm * kp.M[idx];
-              kp.kx[idx] = v;
-            }
+        for (int a = 0; a < 4; ++a) {
+          float v[32];
+          tmem_ld32(tl + a * BN + cb, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 32; ++q) stg[(a * 32 + lane) * 33 + q] = v[q];
+        }
+        __syncwarp();
+        const int col = i0 + cb + lane;
+        if (col < kp.n1) {
+          for (int rr = 0; rr < 32; ++rr) {
+            const int row = j0 + g * 32 + rr;
+            if (row >= kp.n2) break;
+            const size_t idx = (size_t)row * kp.n1 + col;
+            float v = kp.inv_scale * (kp.dp[idx] * stg[(0 * 32 + rr) * 33 + lane] +
+                                      kp.dm[idx] * stg[(1 * 32 + rr) * 33 + lane] +
+                                      kp.ep[idx] * stg[(2 * 32 + rr) * 33 + lane] +
+                                      kp.em[idx] * stg[(3 * 32 + rr) * 33 + lane]);
+            if (kp.M) v += kp.cm * kp.M[idx];
+            kp.kx[idx] = v;
           }
         }
+        __syncwarp();
       }
     }
   }
