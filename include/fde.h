@@ -189,6 +189,25 @@ int fde_profile_query(fde_handle* h, int kclass, long long* launches, double* ms
 /* Total kernels this handle has launched. */
 long long fde_launch_count(const fde_handle* h);
 
+/* y = M x (Eq. M) with the given coefficients (device arrays d+, d-, e+, e-,
+ * n2 x n1, as for fde_set_coefficients) in FP64, WITHOUT a handle and WITHOUT
+ * allocating device memory: for callers that cannot allocate GPU memory (the
+ * device heap is owned by another runtime's fixed pool or allocator, or the
+ * process must not grow its device footprint), and who therefore cannot call
+ * fde_create.  The paper has no counterpart; it is a deployment convenience.
+ * Only alpha, beta, qx, qy, a1, b1, a2, b2, n1, n2 and dt of *p are read.
+ * Grids larger than 2048 points on either axis are rejected (FDE_ERR_ARG):
+ * the working data (weights, spectra, twiddles, about 450 KB) lives in one
+ * fixed device array that every GPU loading the library holds until exit.
+ * The first call on a device looks that array up (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.  Each
+ * call rewrites the array before using it; calls that overlap on the GPU
+ * (other streams or host threads) race on it and must be serialised by the
+ * caller.  Work is enqueued on `stream`; errors via fde_last_error(NULL). */
+int fde_apply_noalloc(const fde_params* p, const double* dp, const double* dm,
+                      const double* ep, const double* em, const double* x, double* y,
+                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

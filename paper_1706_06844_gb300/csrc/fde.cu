@@ -36,6 +36,11 @@ struct ProfEvent {
 
 }  // namespace
 
+namespace fde {
+// message returned by fde_last_error(NULL) for calls without a handle
+void set_global_error(const char* msg) { g_create_error = msg; }
+}  // namespace fde
+
 struct MGBase;
 
 struct fde_handle {

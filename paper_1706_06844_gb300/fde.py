@@ -66,6 +66,8 @@ SIGNATURES = {
     "fde_profile_query": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_double)]),
     "fde_launch_count": (ctypes.c_longlong, [_VP]),
+    "fde_apply_noalloc": (ctypes.c_int, [ctypes.POINTER(fde_params), _DP, _DP, _DP, _DP, _DP,
+                                         _DP, _VP]),
 }
 
 
@@ -213,6 +215,14 @@ def fde_profile_query(h, kclass):
 
 def fde_launch_count(h):
     return lib().fde_launch_count(h)
+
+
+def fde_apply_noalloc(params, dp, dm, ep, em, x, y, stream=0):
+    rc = lib().fde_apply_noalloc(ctypes.byref(params), _ptr(dp), _ptr(dm), _ptr(ep), _ptr(em),
+                                 _ptr(x), _ptr(y), ctypes.c_void_p(stream))
+    if rc != FDE_OK:
+        raise FDEError(rc, fde_last_error(None))
+    return rc
 
 
 # ---------------------------------------------------------------- convenience
