@@ -49,7 +49,8 @@ def _peaks():
 
 # FP64 issue rate of GB300: 2 FMA per SM per clock (nominal 1.25 TFLOP/s)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # = 1258.6 GFLOP/s at the 2070 MHz maximum clock
-FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07  # = 80 548 GFLOP/s
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07  # = 80 548 GFLOP/s (FMA = 2 flops)
+FP32_ISSUE_TOPS = 152 * 128 * 2.07 / 1e3  # = 40.3 T FP32 instructions/s
 
 
 def problem():
@@ -205,7 +206,24 @@ def e2e_steps(w, steps):
     return steps / dt, 2 * nbytes, nbytes
 
 
-def roofline(w, steps):
+def fft_pass_work(n, outer):
+    """Algorithmic work of one outer-apply pass (all rows or all columns): per
+    pair of grid vectors one forward and two inverse complex FFTs of length L
+    (radix-2^2: per group of 4 points 3 complex multiplies and 8 complex
+    additions per two stages) and two complex spectral products per point.
+    FP64: real flops (complex multiply 6, complex add 2).  Double-float: the
+    FP32 operations of the double-float formulas used (complex multiply as two
+    fused two-product dot products, 2 x 19; complex add as two double-float
+    additions, 2 x 11), each operation one FP32 instruction."""
+    L = 1 << (2 * n - 2).bit_length()
+    logL = L.bit_length() - 1
+    cm, ca = (6, 2) if outer == "fp64" else (38, 22)
+    groups = (logL // 2) * (L // 4)
+    fft = groups * (3 * cm + 8 * ca) + (L // 2 if logL % 2 else 0) * (cm + 2 * ca)
+    return ((n + 1) // 2) * (3 * fft + 2 * cm * L)
+
+
+def roofline(w, steps, outer):
     """Dominant kernel: the FP64-accurate outer Toeplitz apply (one launch = one
     FFT pass over all rows or all columns).  Timed with CUDA events on the
     library's stream over `steps` further time steps."""
@@ -219,22 +237,23 @@ def roofline(w, steps):
                     (fde.FDE_KCLASS_KRYLOV, "krylov"), (fde.FDE_KCLASS_MG_OTHER, "mg_other")]:
         res[name] = fde.fde_profile_query(w.h, k)
     fde.fde_profile_enable(w.h, 0)
-    n, L = N_GRID, 4096
-    logL = 12
-    # algorithmic FP64 flops of one pass: per pair of vectors one forward and two
-    # inverse complex FFTs of length L (5 L log2 L each) and two complex spectral
-    # products (6 flops per point each); n vectors per pass
-    flops_pass = (n / 2) * (3 * 5 * L * logL + 2 * 6 * L)
+    work = fft_pass_work(N_GRID, outer)
     launches, ms = res["outer_apply"]
     avg_s = ms / max(launches, 1) * 1e-3
-    achieved = flops_pass / avg_s / 1e9
+    achieved = work / avg_s / 1e12
+    if outer == "fp64":
+        peak, unit = FP64_PEAK_GFLOPS / 1e3, "TFLOP/s"
+        kern = "fft_pass_kernel<double,double,double> (outer FP64 Toeplitz apply)"
+        src = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"
+    else:
+        peak, unit = FP32_ISSUE_TOPS, "T FP32-op/s"
+        kern = "fft_pass_kernel<double,df,df> (outer double-float Toeplitz apply)"
+        src = "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (one instruction = one op)"
     total_ms = sum(v[1] for v in res.values())
-    return {"bound": "alu", "kernel": "fft_pass_kernel<double,double> (outer FP64 Toeplitz apply)",
-            "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
-            "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
-            "traffic": None, "algorithmic_flops_per_launch": flops_pass,
-            "launches": launches, "avg_launch_ms": round(avg_s * 1e3, 4),
+    return {"bound": "alu", "kernel": kern, "achieved": round(achieved, 3), "peak": round(peak, 2),
+            "unit": unit, "frac": round(achieved / peak, 4), "peak_source": src,
+            "traffic": None, "work_per_launch": work, "launches": launches,
+            "avg_launch_ms": round(avg_s * 1e3, 4),
             "share_of_profiled_time": {k: round(v[1] / total_ms, 4) for k, v in res.items()}}
 
 
@@ -332,7 +351,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--precision", default="fp16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--outer", default="df32", choices=["df32", "fp64"])
     args = ap.parse_args()
     if args.kernel:
         kernel_micro(args.kernel, args.reps)
@@ -358,7 +378,8 @@ def main():
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     mixed = {"bf16": fde.FDE_PREC_BF16, "fp16": fde.FDE_PREC_FP16,
              "fp32": fde.FDE_PREC_FP32}[args.precision]
-    w = Workload(mixed)
+    outer = fde.FDE_OUTER_DF32 if args.outer == "df32" else fde.FDE_OUTER_FP64
+    w = Workload(mixed, outer=outer)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         ms, wall, its, launches = time_steps(w, args.steps, args.warmup, dist)
     if dist:
@@ -367,7 +388,7 @@ def main():
         ms = float(t.item())
     value = world * args.steps / (ms * 1e-3)
     e2e_v, h2d, d2h = e2e_steps(w, max(2, min(args.steps, 4)))
-    roof = roofline(w, 2)
+    roof = roofline(w, 2, args.outer)
     w.close()
     fp64 = None
     if not args.no_fp64:
@@ -392,8 +413,8 @@ def main():
                 "dtype": f"f64 Krylov + {args.precision} V-cycle products", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": N_GRID, "restart": RESTART, "rtol": RTOL,
                            "precond": "MG_SG",
-                           "precision": f"{args.precision} tensor-core V-cycle products (FP32 "
-                                        "vectors), FP64 FFT outer apply",
+                           "precision": f"{args.precision} V-cycle products (FP32 vectors), "
+                                        f"{args.outer} FFT outer apply",
                            "l2": "inputs larger than L2 (Krylov basis 31 x 33.5 MB)",
                            "parallelism": f"replicas x{world}"},
                 "iterations_per_step": its, "wall_s": round(wall, 3),

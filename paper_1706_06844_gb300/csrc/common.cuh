@@ -75,6 +75,10 @@ template <typename T>
 cudaError_t launch_level_epilogue(int mode, size_t N, const T* KX, const T* B, const T* X,
                                   const T* W, T* Y, cudaStream_t st);
 
+// out[c][r] = in[r][c] (in: rows x cols, out: cols x rows); add = 1: out[c][r] += in[r][c]
+template <typename T>
+cudaError_t launch_transpose(const T* in, int rows, int cols, T* out, int add, cudaStream_t st);
+
 // Y = W * B (Jacobi sweep from a zero guess)
 template <typename T>
 cudaError_t launch_mul(size_t N, const T* W, const T* B, T* Y, cudaStream_t st);

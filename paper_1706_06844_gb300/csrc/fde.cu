@@ -65,6 +65,10 @@ struct fde_handle {
   cx<df> *S1xd = nullptr, *S2xd = nullptr, *S1yd = nullptr, *S2yd = nullptr, *twxd = nullptr,
          *twyd = nullptr;
   df *cfN[4] = {nullptr, nullptr, nullptr, nullptr}, *cfO[4] = {nullptr, nullptr, nullptr, nullptr};
+  // transposed (n1 x n2) copies of sigma e+- for the column pass: FP64 and double-float
+  double *epNsT = nullptr, *emNsT = nullptr, *epOsT = nullptr, *emOsT = nullptr;
+  df *cfNT[2] = {nullptr, nullptr}, *cfOT[2] = {nullptr, nullptr};
+  double *xT = nullptr, *yT = nullptr;  // transposed operand / result of the column pass
   bool have_new = false, have_old = false;
 
   std::unique_ptr<MGBase> mg;
@@ -183,6 +187,7 @@ struct MG : MGBase {
     T *txT = nullptr, *tyT = nullptr;
     T *dp, *dm, *ep, *em, *W;
     T *x, *b, *kx, *xby = nullptr, *xbx = nullptr, *mass = nullptr;
+    T *epT = nullptr, *emT = nullptr, *xT = nullptr, *yT = nullptr;  // column pass (FFT levels)
     tc::ToeplitzGemmLevel gemm;
   };
   std::vector<Lv> lv;
@@ -266,6 +271,10 @@ struct MG : MGBase {
         RCHK(h->alloc(&L.S1x, (size_t)1 << L.logLx));
         RCHK(h->alloc(&L.S2x, (size_t)1 << L.logLx));
         RCHK(h->alloc(&L.twx, (size_t)1 << L.logLx));
+        RCHK(h->alloc(&L.epT, L.N));
+        RCHK(h->alloc(&L.emT, L.N));
+        RCHK(h->alloc(&L.xT, L.N));
+        RCHK(h->alloc(&L.yT, L.N));
         RCHK(h->alloc(&L.S1y, (size_t)1 << L.logLy));
         RCHK(h->alloc(&L.S2y, (size_t)1 << L.logLy));
         RCHK(h->alloc(&L.twy, (size_t)1 << L.logLy));
@@ -309,6 +318,8 @@ struct MG : MGBase {
                                   h->sigma, h->c, L.bx0, L.by0, L.tx, L.ty, p.omega, L.dp, L.dm,
                                   L.ep, L.em, L.W, st));
       if (L.path == FDE_PATH_FFT && l + 1 < lv.size()) {
+        LCHK(launch_transpose<T>(L.ep, L.n2, L.n1, L.epT, 0, st));
+        LCHK(launch_transpose<T>(L.em, L.n2, L.n1, L.emT, 0, st));
         LCHK(launch_build_spectra<T>(L.tx, L.n1, L.logLx, 1.0, L.S1x, L.S2x, L.twx, st));
         LCHK(launch_build_spectra<T>(L.ty, L.n2, L.logLy, 1.0, L.S1y, L.S2y, L.twy, st));
       } else if (L.path == FDE_PATH_DIRECT && l + 1 < lv.size()) {
@@ -353,8 +364,10 @@ struct MG : MGBase {
     if (L.path == FDE_PATH_FFT) {
       LCHK((launch_fft_pass<T, T, T>(xin_x, 1, L.n1, L.n2, L.n1, L.logLx, L.S1x, L.S2x, L.twx, L.dp,
                                   L.dm, M, cm, kx, 0, st)));
-      LCHK((launch_fft_pass<T, T, T>(xin_y, L.n1, 1, L.n1, L.n2, L.logLy, L.S1y, L.S2y, L.twy, L.ep,
-                                  L.em, nullptr, 0.0, kx, 1, st)));
+      LCHK(launch_transpose<T>(xin_y, L.n2, L.n1, L.xT, 0, st));
+      LCHK((launch_fft_pass<T, T, T>(L.xT, 1, L.n2, L.n1, L.n2, L.logLy, L.S1y, L.S2y, L.twy,
+                                     L.epT, L.emT, nullptr, 0.0, L.yT, 0, st)));
+      LCHK(launch_transpose<T>(L.yT, L.n1, L.n2, kx, 1, st));
     } else if (L.path == FDE_PATH_DIRECT) {
       LCHK(launch_direct_pass<T>(xin_x, 1, L.n1, L.n2, L.n1, L.txT, L.dp, L.dm, M, cm, kx, 0, st));
       LCHK(launch_direct_pass<T>(xin_y, L.n1, 1, L.n1, L.n2, L.tyT, L.ep, L.em, nullptr, 0.0, kx,
@@ -465,10 +478,14 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
     LCHK((launch_fft_pass<double, df, df>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1xd, h->S2xd,
                                           h->twxd, cf[0], cf[1], x, h->c, y, 0, h->st)));
     h->pend(pi);
+    df* const* cfT = old ? h->cfOT : h->cfNT;
+    LCHK(launch_transpose<double>(x, h->n2, h->n1, h->xT, 0, h->st));
     pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
-    LCHK((launch_fft_pass<double, df, df>(x, h->n1, 1, h->n1, h->n2, h->logLy, h->S1yd, h->S2yd,
-                                          h->twyd, cf[2], cf[3], nullptr, 0.0, y, 1, h->st)));
+    LCHK((launch_fft_pass<double, df, df>(h->xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1yd,
+                                          h->S2yd, h->twyd, cfT[0], cfT[1], nullptr, 0.0, h->yT, 0,
+                                          h->st)));
     h->pend(pi);
+    LCHK(launch_transpose<double>(h->yT, h->n1, h->n2, y, 1, h->st));
     return FDE_OK;
   }
   const double* dp = old ? h->dpO : h->dpN;
@@ -479,10 +496,15 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
   LCHK((launch_fft_pass<double, double, double>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x, h->S2x,
                                         h->twx, dp, dm, x, h->c, y, 0, h->st)));
   h->pend(pi);
+  const double* epT = old ? h->epOsT : h->epNsT;
+  const double* emT = old ? h->emOsT : h->emNsT;
+  LCHK(launch_transpose<double>(x, h->n2, h->n1, h->xT, 0, h->st));
   pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
-  LCHK((launch_fft_pass<double, double, double>(x, h->n1, 1, h->n1, h->n2, h->logLy, h->S1y, h->S2y,
-                                        h->twy, ep, em, nullptr, 0.0, y, 1, h->st)));
+  LCHK((launch_fft_pass<double, double, double>(h->xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1y,
+                                                h->S2y, h->twy, epT, emT, nullptr, 0.0, h->yT, 0,
+                                                h->st)));
   h->pend(pi);
+  LCHK(launch_transpose<double>(h->yT, h->n1, h->n2, y, 1, h->st));
   return FDE_OK;
 }
 
@@ -725,10 +747,15 @@ int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
         RCHK(h->alloc(&h->cfN[k], N));
         RCHK(h->alloc(&h->cfO[k], N));
       }
+      for (int k = 0; k < 2; ++k) {
+        RCHK(h->alloc(&h->cfNT[k], N));
+        RCHK(h->alloc(&h->cfOT[k], N));
+      }
     }
     double** fields[] = {&h->dpN, &h->dmN, &h->epN, &h->emN, &h->epNs, &h->emNs,
                          &h->dpO, &h->dmO, &h->epOs, &h->emOs, &h->tmp, &h->bwork,
-                         &h->hu, &h->hv, &h->hx_out, &h->u_last};
+                         &h->hu, &h->hv, &h->hx_out, &h->u_last, &h->epNsT, &h->emNsT,
+                         &h->epOsT, &h->emOsT, &h->xT, &h->yT};
     for (double** f : fields) RCHK(h->alloc(f, N));
     RCHK(h->alloc(&h->V, N * (size_t)(p.restart + 1)));
     RCHK(h->alloc(&h->Z, N * (size_t)p.restart));
@@ -792,11 +819,15 @@ int fde_set_coefficients(fde_handle* h, int which, const double* dp, const doubl
     CCHK(cudaMemcpyAsync(h->emN, em, N * 8, cudaMemcpyDeviceToDevice, h->st));
     LCHK((launch_convert<double, double>(N, ep, h->sigma, h->epNs, h->st)));
     LCHK((launch_convert<double, double>(N, em, h->sigma, h->emNs, h->st)));
+    LCHK(launch_transpose<double>(h->epNs, h->n2, h->n1, h->epNsT, 0, h->st));
+    LCHK(launch_transpose<double>(h->emNs, h->n2, h->n1, h->emNsT, 0, h->st));
     if (h->p.outer == FDE_OUTER_DF32) {
       LCHK(launch_to_df(N, dp, 1.0, h->cfN[0], h->st));
       LCHK(launch_to_df(N, dm, 1.0, h->cfN[1], h->st));
       LCHK(launch_to_df(N, ep, h->sigma, h->cfN[2], h->st));
       LCHK(launch_to_df(N, em, h->sigma, h->cfN[3], h->st));
+      LCHK(launch_to_df(N, h->epNsT, 1.0, h->cfNT[0], h->st));
+      LCHK(launch_to_df(N, h->emNsT, 1.0, h->cfNT[1], h->st));
     }
     h->have_new = true;
     if (h->mg) RCHK(h->mg->setup(h));
@@ -805,11 +836,15 @@ int fde_set_coefficients(fde_handle* h, int which, const double* dp, const doubl
     CCHK(cudaMemcpyAsync(h->dmO, dm, N * 8, cudaMemcpyDeviceToDevice, h->st));
     LCHK((launch_convert<double, double>(N, ep, h->sigma, h->epOs, h->st)));
     LCHK((launch_convert<double, double>(N, em, h->sigma, h->emOs, h->st)));
+    LCHK(launch_transpose<double>(h->epOs, h->n2, h->n1, h->epOsT, 0, h->st));
+    LCHK(launch_transpose<double>(h->emOs, h->n2, h->n1, h->emOsT, 0, h->st));
     if (h->p.outer == FDE_OUTER_DF32) {
       LCHK(launch_to_df(N, dp, 1.0, h->cfO[0], h->st));
       LCHK(launch_to_df(N, dm, 1.0, h->cfO[1], h->st));
       LCHK(launch_to_df(N, ep, h->sigma, h->cfO[2], h->st));
       LCHK(launch_to_df(N, em, h->sigma, h->cfO[3], h->st));
+      LCHK(launch_to_df(N, h->epOsT, 1.0, h->cfOT[0], h->st));
+      LCHK(launch_to_df(N, h->emOsT, 1.0, h->cfOT[1], h->st));
     }
     h->have_old = true;
   }

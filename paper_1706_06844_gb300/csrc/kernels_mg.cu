@@ -65,6 +65,33 @@ cudaError_t launch_level_epilogue(int mode, size_t N, const T* KX, const T* B, c
   return cudaGetLastError();
 }
 
+// 32 x 32 tiles through shared memory (padded against bank conflicts); both the
+// read of `in` and the write of `out` are row segments
+template <typename T>
+__global__ void transpose_kernel(const T* __restrict__ in, int rows, int cols, T* out, int add) {
+  __shared__ T tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;  // out row c, column r
+    if (r < rows && c < cols) {
+      const size_t o = (size_t)c * rows + r;
+      out[o] = add ? out[o] + tile[threadIdx.x][k] : tile[threadIdx.x][k];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_transpose(const T* in, int rows, int cols, T* out, int add, cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+  transpose_kernel<T><<<grid, block, 0, st>>>(in, rows, cols, out, add);
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void mul_kernel(size_t N, const T* __restrict__ W, const T* __restrict__ B, T* Y) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
@@ -442,9 +469,11 @@ cudaError_t launch_coarse_solve(const double* inv, int N, const T* b, T* x, cuda
                                               const double*, int, int, int, int, double, double,  \
                                               double, double, const double*, const double*,       \
                                               double, T*, T*, T*, T*, T*, cudaStream_t);          \
-  template cudaError_t launch_coarse_solve<T>(const double*, int, const T*, T*, cudaStream_t);
+  template cudaError_t launch_coarse_solve<T>(const double*, int, const T*, T*, cudaStream_t); \
+  template cudaError_t launch_transpose<T>(const T*, int, int, T*, int, cudaStream_t);
 INST_T(double)
 INST_T(float)
+template cudaError_t launch_transpose<df>(const df*, int, int, df*, int, cudaStream_t);
 template cudaError_t launch_convert<double, float>(size_t, const double*, double, float*,
                                                    cudaStream_t);
 template cudaError_t launch_convert<float, double>(size_t, const float*, double, double*,

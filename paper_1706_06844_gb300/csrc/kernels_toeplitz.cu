@@ -39,90 +39,105 @@ __device__ __forceinline__ df coef<df, df>(const df* p, size_t i) {
 // 2 half) the factors omega_{2 half}^pos, pos < half, are stored contiguously
 // at T[half - 1 + pos] (L - 1 entries in all), so the threads of a warp,
 // which handle consecutive `pos`, read consecutive words.
+//
+// Shared-memory layout: element i lives at pad(i) = i + i/16, so that the
+// stride-16 accesses of the last fused pass fall into different banks.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int L) { return L + (L >> 4); }
 
-// forward transform, in place, natural order -> bit-reversed order.
-// Radix-2^2: two radix-2 decimation-in-frequency stages per pass through
-// shared memory (one extra radix-2 stage first when log2 L is odd).
+// One fused decimation-in-frequency pass: stages s .. s+q-1 (Q = 2^q points per
+// thread group, held in registers).  Group g covers the points
+// i0 + m h, m < Q, with h = L >> (s+q) the span of the last stage.
+template <int Q, typename R>
+__device__ __forceinline__ void dif_group(cx<R>* a, int i0, int h, int pos,
+                                          const cx<R>* __restrict__ tw) {
+  cx<R> v[Q];
+#pragma unroll
+  for (int m = 0; m < Q; ++m) v[m] = a[pad(i0 + m * h)];
+#pragma unroll
+  for (int sm = Q / 2; sm >= 1; sm >>= 1) {  // span in units of h
+    const int span = sm * h;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      if (m & sm) continue;
+      const cx<R> w = tw[span - 1 + pos + (m & (sm - 1)) * h];
+      const cx<R> u = v[m], x = v[m + sm];
+      v[m] = cadd(u, x);
+      v[m + sm] = cmul(csub(u, x), w);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < Q; ++m) a[pad(i0 + m * h)] = v[m];
+}
+
+// One fused decimation-in-time inverse pass: stages s .. s+q-1 (spans h .. 2^(q-1) h,
+// h = 2^s), conjugated twiddles.
+template <int Q, typename R>
+__device__ __forceinline__ void dit_group(cx<R>* a, int i0, int h, int pos,
+                                          const cx<R>* __restrict__ tw) {
+  cx<R> v[Q];
+#pragma unroll
+  for (int m = 0; m < Q; ++m) v[m] = a[pad(i0 + m * h)];
+#pragma unroll
+  for (int sm = 1; sm < Q; sm <<= 1) {
+    const int span = sm * h;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      if (m & sm) continue;
+      const cx<R> w = tw[span - 1 + pos + (m & (sm - 1)) * h];
+      const cx<R> t = cmulc(v[m + sm], w);
+      const cx<R> u = v[m];
+      v[m] = cadd(u, t);
+      v[m + sm] = csub(u, t);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < Q; ++m) a[pad(i0 + m * h)] = v[m];
+}
+
+// forward transform, in place, natural order -> bit-reversed order
 template <typename R>
 __device__ void fft_dif(cx<R>* a, int logL, const cx<R>* __restrict__ tw) {
-  const int L = 1 << logL;
   int s = 0;
-  if (logL & 1) {  // span L/2
-    const int half = L >> 1;
-    for (int b = threadIdx.x; b < half; b += blockDim.x) {
-      const cx<R> u = a[b], v = a[b + half];
-      a[b] = cadd(u, v);
-      a[b + half] = cmul(csub(u, v), tw[half - 1 + b]);
+  while (s < logL) {
+    const int rem = logL - s;
+    const int q = rem >= 4 ? 4 : (rem >= 2 ? 2 : 1);
+    const int lh = logL - s - q;  // log2 h
+    const int h = 1 << lh;
+    const int ngroups = 1 << (logL - q);
+    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+      const int pos = g & (h - 1);
+      const int i0 = ((g >> lh) << (lh + q)) + pos;
+      if (q == 4) dif_group<16>(a, i0, h, pos, tw);
+      else if (q == 2) dif_group<4>(a, i0, h, pos, tw);
+      else dif_group<2>(a, i0, h, pos, tw);
     }
     __syncthreads();
-    s = 1;
-  }
-  for (; s < logL; s += 2) {
-    const int h1 = L >> (s + 1), h2 = h1 >> 1;  // spans of the two stages
-    const int lh2 = logL - s - 2;
-    for (int g = threadIdx.x; g < (L >> 2); g += blockDim.x) {
-      const int pos = g & (h2 - 1);
-      const int i0 = ((g >> lh2) << (lh2 + 2)) + pos;
-      cx<R> a0 = a[i0], a1 = a[i0 + h2], a2 = a[i0 + h1], a3 = a[i0 + h1 + h2];
-      const cx<R> w1a = tw[h1 - 1 + pos], w1b = tw[h1 - 1 + pos + h2], w2 = tw[h2 - 1 + pos];
-      cx<R> b0 = cadd(a0, a2), b2 = cmul(csub(a0, a2), w1a);
-      cx<R> b1 = cadd(a1, a3), b3 = cmul(csub(a1, a3), w1b);
-      a[i0] = cadd(b0, b1);
-      a[i0 + h2] = cmul(csub(b0, b1), w2);
-      a[i0 + h1] = cadd(b2, b3);
-      a[i0 + h1 + h2] = cmul(csub(b2, b3), w2);
-    }
-    __syncthreads();
+    s += q;
   }
 }
 
 // inverse transform (unnormalised) of two arrays, in place,
-// bit-reversed order -> natural order; radix-2^2 decimation in time (one
-// extra radix-2 stage last when log2 L is odd)
-template <typename R>
-__device__ __forceinline__ void dit4(cx<R>* a, int i0, int h, cx<R> w1, cx<R> w2, cx<R> w3) {
-  const cx<R> a0 = a[i0], a1 = a[i0 + h], a2 = a[i0 + 2 * h], a3 = a[i0 + 3 * h];
-  cx<R> t = cmulc(a1, w1);
-  const cx<R> b0 = cadd(a0, t), b1 = csub(a0, t);
-  t = cmulc(a3, w1);
-  const cx<R> b2 = cadd(a2, t), b3 = csub(a2, t);
-  t = cmulc(b2, w2);
-  a[i0] = cadd(b0, t);
-  a[i0 + 2 * h] = csub(b0, t);
-  t = cmulc(b3, w3);
-  a[i0 + h] = cadd(b1, t);
-  a[i0 + 3 * h] = csub(b1, t);
-}
-
+// bit-reversed order -> natural order
 template <typename R>
 __device__ void fft_dit_inv2(cx<R>* a, cx<R>* c, int logL, const cx<R>* __restrict__ tw) {
-  const int L = 1 << logL;
   int s = 0;
-  for (; s + 1 < logL; s += 2) {
-    const int h = 1 << s;  // spans h and 2h
-    for (int g = threadIdx.x; g < (L >> 2); g += blockDim.x) {
+  while (s < logL) {
+    const int rem = logL - s;
+    const int q = rem >= 4 ? 4 : (rem >= 2 ? 2 : 1);
+    const int h = 1 << s;
+    const int ngroups = 1 << (logL - q);
+    for (int gg = threadIdx.x; gg < 2 * ngroups; gg += blockDim.x) {
+      cx<R>* arr = gg < ngroups ? a : c;
+      const int g = gg < ngroups ? gg : gg - ngroups;
       const int pos = g & (h - 1);
-      const int i0 = ((g >> s) << (s + 2)) + pos;
-      const cx<R> w1 = tw[h - 1 + pos], w2 = tw[2 * h - 1 + pos], w3 = tw[2 * h - 1 + pos + h];
-      dit4(a, i0, h, w1, w2, w3);
-      dit4(c, i0, h, w1, w2, w3);
+      const int i0 = ((g >> s) << (s + q)) + pos;
+      if (q == 4) dit_group<16>(arr, i0, h, pos, tw);
+      else if (q == 2) dit_group<4>(arr, i0, h, pos, tw);
+      else dit_group<2>(arr, i0, h, pos, tw);
     }
     __syncthreads();
-  }
-  if (s < logL) {  // last radix-2 stage, span L/2
-    const int half = L >> 1;
-    for (int b = threadIdx.x; b < half; b += blockDim.x) {
-      const cx<R> w = tw[half - 1 + b];
-      cx<R> t = cmulc(a[b + half], w);
-      cx<R> u = a[b];
-      a[b] = cadd(u, t);
-      a[b + half] = csub(u, t);
-      t = cmulc(c[b + half], w);
-      u = c[b];
-      c[b] = cadd(u, t);
-      c[b + half] = csub(u, t);
-    }
-    __syncthreads();
+    s += q;
   }
 }
 
@@ -137,7 +152,7 @@ fft_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int lo
   const int L = 1 << logL;
   const R cmass = R(cmass_d);
   cx<R>* a = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* c = a + L;
+  cx<R>* c = a + padded_len(L);
   const int npairs = (nvec + 1) >> 1;
   for (int pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
     const int va = 2 * pair;
@@ -149,26 +164,27 @@ fft_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int lo
         z.re = R(X[oa + (size_t)i * es]);
         if (hasb) z.im = R(X[ob + (size_t)i * es]);
       }
-      a[i] = z;
+      a[pad(i)] = z;
     }
     __syncthreads();
     fft_dif(a, logL, tw);
     for (int p = threadIdx.x; p < L; p += blockDim.x) {
-      const cx<R> z = a[p];
-      c[p] = cmul(z, S2[p]);
-      a[p] = cmul(z, S1[p]);
+      const cx<R> z = a[pad(p)];
+      c[pad(p)] = cmul(z, S2[p]);
+      a[pad(p)] = cmul(z, S1[p]);
     }
     __syncthreads();
     fft_dit_inv2(a, c, logL, tw);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const size_t ia = oa + (size_t)i * es;
-      R y = a[i].re * coef<R, C>(cp, ia) + c[i].re * coef<R, C>(cm, ia);
+      const cx<R> ya_ = a[pad(i)], yc_ = c[pad(i)];
+      R y = ya_.re * coef<R, C>(cp, ia) + yc_.re * coef<R, C>(cm, ia);
       if (M) y += cmass * R(M[ia]);
       if (accumulate) y += R(Y[ia]);
       Y[ia] = T(y);
       if (hasb) {
         const size_t ib = ob + (size_t)i * es;
-        R yb = a[i].im * coef<R, C>(cp, ib) + c[i].im * coef<R, C>(cm, ib);
+        R yb = ya_.im * coef<R, C>(cp, ib) + yc_.im * coef<R, C>(cm, ib);
         if (M) yb += cmass * R(M[ib]);
         if (accumulate) yb += R(Y[ib]);
         Y[ib] = T(yb);
@@ -184,7 +200,7 @@ cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int log
                             const C* cm, const T* M, double cmass, T* Y, int accumulate,
                             cudaStream_t st) {
   const int L = 1 << logL;
-  const size_t smem = 2 * (size_t)L * sizeof(cx<R>);
+  const size_t smem = 2 * (size_t)padded_len(L) * sizeof(cx<R>);
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, R, C>,
@@ -209,7 +225,7 @@ __global__ void build_spectra_kernel(const double* __restrict__ t, int n, int lo
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 1 << logL;
   cx<double>* a = reinterpret_cast<cx<double>*>(smem_raw);
-  cx<double>* tw = a + L;
+  cx<double>* tw = a + padded_len(L);
   // tw[half - 1 + pos] = exp(-2 pi i pos / (2 half)), half = 1, 2, 4, ..., L/2
   for (int k = threadIdx.x; k < L - 1; k += blockDim.x) {
     const int lh = 31 - __clz(k + 1);  // half = 2^lh <= k + 1 < 2 half
@@ -226,7 +242,7 @@ __global__ void build_spectra_kernel(const double* __restrict__ t, int n, int lo
     const double h1 = (d1 >= -1 && d1 <= n - 1) ? t[d1 + 1] : 0.0;
     const int m2 = (m <= 1) ? m : m - L;
     const double h2 = (m2 >= -(n - 1) && m2 <= 1) ? t[-m2 + 1] : 0.0;
-    a[m] = {h1, h2};
+    a[pad(m)] = {h1, h2};
   }
   __syncthreads();
   fft_dif(a, logL, tw);
@@ -234,7 +250,7 @@ __global__ void build_spectra_kernel(const double* __restrict__ t, int n, int lo
   for (int p = threadIdx.x; p < L; p += blockDim.x) {
     const int f = bitrev(p, logL);
     const int pp = bitrev((L - f) & (L - 1), logL);
-    const cx<double> z = a[p], zc = {a[pp].re, -a[pp].im};
+    const cx<double> z = a[pad(p)], zc = {a[pad(pp)].re, -a[pad(pp)].im};
     const cx<double> h1 = {0.5 * (z.re + zc.re) * sc, 0.5 * (z.im + zc.im) * sc};
     // (z - zc) / (2i)
     const cx<double> h2 = {0.5 * (z.im - zc.im) * sc, -0.5 * (z.re - zc.re) * sc};
@@ -247,7 +263,7 @@ template <typename R>
 cudaError_t launch_build_spectra(const double* t, int n, int logL, double scale, cx<R>* S1,
                                  cx<R>* S2, cx<R>* tw, cudaStream_t st) {
   const int L = 1 << logL;
-  const size_t smem = (size_t)(2 * L) * sizeof(cx<double>);
+  const size_t smem = (size_t)(padded_len(L) + L) * sizeof(cx<double>);
   cudaError_t e = cudaFuncSetAttribute(build_spectra_kernel<R>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
