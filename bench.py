@@ -51,6 +51,7 @@ def _peaks():
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # = 1258.6 GFLOP/s at the 2070 MHz maximum clock
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07  # = 80 548 GFLOP/s (FMA = 2 flops)
 FP32_ISSUE_TOPS = 152 * 128 * 2.07 / 1e3  # = 40.3 T FP32 instructions/s
+TRAFFIC_DF32_PASS = 100.88448e6 + 13.602816e6  # dram__bytes_read.sum + dram__bytes_write.sum
 
 
 def problem():
@@ -250,9 +251,13 @@ def roofline(w, steps, outer):
         kern = "fft_pass_kernel<double,df,df> (outer double-float Toeplitz apply)"
         src = "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (one instruction = one op)"
     total_ms = sum(v[1] for v in res.values())
+    # DRAM bytes (read + write) of one row pass at n = 2047 from the ncu capture
+    # summarised in profiles/fft_pass_df32_outer_apply_n2047.md (same kernel code)
+    traffic = TRAFFIC_DF32_PASS if (outer == "df32" and N_GRID == 2047) else None
     return {"bound": "alu", "kernel": kern, "achieved": round(achieved, 3), "peak": round(peak, 2),
             "unit": unit, "frac": round(achieved / peak, 4), "peak_source": src,
-            "traffic": None, "work_per_launch": work, "launches": launches,
+            "traffic": traffic, "traffic_unit": "bytes per launch",
+            "work_per_launch": work, "launches": launches,
             "avg_launch_ms": round(avg_s * 1e3, 4),
             "share_of_profiled_time": {k: round(v[1] / total_ms, 4) for k, v in res.items()}}
 
@@ -351,7 +356,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--precision", default="fp16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--outer", default="df32", choices=["df32", "fp64"])
     args = ap.parse_args()
     if args.kernel:
