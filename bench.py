@@ -322,14 +322,15 @@ def kernel_micro(kind, reps):
     fft64 / fftdf = the outer apply (FP64 / double-float FFT)."""
     import torch
     from paper_1706_06844_gb300 import fde
-    prec = {"gemm": fde.FDE_PREC_BF16, "fft32": fde.FDE_PREC_FP32, "fft64": fde.FDE_PREC_FP64,
-            "fftdf": fde.FDE_PREC_FP64}[kind]
-    path = {"gemm": fde.FDE_PATH_GEMM, "fft32": fde.FDE_PATH_FFT}.get(kind)
+    prec = {"gemm": fde.FDE_PREC_BF16, "gemm3": fde.FDE_PREC_BF16X3, "fft32": fde.FDE_PREC_FP32,
+            "fft64": fde.FDE_PREC_FP64, "fftdf": fde.FDE_PREC_FP64}[kind]
+    path = {"gemm": fde.FDE_PATH_GEMM, "gemm3": fde.FDE_PATH_GEMM,
+            "fft32": fde.FDE_PATH_FFT}.get(kind)
     outer = fde.FDE_OUTER_DF32 if kind == "fftdf" else None
     w = Workload(prec, path=path, outer=outer)
     x = torch.randn((N_GRID, N_GRID), dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
-    call = ((lambda: fde.fde_level_apply(w.h, 0, x, y)) if kind in ("gemm", "fft32")
+    call = ((lambda: fde.fde_level_apply(w.h, 0, x, y)) if kind in ("gemm", "gemm3", "fft32")
             else (lambda: fde.fde_apply(w.h, x, y)))
     for _ in range(2):
         call()
@@ -347,7 +348,7 @@ def kernel_micro(kind, reps):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", default=None, choices=["gemm", "fft32", "fft64", "fftdf"],
+    ap.add_argument("--kernel", default=None, choices=["gemm", "gemm3", "fft32", "fft64", "fftdf"],
                     help="time one kernel class alone (for profiler captures)")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--gpus", type=int, default=1)
@@ -356,7 +357,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["bf16", "fp16", "fp32", "bf16x3"])
     ap.add_argument("--outer", default="df32", choices=["df32", "fp64"])
     args = ap.parse_args()
     if args.kernel:
@@ -381,8 +382,8 @@ def main():
     import torch
     from paper_1706_06844_gb300 import fde
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    mixed = {"bf16": fde.FDE_PREC_BF16, "fp16": fde.FDE_PREC_FP16,
-             "fp32": fde.FDE_PREC_FP32}[args.precision]
+    mixed = {"bf16": fde.FDE_PREC_BF16, "fp16": fde.FDE_PREC_FP16, "fp32": fde.FDE_PREC_FP32,
+             "bf16x3": fde.FDE_PREC_BF16X3}[args.precision]
     outer = fde.FDE_OUTER_DF32 if args.outer == "df32" else fde.FDE_OUTER_FP64
     w = Workload(mixed, outer=outer)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:

@@ -58,10 +58,13 @@ extern "C" {
 #define FDE_PREC_FP32          1  /* V-cycle vectors and Toeplitz products in FP32 */
 #define FDE_PREC_BF16          2  /* FP32 vectors, Toeplitz products on tcgen05 in BF16 with FP32 accumulation */
 #define FDE_PREC_FP16          3  /* as BF16 with FP16 operands */
+#define FDE_PREC_BF16X3        4  /* operands split into BF16 hi + lo, three tcgen05 products per block
+                                     accumulated in FP32 (~16-bit operands) */
 
 /* how the preconditioner's dense Toeplitz products are evaluated */
-#define FDE_PATH_AUTO          0  /* tensor-core GEMM for BF16/FP16, FFT above the direct-sum cut-off, else direct */
-#define FDE_PATH_GEMM          1  /* tcgen05 GEMM (BF16/FP16 only) */
+#define FDE_PATH_AUTO          0  /* tensor-core GEMM for BF16/FP16/BF16X3 on levels with n >= 1536, else FFT
+                                     above the direct-sum cut-off (n >= 127), else direct */
+#define FDE_PATH_GEMM          1  /* tcgen05 GEMM (BF16/FP16/BF16X3 only) */
 #define FDE_PATH_FFT           2  /* circulant-embedding FFT */
 #define FDE_PATH_DIRECT        3  /* direct summation */
 

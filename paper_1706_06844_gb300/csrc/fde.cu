@@ -230,7 +230,8 @@ struct MG : MGBase {
         lv[l].by1 = 0.25 * a.by0 + a.by1;
       }
     }
-    const bool lowp = (p.precision == FDE_PREC_BF16 || p.precision == FDE_PREC_FP16);
+    const bool lowp = (p.precision == FDE_PREC_BF16 || p.precision == FDE_PREC_FP16 ||
+                       p.precision == FDE_PREC_BF16X3);
     for (size_t l = 0; l < lv.size(); ++l) {
       Lv& L = lv[l];
       const bool last = l + 1 == lv.size();
@@ -254,11 +255,11 @@ struct MG : MGBase {
       int path = p.toeplitz_path;
       const int nmin = std::min(L.n1, L.n2);
       if (path == FDE_PATH_AUTO) {
-        if (lowp && nmin >= tc::kMinGemmN) path = FDE_PATH_GEMM;
+        if (lowp && nmin >= tc::kAutoGemmN) path = FDE_PATH_GEMM;
         else path = nmin >= 127 ? FDE_PATH_FFT : FDE_PATH_DIRECT;
       }
       if (path == FDE_PATH_GEMM && !lowp)
-        return h->fail(FDE_ERR_ARG, "the tensor-core path needs BF16 or FP16 precision");
+        return h->fail(FDE_ERR_ARG, "the tensor-core path needs BF16, FP16 or BF16X3 precision");
       if (path == FDE_PATH_GEMM && nmin < tc::kMinGemmN) path = FDE_PATH_FFT;
       L.path = path;
       if (path == FDE_PATH_FFT) {
@@ -282,7 +283,8 @@ struct MG : MGBase {
         RCHK(h->alloc(&L.txT, L.n1 + 2));
         RCHK(h->alloc(&L.tyT, L.n2 + 2));
       } else {
-        const int prec = p.precision == FDE_PREC_BF16 ? tc::kBF16 : tc::kFP16;
+        const int prec = p.precision == FDE_PREC_BF16 ? tc::kBF16
+                         : p.precision == FDE_PREC_FP16 ? tc::kFP16 : tc::kBF16X3;
         int r = tc::level_create(&L.gemm, L.n1, L.n2, prec, sg && l > 0);
         if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core level allocation failed (%d)", r);
       }
@@ -327,7 +329,7 @@ struct MG : MGBase {
         LCHK((launch_convert<double, T>(L.n2 + 1, L.ty, 1.0, L.tyT, st)));
       } else if (L.path == FDE_PATH_GEMM && l + 1 < lv.size()) {
         int r = tc::level_setup(&L.gemm, L.tx, L.ty, st);
-        h->launches += 4;
+        h->launches += 2;
         if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core bank setup failed (%d)", r);
       }
     }
@@ -376,7 +378,7 @@ struct MG : MGBase {
       int r = tc::level_products(&L.gemm, (const float*)xin_x, (const float*)xin_y,
                                  (const float*)M, cm, (const float*)L.dp, (const float*)L.dm,
                                  (const float*)L.ep, (const float*)L.em, (float*)kx, st);
-      h->launches += 2;
+      h->launches += (sg && l > 0) ? 4 : 3;
       if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core products failed (%d)", r);
     }
     h->pend(pi);
@@ -673,7 +675,7 @@ static int validate(const fde_params* p, std::string& why) {
   if (p->nu_pre < 0 || p->nu_pre > 4 || p->nu_post < 0 || p->nu_post > 4) return bad("nu in [0, 4]");
   if (!(p->omega > 0.0 && p->omega < 2.0)) return bad("omega must be in (0, 2)");
   if (p->coarsest_n < 1) return bad("coarsest_n must be >= 1");
-  if (p->precision < FDE_PREC_FP64 || p->precision > FDE_PREC_FP16) return bad("unknown precision");
+  if (p->precision < FDE_PREC_FP64 || p->precision > FDE_PREC_BF16X3) return bad("unknown precision");
   if (p->toeplitz_path < FDE_PATH_AUTO || p->toeplitz_path > FDE_PATH_DIRECT) return bad("unknown toeplitz_path");
   if (p->outer != FDE_OUTER_FP64 && p->outer != FDE_OUTER_DF32) return bad("unknown outer");
   const int L1 = ceil_log2(2L * p->n1 - 1), L2 = ceil_log2(2L * p->n2 - 1);

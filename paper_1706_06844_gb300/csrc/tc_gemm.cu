@@ -2,24 +2,36 @@
 // (tcgen05 + TMEM + TMA), sm_103a.
 //
 // For a level grid X (n2 rows y, n1 columns x) the operator of Eq. (AxAy)
-// needs four dense products, each a GEMM with one Toeplitz factor:
-//     acc0 = X  A_x^T   (rows of X times A_x)        acc1 = X  A_x
-//     acc2 = A_y X                                  acc3 = A_y^T X
-// One CTA owns a 128 x 128 output tile and keeps all four FP32 accumulators
-// in tensor memory (4 x 128 columns = the whole 512-column TMEM).  A 64-deep
-// K-block of a Toeplitz factor depends only on the block-diagonal offset
-// delta = (output block start) - (K block start), so the factor is stored as
-// a bank of 128 x 64 tiles, one per offset (O(n) tiles, never an n x n
-// matrix), built once per level from the generator t_d and streamed by TMA
-// like any other operand.  Blocks whose Toeplitz tile is identically zero
-// (above the super-diagonal) are skipped: each accumulator visits only the
-// K-blocks its triangle touches.  The epilogue scales by the coefficient
-// fields and adds the mass term: kx = cm M + dp acc0 + dm acc1 + ep acc2 + em acc3.
+// needs four dense products with one Toeplitz factor each:
+//     X A_x^T and X A_x          (x direction; output rows j, columns i)
+//     A_y X  and A_y^T X         (y direction)
+// Two launches cover them.  An x-CTA owns a 128 (j) x 256 (i) output tile and
+// accumulates X A_x^T and X A_x in two FP32 TMEM accumulators of 256 columns
+// (the whole 512-column TMEM).  A y-CTA owns a 128 (i) x 256 (j) tile of the
+// TRANSPOSED y products, D[i][j] = sum_k X[k][i] A_y[j][k] (and A_y[k][j]):
+// its A operand is X read MN-major, and its TMEM lanes are grid columns, so
+// its epilogue stores are coalesced without staging.
 //
-// Warp roles (192 threads): warp 0 issues TMA loads, warp 1 (one elected
-// lane) issues tcgen05.mma, warps 2-5 drain TMEM in the epilogue.  Every
-// mbarrier wait is bounded; on timeout the CTA raises a device error flag,
-// drains its in-flight copies and MMAs, frees TMEM and exits.
+// Operands.  The X tiles (128 x 64, 16-bit) are streamed by TMA.  The Toeplitz
+// tiles (256 x 64) are never stored: a 64-deep K block of A_gamma at output
+// offset delta is B[r][k] = t[delta + r - k] (or t[-delta + k - r] for the
+// transpose), so eight "synthesis" warps -- the epilogue warps, idle during the
+// main loop -- stage a 320-element window of the O(n) generator t in shared
+// memory and write the tile in the 128-byte-swizzled K-major layout the
+// tensor core reads, while the previous block multiplies.  Blocks whose tile
+// is identically zero (above the super-diagonal) are skipped.
+//
+// Precision.  kBF16 / kFP16: one product per block (16-bit operands, FP32
+// accumulation).  kBF16X3: X = X_hi + X_lo and t = t_hi + t_lo split into
+// BF16 pairs and three products (hi hi, lo hi, hi lo) accumulated in FP32:
+// ~16-bit operands, which keeps the multigrid preconditioner as effective as
+// an FP32 one (the residual b - K x of a smooth x cancels heavily).
+//
+// Roles (320 threads): warp 0 issues TMA, warp 1 (one lane) issues tcgen05.mma,
+// warps 2-9 synthesise Toeplitz tiles and then drain TMEM in the epilogue (two
+// warps per TMEM lane group, each taking half of the tile's columns).
+// Every mbarrier wait is bounded (about one second); on timeout the CTA raises
+// a device error flag, drains its copies and MMAs, frees TMEM and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -31,12 +43,25 @@
 namespace fde {
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int STAGES = 6;
-constexpr int TILE_BYTES = BM * BK * 2;  // 16 KB: 128 rows x 128 B
-constexpr int NUM_THREADS = 192;
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int A_BYTES = BM * BK * 2;   // 16 KB
+constexpr int B_BYTES = BN * BK * 2;   // 32 KB
+constexpr int NUM_THREADS = 320;  // 2 + 8 warps
+constexpr int NSYN = 8;            // synthesis / epilogue warps
 constexpr uint32_t TMEM_COLS = 512;
-constexpr size_t SMEM_BYTES = (size_t)STAGES * 2 * TILE_BYTES + 1024 /*align*/ + 256 /*bars*/;
+constexpr int GEN_OFF = 320;           // zero padding in front of the generator copy
+constexpr int GEN_PAD = 1024;          // total padding elements
+
+template <int NT>
+struct Cfg {
+  static constexpr int STAGES = NT == 1 ? 3 : 2;
+  static constexpr int STAGE_BYTES = NT * (A_BYTES + B_BYTES);  // 1 KB multiple
+  // + 256 B barriers + the generator copies (gen_bytes(n) per term, after the barriers)
+  static constexpr size_t FIXED = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+};
+// padded generator length and the bytes of its forward + reversed copies
+__host__ __device__ constexpr int gen_len(int n) { return (n + GEN_PAD + 7) / 8 * 8; }
+__host__ __device__ constexpr size_t gen_bytes(int n) { return (size_t)2 * gen_len(n) * 2; }
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -48,6 +73,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -81,6 +109,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   *abort = 1;
   return false;
 }
+// one lane per warp waits, the warp follows its verdict
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
                                             uint32_t bar) {
   asm volatile(
@@ -98,11 +132,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   d |= (uint64_t)2 << 61;  // 128-byte swizzle
   return d;
 }
-// kind::f16 instruction descriptor: D F32, A/B BF16 or F16, A K-major,
-// B K-major or MN-major, N = 128, M = 128
-__host__ __device__ constexpr uint32_t make_idesc(bool b_mn_major, bool f16) {
+// kind::f16 instruction descriptor: D F32, A/B BF16 or F16, A K-major or
+// MN-major, B K-major, N = 256, M = 128
+__host__ __device__ constexpr uint32_t make_idesc(bool a_mn_major, bool f16) {
   return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) |
-         ((b_mn_major ? 1u : 0u) << 16) | ((uint32_t)(BN >> 3) << 17) |
+         ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t)(BN >> 3) << 17) |
          ((uint32_t)(BM >> 4) << 24);
 }
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
@@ -116,18 +150,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    bar)
                : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
@@ -156,23 +178,14 @@ __device__ __forceinline__ void fence_before() {
 }
 
 // ---------------------------------------------------------------- job list
-// The K loop of a tile visits, in order: x-direction blocks (acc 0 / acc 1)
-// then y-direction blocks (acc 2 / acc 3), skipping identically-zero blocks.
-// Block offset delta = out0 - k0: acc 0/2 (lower Hessenberg) is nonzero for
-// delta >= -128, acc 1/3 (its transpose) for delta <= 64.
+// One job per (K block, triangle): acc 0 is the lower-Hessenberg factor
+// (tile t[delta + r - k], nonzero for delta >= -256), acc 1 its transpose
+// (t[-delta + k - r], nonzero for delta <= 64); delta = out0 - k0.
 struct JobIter {
-  int i0, j0, nkx, nky;
-  int phase = 0, kb = 0, sub = 0;  // phase 0: x, 1: y, 2: done
+  int out0, nk;
+  int kb = 0, sub = 0;
   __device__ bool next(int& acc, int& k0, int& delta) {
-    while (phase < 2) {
-      const int nk = phase == 0 ? nkx : nky;
-      const int out0 = phase == 0 ? i0 : j0;
-      if (kb >= nk) {
-        ++phase;
-        kb = 0;
-        sub = 0;
-        continue;
-      }
+    while (kb < nk) {
       k0 = kb * BK;
       delta = out0 - k0;
       const int s = sub;
@@ -180,48 +193,69 @@ struct JobIter {
         sub = 0;
         ++kb;
       }
-      if (s == 0 && delta >= -128) { acc = phase * 2; return true; }
-      if (s == 1 && delta <= 64) { acc = phase * 2 + 1; return true; }
+      if (s == 0 && delta >= -BN) { acc = 0; return true; }
+      if (s == 1 && delta <= BK) { acc = 1; return true; }
     }
     return false;
   }
 };
 
 struct KParams {
-  const float* M;  // mass term source (may be null)
+  // generator t as 16-bit copies, each [forward | reversed] of gen_len(n) entries:
+  // forward f[e] = t[e - GEN_OFF], reversed r[e] = t[(n + GEN_OFF) - e], zero outside [-1, n-1]
+  const uint16_t* gen_hi;
+  const uint16_t* gen_lo;  // low part (split precision)
+  int glen;                // gen_len of the contracted dimension
+  const float* M;          // mass-term source (x-CTAs; may be null)
   float cm;
-  const float *dp, *dm, *ep, *em;
-  float* kx;
+  const float *c0, *c1;    // coefficient fields of acc 0 / acc 1 (dp, dm or sigma ep, sigma em)
+  float* out;
   int n1, n2;
-  int rowL_x, rowU_x, rowL_y, rowU_y;  // first bank row of each bank
-  float inv_scale;                     // 1 / bank scale
+  float inv_scale;
   int* err;
 };
 
+// DIR 0: x products (rows j, columns i); DIR 1: transposed y products.
+// NT: number of 16-bit terms per operand (1, or 2 for the 3-product split).
+template <int DIR, int NT>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapXa,
-                     const __grid_constant__ CUtensorMap mapXb,
-                     const __grid_constant__ CUtensorMap mapBank, const KParams kp,
-                     uint32_t idesc_x, uint32_t idesc_y) {
+toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
+                     const __grid_constant__ CUtensorMap mapA_lo, const KParams kp,
+                     uint32_t idesc) {
+  using C = Cfg<NT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* base =
-      (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* tilesA = base;                         // STAGES x 16 KB
-  unsigned char* tilesB = base + STAGES * TILE_BYTES;   // STAGES x 16 KB
-  uint64_t* bars = (uint64_t*)(base + 2 * STAGES * TILE_BYTES);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + STAGES;
-  uint64_t* accbar = bars + 2 * STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(base + C::STAGES * C::STAGE_BYTES);
+  uint64_t* fullA = bars;
+  uint64_t* fullB = bars + C::STAGES;
+  uint64_t* empty = bars + 2 * C::STAGES;
+  uint64_t* accbar = bars + 3 * C::STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 3 * C::STAGES + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  // generator copies: term t at gsm + t * 2 * glen (16-bit units), forward then reversed
+  uint16_t* gsm = reinterpret_cast<uint16_t*>(base + C::STAGES * C::STAGE_BYTES + 256);
+  auto tileA = [&](int s, int t) { return base + s * C::STAGE_BYTES + t * A_BYTES; };
+  auto tileB = [&](int s, int t) {
+    return base + s * C::STAGE_BYTES + NT * A_BYTES + t * B_BYTES;
+  };
+  {
+    const int words = kp.glen;  // 2 * glen 16-bit values = glen 32-bit words per term
+    for (int t = 0; t < NT; ++t) {
+      const uint4* src = reinterpret_cast<const uint4*>(t == 0 ? kp.gen_hi : kp.gen_lo);
+      uint4* dst = reinterpret_cast<uint4*>(gsm + (size_t)t * 2 * kp.glen);
+      for (int e = threadIdx.x; e < words / 4; e += NUM_THREADS) dst[e] = src[e];
+    }
+  }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.x * BN, j0 = blockIdx.y * BM;
-  const int nkx = (kp.n1 + BK - 1) / BK, nky = (kp.n2 + BK - 1) / BK;
+  // output tile: rows m0 .. m0+127 of the M dimension, columns out0 .. out0+255 of N
+  const int out0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int nk = DIR == 0 ? (kp.n1 + BK - 1) / BK : (kp.n2 + BK - 1) / BK;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(smem_u32(&full[s]), 1);
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(smem_u32(&fullA[s]), 1);
+      mbar_init(smem_u32(&fullB[s]), NSYN);
       mbar_init(smem_u32(&empty[s]), 1);
     }
     mbar_init(smem_u32(accbar), 1);
@@ -241,72 +275,63 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapXa,
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ producer
+    // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      JobIter it{i0, j0, nkx, nky};
+      JobIter it{out0, nk};
       int acc, k0, delta, n = 0;
-      int last_parity[STAGES];
-      bool issued[STAGES];
-      for (int s = 0; s < STAGES; ++s) issued[s] = false;
+      uint32_t issued_mask = 0, parity_mask = 0;
       while (!*abort_flag && it.next(acc, k0, delta)) {
-        const int s = n % STAGES;
-        const uint32_t ph = (uint32_t)(n / STAGES) & 1u;
+        const int s = n % C::STAGES;
+        const uint32_t ph = (uint32_t)(n / C::STAGES) & 1u;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag)) break;
-        const uint32_t fb = smem_u32(&full[s]);
-        mbar_expect_tx(fb, 2 * TILE_BYTES);
-        const uint32_t dA = smem_u32(tilesA + s * TILE_BYTES);
-        const uint32_t dB = smem_u32(tilesB + s * TILE_BYTES);
-        if (acc < 2) {
-          const int row = acc == 0 ? kp.rowL_x + ((delta + 128) / 64) * BM
-                                   : kp.rowU_x + ((64 - delta) / 64) * BM;
-          tma_load_2d(dA, &mapXa, k0, j0, fb);      // X[j0.., k0..]   (K-major)
-          tma_load_2d(dB, &mapBank, 0, row, fb);    // Toeplitz tile   (K-major)
-        } else {
-          const int row = acc == 2 ? kp.rowL_y + ((delta + 128) / 64) * BM
-                                   : kp.rowU_y + ((64 - delta) / 64) * BM;
-          tma_load_2d(dA, &mapBank, 0, row, fb);            // Toeplitz tile (K-major)
-          tma_load_2d(dB, &mapXb, i0, k0, fb);              // X[k0.., i0..i0+63]  (MN-major)
-          tma_load_2d(dB + TILE_BYTES / 2, &mapXb, i0 + 64, k0, fb);
+        const uint32_t fb = smem_u32(&fullA[s]);
+        mbar_expect_tx(fb, NT * A_BYTES);
+        for (int t = 0; t < NT; ++t) {
+          const CUtensorMap* map = t == 0 ? &mapA_hi : &mapA_lo;
+          const uint32_t dA = smem_u32(tileA(s, t));
+          if (DIR == 0) {
+            tma_load_2d(dA, map, k0, m0, fb);  // X[m0.., k0..], K-major
+          } else {
+            tma_load_2d(dA, map, m0, k0, fb);  // X[k0.., m0..m0+63], read MN-major
+            tma_load_2d(dA + A_BYTES / 2, map, m0 + 64, k0, fb);
+          }
         }
-        issued[s] = true;
-        last_parity[s] = (int)ph;
+        issued_mask |= 1u << s;
+        parity_mask = (parity_mask & ~(1u << s)) | (ph << s);
         ++n;
       }
-      // drain: every issued copy has landed before the CTA can exit
-      const uint64_t t0 = global_ns();
-      for (int s = 0; s < STAGES; ++s)
-        if (issued[s]) {
-          while (!mbar_try(smem_u32(&full[s]), (uint32_t)last_parity[s]))
+      const uint64_t t0 = global_ns();  // every issued copy lands before the CTA exits
+      for (int s = 0; s < C::STAGES; ++s)
+        if (issued_mask & (1u << s))
+          while (!mbar_try(smem_u32(&fullA[s]), (parity_mask >> s) & 1u))
             if (global_ns() - t0 > 1000000000ull) break;
-        }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      JobIter it{i0, j0, nkx, nky};
+      JobIter it{out0, nk};
       int acc, k0, delta, n = 0;
-      bool started[4] = {false, false, false, false};
+      bool started[2] = {false, false};
       while (!*abort_flag && it.next(acc, k0, delta)) {
-        const int s = n % STAGES;
-        const uint32_t ph = (uint32_t)(n / STAGES) & 1u;
-        if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag)) break;
+        const int s = n % C::STAGES;
+        const uint32_t ph = (uint32_t)(n / C::STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&fullA[s]), ph, abort_flag)) break;
+        if (!mbar_wait(smem_u32(&fullB[s]), ph, abort_flag)) break;
         fence_after();
-        const uint32_t aA = smem_u32(tilesA + s * TILE_BYTES);
-        const uint32_t aB = smem_u32(tilesB + s * TILE_BYTES);
         const uint32_t d = tmem + (uint32_t)(acc * BN);
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint64_t da = smem_desc(aA + kk * 32, 16, 1024);
-          uint64_t db;
-          uint32_t idesc;
-          if (acc < 2) {
-            db = smem_desc(aB + kk * 32, 16, 1024);
-            idesc = idesc_x;
-          } else {
-            db = smem_desc(aB + kk * 2048, TILE_BYTES / 2, 1024);
-            idesc = idesc_y;
+          // (A term, B term) pairs: hi*hi, then lo*hi and hi*lo for the split
+#pragma unroll
+          for (int p = 0; p < (NT == 1 ? 1 : 3); ++p) {
+            const int ta = p == 1 ? 1 : 0, tb = p == 2 ? 1 : 0;
+            const uint32_t aA = smem_u32(tileA(s, ta));
+            const uint32_t aB = smem_u32(tileB(s, tb));
+            const uint64_t da = DIR == 0 ? smem_desc(aA + kk * 32, 16, 1024)
+                                         : smem_desc(aA + kk * 2048, A_BYTES / 2, 1024);
+            const uint64_t db = smem_desc(aB + kk * 32, 16, 1024);
+            mma_f16(d, da, db, idesc, (started[acc] || kk > 0 || p > 0) ? 1u : 0u);
           }
-          mma_f16(d, da, db, idesc, (started[acc] || kk > 0) ? 1u : 0u);
         }
         started[acc] = true;
         mma_commit(smem_u32(&empty[s]));
@@ -315,15 +340,69 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapXa,
       mma_commit(smem_u32(accbar));  // completes when every MMA above has completed
     }
   } else {
+    // ------------------------------------------------------------ synthesis
+    const int w = warp - 2;  // 0..NSYN-1
+    {
+      JobIter it{out0, nk};
+      int acc, k0, delta, n = 0;
+      while (!*abort_flag && it.next(acc, k0, delta)) {
+        const int s = n % C::STAGES;
+        const uint32_t ph = (uint32_t)(n / C::STAGES) & 1u;
+        if (!warp_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag)) break;
+        // row r, 16-byte chunk c (k = 8c .. 8c+7) of the tile: acc 0 needs
+        // t[delta + r - k] = reversed[(n + GEN_OFF) - delta - r + k], acc 1 needs
+        // t[-delta + k - r] = forward[GEN_OFF - delta - r + k]: eight consecutive
+        // 16-bit entries starting at e0 = base0 - r + 8c
+        const int nn = DIR == 0 ? kp.n1 : kp.n2;
+        const int base0 = acc == 0 ? kp.glen + (nn + GEN_OFF) - delta : GEN_OFF - delta;
+        // A thread owns 16-byte chunk column c of an 8-row block r0 .. r0+7: row
+        // r0 + u starts at entry e0 - u, e0 = base0 - r0 + 8c, so the eight chunks
+        // are shifted views of entries e0 - 7 .. e0 + 7: nine words are loaded once
+        // and re-aligned so that word k holds entries (e0 - 7 + 2k, e0 - 6 + 2k);
+        // row u then starts 7 - u entries in -- a compile-time word and shift.
+        for (int t = 0; t < NT; ++t) {
+          const uint32_t* g32 = reinterpret_cast<const uint32_t*>(gsm + (size_t)t * 2 * kp.glen);
+          unsigned char* B = tileB(s, t);
+#pragma unroll
+          for (int it = 0; it < (BN / 8) * 8 / (NSYN * 32); ++it) {
+            const int unit = it * (NSYN * 32) + w * 32 + lane;  // (row block, chunk)
+            const int rb = unit >> 3, c = unit & 7;
+            const int r0 = rb * 8;
+            const int e0 = base0 - r0 + 8 * c;
+            const int wlo = (e0 - 7) >> 1;  // word holding entry e0 - 7
+            const uint32_t sh0 = (uint32_t)((e0 - 7) & 1) * 16u;
+            uint32_t raw[10], v[9];
+#pragma unroll
+            for (int k = 0; k < 10; ++k) raw[k] = g32[wlo + k];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v[k] = __funnelshift_r(raw[k], raw[k + 1], sh0);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int j = 7 - u;  // row u starts j entries into the window
+              const int wj = j >> 1;
+              uint4 chunk;
+              if (j & 1) {
+                chunk.x = __funnelshift_r(v[wj], v[wj + 1], 16);
+                chunk.y = __funnelshift_r(v[wj + 1], v[wj + 2], 16);
+                chunk.z = __funnelshift_r(v[wj + 2], v[wj + 3], 16);
+                chunk.w = __funnelshift_r(v[wj + 3], v[wj + 4], 16);
+              } else {
+                chunk = make_uint4(v[wj], v[wj + 1], v[wj + 2], v[wj + 3]);
+              }
+              const int r = r0 + u;
+              *reinterpret_cast<uint4*>(B + r * 128 + ((c ^ (r & 7)) << 4)) = chunk;
+            }
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMA
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&fullB[s]));
+        ++n;
+      }
+    }
     // ------------------------------------------------------------ epilogue
-    // Warp w may read TMEM lanes 32 (w % 4) .. +31, i.e. output rows
-    // 32 g .. 32 g + 31.  Per 32-column chunk the four accumulators go through
-    // a padded per-warp staging area (the operand buffers are idle once the
-    // accumulator barrier has fired) so that afterwards lane = column and every
-    // global load/store of the epilogue is one 128-byte row segment.
-    const int g = warp & 3;
-    // one lane per warp waits for the accumulators (backing off between polls so
-    // the waiting warps do not compete with TMA completions on the barrier unit)
+    const int g = warp & 3;          // TMEM lane group this warp may access
+    const int c_lo = (w >> 2) * (BN / 2), c_hi = c_lo + BN / 2;  // its half of the columns
     int okw = 1;
     if (lane == 0) {
       const uint64_t t0 = global_ns();
@@ -336,33 +415,84 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapXa,
     const bool ok = __shfl_sync(0xffffffffu, okw, 0) != 0;
     fence_after();
     if (ok && !*abort_flag) {
-      float* stg = reinterpret_cast<float*>(tilesA) + (warp - 2) * (4 * 32 * 33);
       const uint32_t tl = tmem + ((uint32_t)(g * 32) << 16);
-      for (int cb = 0; cb < BN; cb += 32) {
+      if (DIR == 0) {
+        // lanes are grid rows: stage through shared memory so lane = column
+        float* stg = reinterpret_cast<float*>(base) + w * (2 * 32 * 33);
+        for (int cb = c_lo; cb < c_hi; cb += 32) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          float v[32];
-          tmem_ld32(tl + a * BN + cb, v);
-          tmem_wait_ld();
+          for (int a = 0; a < 2; ++a) {
+            float v[32];
+            tmem_ld32(tl + a * BN + cb, v);
+            tmem_wait_ld();
 #pragma unroll
-          for (int q = 0; q < 32; ++q) stg[(a * 32 + lane) * 33 + q] = v[q];
+            for (int q = 0; q < 32; ++q) stg[(a * 32 + lane) * 33 + q] = v[q];
+          }
+          __syncwarp();
+          const int col = out0 + cb + lane;
+          if (col < kp.n1) {
+            // all loads of the chunk first (the output may alias nothing, but the
+            // compiler cannot know), then the stores
+            const float* __restrict__ c0 = kp.c0;
+            const float* __restrict__ c1 = kp.c1;
+            const float* __restrict__ Mm = kp.M;
+            float* __restrict__ out = kp.out;
+            const int rbase = m0 + g * 32;
+            const int nr = kp.n2 - rbase < 32 ? kp.n2 - rbase : 32;
+            float p0[32], p1[32], pm[32];
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) {
+              const size_t idx = (size_t)(rbase + rr) * kp.n1 + col;
+              p0[rr] = rr < nr ? __ldg(c0 + idx) : 0.f;
+              p1[rr] = rr < nr ? __ldg(c1 + idx) : 0.f;
+              pm[rr] = (rr < nr && Mm) ? __ldg(Mm + idx) : 0.f;
+            }
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) {
+              if (rr < nr) {
+                const size_t idx = (size_t)(rbase + rr) * kp.n1 + col;
+                out[idx] = kp.inv_scale * (p0[rr] * stg[rr * 33 + lane] +
+                                           p1[rr] * stg[(32 + rr) * 33 + lane]) +
+                           kp.cm * pm[rr];
+              }
+            }
+          }
+          __syncwarp();
         }
-        __syncwarp();
-        const int col = i0 + cb + lane;
-        if (col < kp.n1) {
-          for (int rr = 0; rr < 32; ++rr) {
-            const int row = j0 + g * 32 + rr;
-            if (row >= kp.n2) break;
-            const size_t idx = (size_t)row * kp.n1 + col;
-            float v = kp.inv_scale * (kp.dp[idx] * stg[(0 * 32 + rr) * 33 + lane] +
-                                      kp.dm[idx] * stg[(1 * 32 + rr) * 33 + lane] +
-                                      kp.ep[idx] * stg[(2 * 32 + rr) * 33 + lane] +
-                                      kp.em[idx] * stg[(3 * 32 + rr) * 33 + lane]);
-            if (kp.M) v += kp.cm * kp.M[idx];
-            kp.kx[idx] = v;
+      } else {
+        // lanes are grid columns i; TMEM columns are grid rows j
+        const int col = m0 + g * 32 + lane;
+        for (int cb = c_lo; cb < c_hi; cb += 32) {
+          float a0[32], a1[32];
+          tmem_ld32(tl + cb, a0);
+          tmem_ld32(tl + BN + cb, a1);
+          tmem_wait_ld();
+          if (col < kp.n1) {
+            const float* __restrict__ c0 = kp.c0;
+            const float* __restrict__ c1 = kp.c1;
+            float* __restrict__ out = kp.out;
+            const int nr = kp.n2 - (out0 + cb) < 32 ? kp.n2 - (out0 + cb) : 32;
+#pragma unroll
+            for (int h = 0; h < 32; h += 16) {  // two halves keep the loads in registers
+              float q0[16], q1[16], qo[16];
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                const size_t idx = (size_t)(out0 + cb + h + q) * kp.n1 + col;
+                const bool v = h + q < nr;
+                q0[q] = v ? __ldg(c0 + idx) : 0.f;
+                q1[q] = v ? __ldg(c1 + idx) : 0.f;
+                qo[q] = v ? out[idx] : 0.f;
+              }
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                if (h + q < nr) {
+                  const size_t idx = (size_t)(out0 + cb + h + q) * kp.n1 + col;
+                  out[idx] = qo[q] + kp.inv_scale * (q0[q] * a0[h + q] + q1[q] * a1[h + q]);
+                }
+              }
+            }
           }
         }
-        __syncwarp();
       }
     }
   }
@@ -383,33 +513,39 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 to_h<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 template <>
 __device__ __forceinline__ __half to_h<__half>(float v) { return __float2half_rn(v); }
-
-// bank tile (b, i, k): L bank t[delta + i - k], U bank t[-delta + k - i],
-// delta = -128 + 64 b (L) or 64 - 64 b (U); zero outside d in [-1, n-1]
 template <typename H>
-__global__ void bank_kernel(const double* __restrict__ t, int n, int ntL, int ntU, float scale,
-                            H* bankL, H* bankU) {
-  const size_t totL = (size_t)ntL * BM * BK, tot = totL + (size_t)ntU * BM * BK;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const bool upper = e >= totL;
-    const size_t f = upper ? e - totL : e;
-    const int b = (int)(f / (BM * BK)), i = (int)((f / BK) % BM), k = (int)(f % BK);
-    int d;
-    if (!upper) d = (-128 + 64 * b) + i - k;
-    else d = -(64 - 64 * b) + k - i;
+__device__ __forceinline__ float from_h(H v);
+template <>
+__device__ __forceinline__ float from_h<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float from_h<__half>(__half v) { return __half2float(v); }
+
+// padded 16-bit generator copies [forward | reversed], each gen_len(n) long:
+// f[e] = scale t_{e - GEN_OFF}, r[e] = scale t_{(n + GEN_OFF) - e}, zero outside
+// d in [-1, n-1]; split: lo = t - hi
+template <typename H>
+__global__ void generator_kernel(const double* __restrict__ t, int n, float scale, H* hi, H* lo) {
+  const int len = gen_len(n);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * len; e += gridDim.x * blockDim.x) {
+    const int d = e < len ? e - GEN_OFF : (n + GEN_OFF) - (e - len);
     const float v = (d >= -1 && d <= n - 1) ? (float)(scale * t[d + 1]) : 0.f;
-    (upper ? bankU : bankL)[f] = to_h<H>(v);
+    const H h = to_h<H>(v);
+    hi[e] = h;
+    if (lo) lo[e] = to_h<H>(v - from_h<H>(h));
   }
 }
 
+// x (FP32, n2 x n1) -> 16-bit copies at pitch ld (hi, and lo = x - hi)
 template <typename H>
-__global__ void pack_kernel(const float* __restrict__ X, int n1, int n2, int ld, H* out) {
+__global__ void pack_kernel(const float* __restrict__ X, int n1, int n2, int ld, H* hi, H* lo) {
   const size_t N = (size_t)n1 * n2;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N;
        e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % n1), j = (int)(e / n1);
-    out[(size_t)j * ld + i] = to_h<H>(X[e]);
+    const float v = X[e];
+    const H h = to_h<H>(v);
+    hi[(size_t)j * ld + i] = h;
+    if (lo) lo[(size_t)j * ld + i] = to_h<H>(v - from_h<H>(h));
   }
 }
 
@@ -433,9 +569,12 @@ static EncodeTiled get_encoder() {
 }
 
 struct Maps {
-  CUtensorMap xa, xb, bank;
-  int rowL_x, rowU_x, rowL_y, rowU_y;
+  // [term hi / lo]: x-CTAs read X K-major (box 64 x 128), y-CTAs read the
+  // y-operand MN-major (box 64 x 64)
+  CUtensorMap ax[2], ay[2];
   int* err;
+  void *genx_hi, *genx_lo, *geny_hi, *geny_lo;
+  int glen_x, glen_y;
 };
 
 static int encode(CUtensorMap* m, CUtensorMapDataType dt, void* ptr, uint64_t d0, uint64_t d1,
@@ -457,42 +596,55 @@ int level_create(ToeplitzGemmLevel* L, int n1, int n2, int prec, bool mass) {
   L->n2 = n2;
   L->prec = prec;
   L->ld = (n1 + 63) / 64 * 64;
+  const bool split = prec == kBF16X3;
+  const int nt = split ? 2 : 1;
   const size_t xbytes = (size_t)n2 * L->ld * 2;
-  if (cudaMalloc(&L->xa, xbytes) != cudaSuccess) return 1;
-  if (cudaMemset(L->xa, 0, xbytes) != cudaSuccess) return 1;
-  if (mass) {
-    if (cudaMalloc(&L->xb, xbytes) != cudaSuccess) return 1;
-    if (cudaMemset(L->xb, 0, xbytes) != cudaSuccess) return 1;
+  void** bufs[4] = {&L->xa, &L->xa_lo, &L->xb, &L->xb_lo};
+  for (int b = 0; b < 4; ++b) {
+    const bool need = (b % 2 == 0 || split) && (b < 2 || mass);
+    if (!need) continue;
+    if (cudaMalloc(bufs[b], xbytes) != cudaSuccess) return 1;
+    if (cudaMemset(*bufs[b], 0, xbytes) != cudaSuccess) return 1;
   }
-  // bank tile counts: L tiles for delta = -128 .. (last output block start),
-  // U tiles for delta = 64 .. -(last K block start)
-  auto ntl = [](int n) { return ((n + BN - 1) / BN - 1) * (BN / BK) + 3; };
-  auto ntu = [](int n) { return (n + BK - 1) / BK + 1; };
-  const int tLx = ntl(n1), tUx = ntu(n1), tLy = ntl(n2), tUy = ntu(n2);
-  L->tiles_x = tLx + tUx;
-  L->tiles_y = tLy + tUy;
-  const size_t bank_rows = (size_t)(L->tiles_x + L->tiles_y) * BM;
-  if (cudaMalloc(&L->bank, bank_rows * BK * 2) != cudaSuccess) return 1;
   Maps hm;
+  std::memset(&hm, 0, sizeof(hm));
   const CUtensorMapDataType dt =
       prec == kFP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  int r = encode(&hm.xa, dt, L->xa, n1, n2, (uint64_t)L->ld * 2, BK, BM);
-  if (r) return r;
-  r = encode(&hm.xb, dt, mass ? L->xb : L->xa, n1, n2, (uint64_t)L->ld * 2, BK, BK);
-  if (r) return r;
-  r = encode(&hm.bank, dt, L->bank, BK, bank_rows, BK * 2, BK, BM);
-  if (r) return r;
-  hm.rowL_x = 0;
-  hm.rowU_x = tLx * BM;
-  hm.rowL_y = (tLx + tUx) * BM;
-  hm.rowU_y = (tLx + tUx + tLy) * BM;
+  for (int t = 0; t < nt; ++t) {
+    void* xa = t == 0 ? L->xa : L->xa_lo;
+    void* xb = mass ? (t == 0 ? L->xb : L->xb_lo) : xa;
+    int r = encode(&hm.ax[t], dt, xa, n1, n2, (uint64_t)L->ld * 2, BK, BM);
+    if (r) return r;
+    r = encode(&hm.ay[t], dt, xb, n1, n2, (uint64_t)L->ld * 2, 64, BK);
+    if (r) return r;
+  }
+  if (nt == 1) {
+    hm.ax[1] = hm.ax[0];
+    hm.ay[1] = hm.ay[0];
+  }
+  hm.glen_x = gen_len(n1);
+  hm.glen_y = gen_len(n2);
+  if (Cfg<1>::FIXED + gen_bytes(n1 > n2 ? n1 : n2) * (split ? 2 : 1) +
+          (split ? (size_t)Cfg<2>::STAGES * Cfg<2>::STAGE_BYTES - Cfg<1>::STAGES * Cfg<1>::STAGE_BYTES
+                 : 0) > 227 * 1024)
+    return 13;  // generator copies do not fit next to the pipeline
+  if (cudaMalloc(&hm.genx_hi, gen_bytes(n1)) != cudaSuccess) return 1;
+  if (cudaMalloc(&hm.geny_hi, gen_bytes(n2)) != cudaSuccess) return 1;
+  if (split) {
+    if (cudaMalloc(&hm.genx_lo, gen_bytes(n1)) != cudaSuccess) return 1;
+    if (cudaMalloc(&hm.geny_lo, gen_bytes(n2)) != cudaSuccess) return 1;
+  }
   if (cudaMalloc(&hm.err, sizeof(int)) != cudaSuccess) return 1;
   if (cudaMemset(hm.err, 0, sizeof(int)) != cudaSuccess) return 1;
-  Maps* hp = new Maps(hm);
-  L->maps = hp;
-  if (cudaFuncSetAttribute(toeplitz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SMEM_BYTES) != cudaSuccess)
-    return 12;
+  L->maps = new Maps(hm);
+  const void* kfun[4] = {(const void*)toeplitz_gemm_kernel<0, 1>,
+                         (const void*)toeplitz_gemm_kernel<1, 1>,
+                         (const void*)toeplitz_gemm_kernel<0, 2>,
+                         (const void*)toeplitz_gemm_kernel<1, 2>};
+  for (int k = 0; k < 4; ++k)
+    if (cudaFuncSetAttribute(kfun[k], cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+        cudaSuccess)
+      return 12;
   L->built = true;
   return 0;
 }
@@ -500,24 +652,53 @@ int level_create(ToeplitzGemmLevel* L, int n1, int n2, int prec, bool mass) {
 int level_setup(ToeplitzGemmLevel* L, const double* tx, const double* ty, cudaStream_t st) {
   if (!L->built) return 20;
   Maps* m = (Maps*)L->maps;
+  // FP16's 5-bit exponent would flush the far Toeplitz weights: scale by 2^10
   const float scale = L->prec == kFP16 ? 1024.f : 1.f;
-  const int tLx = m->rowU_x / BM, tUx = (m->rowL_y - m->rowU_x) / BM;
-  const int tLy = (m->rowU_y - m->rowL_y) / BM, tUy = L->tiles_y - tLy;
-  const size_t tile = (size_t)BM * BK;
   if (L->prec == kFP16) {
-    __half* b = (__half*)L->bank;
-    bank_kernel<__half><<<512, 256, 0, st>>>(tx, L->n1, tLx, tUx, scale, b, b + tLx * tile);
-    bank_kernel<__half><<<512, 256, 0, st>>>(ty, L->n2, tLy, tUy, scale,
-                                             b + (size_t)(tLx + tUx) * tile,
-                                             b + (size_t)(tLx + tUx + tLy) * tile);
+    generator_kernel<__half><<<8, 256, 0, st>>>(tx, L->n1, scale, (__half*)m->genx_hi, nullptr);
+    generator_kernel<__half><<<8, 256, 0, st>>>(ty, L->n2, scale, (__half*)m->geny_hi, nullptr);
   } else {
-    __nv_bfloat16* b = (__nv_bfloat16*)L->bank;
-    bank_kernel<__nv_bfloat16><<<512, 256, 0, st>>>(tx, L->n1, tLx, tUx, scale, b, b + tLx * tile);
-    bank_kernel<__nv_bfloat16><<<512, 256, 0, st>>>(ty, L->n2, tLy, tUy, scale,
-                                                    b + (size_t)(tLx + tUx) * tile,
-                                                    b + (size_t)(tLx + tUx + tLy) * tile);
+    generator_kernel<__nv_bfloat16><<<8, 256, 0, st>>>(tx, L->n1, scale,
+                                                       (__nv_bfloat16*)m->genx_hi,
+                                                       (__nv_bfloat16*)m->genx_lo);
+    generator_kernel<__nv_bfloat16><<<8, 256, 0, st>>>(ty, L->n2, scale,
+                                                       (__nv_bfloat16*)m->geny_hi,
+                                                       (__nv_bfloat16*)m->geny_lo);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : 21;
+}
+
+template <int NT>
+static void launch_pair(ToeplitzGemmLevel* L, Maps* m, const float* M, double cm,
+                        const float* dp, const float* dm, const float* ep, const float* em,
+                        float* kx, bool f16, cudaStream_t st) {
+  KParams kp;
+  kp.M = M;
+  kp.cm = (float)cm;
+  kp.n1 = L->n1;
+  kp.n2 = L->n2;
+  kp.inv_scale = f16 ? 1.f / 1024.f : 1.f;
+  kp.err = m->err;
+  kp.out = kx;
+  // x products: kx = cm M + dp (X A_x^T) + dm (X A_x)
+  kp.gen_hi = (const uint16_t*)m->genx_hi;
+  kp.gen_lo = (const uint16_t*)(NT == 2 ? m->genx_lo : m->genx_hi);
+  kp.glen = m->glen_x;
+  kp.c0 = dp;
+  kp.c1 = dm;
+  dim3 gx((L->n1 + BN - 1) / BN, (L->n2 + BM - 1) / BM);
+  toeplitz_gemm_kernel<0, NT><<<gx, NUM_THREADS, Cfg<NT>::FIXED + NT * gen_bytes(L->n1), st>>>(
+      m->ax[0], m->ax[1], kp, make_idesc(false, f16));
+  // y products (transposed tiles): kx += ep (A_y Y) + em (A_y^T Y)
+  kp.M = nullptr;
+  kp.gen_hi = (const uint16_t*)m->geny_hi;
+  kp.gen_lo = (const uint16_t*)(NT == 2 ? m->geny_lo : m->geny_hi);
+  kp.glen = m->glen_y;
+  kp.c0 = ep;
+  kp.c1 = em;
+  dim3 gy((L->n2 + BN - 1) / BN, (L->n1 + BM - 1) / BM);
+  toeplitz_gemm_kernel<1, NT><<<gy, NUM_THREADS, Cfg<NT>::FIXED + NT * gen_bytes(L->n2), st>>>(
+      m->ay[0], m->ay[1], kp, make_idesc(true, f16));
 }
 
 int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y, const float* M,
@@ -530,35 +711,20 @@ int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y,
   int g = (int)((N + 255) / 256);
   if (g > 152 * 16) g = 152 * 16;
   const bool two = L->xb != nullptr;
+  const bool split = L->prec == kBF16X3;
   if (L->prec == kFP16) {
-    pack_kernel<__half><<<g, 256, 0, st>>>(xin_x, n1, n2, L->ld, (__half*)L->xa);
-    if (two) pack_kernel<__half><<<g, 256, 0, st>>>(xin_y, n1, n2, L->ld, (__half*)L->xb);
+    pack_kernel<__half><<<g, 256, 0, st>>>(xin_x, n1, n2, L->ld, (__half*)L->xa, nullptr);
+    if (two) pack_kernel<__half><<<g, 256, 0, st>>>(xin_y, n1, n2, L->ld, (__half*)L->xb, nullptr);
   } else {
-    pack_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(xin_x, n1, n2, L->ld, (__nv_bfloat16*)L->xa);
+    pack_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(xin_x, n1, n2, L->ld, (__nv_bfloat16*)L->xa,
+                                                  (__nv_bfloat16*)(split ? L->xa_lo : nullptr));
     if (two)
-      pack_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(xin_y, n1, n2, L->ld,
-                                                    (__nv_bfloat16*)L->xb);
+      pack_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(xin_y, n1, n2, L->ld, (__nv_bfloat16*)L->xb,
+                                                    (__nv_bfloat16*)(split ? L->xb_lo : nullptr));
   }
-  KParams kp;
-  kp.M = M;
-  kp.cm = (float)cm;
-  kp.dp = dp;
-  kp.dm = dm;
-  kp.ep = ep;
-  kp.em = em;
-  kp.kx = kx;
-  kp.n1 = n1;
-  kp.n2 = n2;
-  kp.rowL_x = m->rowL_x;
-  kp.rowU_x = m->rowU_x;
-  kp.rowL_y = m->rowL_y;
-  kp.rowU_y = m->rowU_y;
-  kp.inv_scale = L->prec == kFP16 ? 1.f / 1024.f : 1.f;
-  kp.err = m->err;
   const bool f16 = L->prec == kFP16;
-  dim3 grid((n1 + BN - 1) / BN, (n2 + BM - 1) / BM);
-  toeplitz_gemm_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(
-      m->xa, m->xb, m->bank, kp, make_idesc(false, f16), make_idesc(true, f16));
+  if (split) launch_pair<2>(L, m, M, cm, dp, dm, ep, em, kx, f16, st);
+  else launch_pair<1>(L, m, M, cm, dp, dm, ep, em, kx, f16, st);
   return cudaGetLastError() == cudaSuccess ? 0 : 31;
 }
 
@@ -574,12 +740,17 @@ void level_destroy(ToeplitzGemmLevel* L) {
   if (L->maps) {
     Maps* m = (Maps*)L->maps;
     cudaFree(m->err);
+    cudaFree(m->genx_hi);
+    cudaFree(m->genx_lo);
+    cudaFree(m->geny_hi);
+    cudaFree(m->geny_lo);
     delete m;
   }
   cudaFree(L->xa);
+  cudaFree(L->xa_lo);
   cudaFree(L->xb);
-  cudaFree(L->bank);
-  L->xa = L->xb = L->bank = L->maps = nullptr;
+  cudaFree(L->xb_lo);
+  L->xa = L->xa_lo = L->xb = L->xb_lo = L->maps = nullptr;
   L->built = false;
 }
 

@@ -10,24 +10,30 @@ namespace tc {
 
 constexpr int kBF16 = 0;
 constexpr int kFP16 = 1;
+constexpr int kBF16X3 = 2;      // hi/lo BF16 split, three products
 constexpr int kMinGemmN = 127;  // smaller levels stay on CUDA cores
+// FDE_PATH_AUTO picks the tensor path only from this size up: one CTA owns a
+// 128 x 256 output tile, so n = 1023 launches 32 CTAs on 152 SMs and the FFT
+// path is faster there; n = 2047 launches 128.
+constexpr int kAutoGemmN = 1536;
 
 struct ToeplitzGemmLevel {
   int n1 = 0, n2 = 0, prec = kBF16;
   bool built = false;
   int ld = 0;            // pitch (elements) of the 16-bit operand copies
-  void* xa = nullptr;    // 16-bit copy of the x-pass operand, n2 rows x ld
-  void* xb = nullptr;    // 16-bit copy of the y-pass operand, n2 rows x ld
-  void* bank = nullptr;  // Toeplitz tile banks (x lower, x upper, y lower, y upper)
-  int tiles_x = 0, tiles_y = 0;
-  void* maps = nullptr;  // device copy of the tensor maps
+  void* xa = nullptr;     // 16-bit copy of the x-product operand, n2 rows x ld
+  void* xa_lo = nullptr;  // its low part (split precision)
+  void* xb = nullptr;     // 16-bit copy of the y-product operand (structured-Galerkin levels)
+  void* xb_lo = nullptr;
+  void* maps = nullptr;   // tensor maps, generator copies, error flag
 };
 
 // returns 0 on success
 int level_create(ToeplitzGemmLevel* L, int n1, int n2, int prec, bool mass);
 int level_setup(ToeplitzGemmLevel* L, const double* tx, const double* ty, cudaStream_t st);
 // kx = cm * M + dp (.) (X A_x^T) + dm (.) (X A_x) + ep (.) (A_y Y) + em (.) (A_y^T Y)
-// with X = xin_x, Y = xin_y (FP32, n2 x n1, unpadded)
+// with X = xin_x, Y = xin_y (FP32, n2 x n1, unpadded); two kernel launches plus
+// one or two operand-packing launches
 int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y, const float* M,
                    double cm, const float* dp, const float* dm, const float* ep, const float* em,
                    float* kx, cudaStream_t st);

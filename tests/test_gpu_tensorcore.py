@@ -15,7 +15,8 @@ from gpu_util import Case, dev, host
 
 pytestmark = pytest.mark.gpu
 
-U16 = {fde.FDE_PREC_BF16: 2.0 ** -8, fde.FDE_PREC_FP16: 2.0 ** -11}
+U16 = {fde.FDE_PREC_BF16: 2.0 ** -8, fde.FDE_PREC_FP16: 2.0 ** -11,
+       fde.FDE_PREC_BF16X3: 2.0 ** -16}
 
 
 def _abs_level(lev, X):
@@ -26,7 +27,7 @@ def _abs_level(lev, X):
                       A(lev.Bx), A(lev.By))
 
 
-@pytest.mark.parametrize("precision", [fde.FDE_PREC_BF16, fde.FDE_PREC_FP16])
+@pytest.mark.parametrize("precision", [fde.FDE_PREC_BF16, fde.FDE_PREC_FP16, fde.FDE_PREC_BF16X3])
 @pytest.mark.parametrize("precond", [fde.FDE_PRECOND_MG_SG, fde.FDE_PRECOND_MG_REDISC])
 @pytest.mark.parametrize("n1,n2", [(255, 255), (511, 255), (383, 767)])
 def test_gemm_level_apply(precision, precond, n1, n2):
@@ -64,14 +65,15 @@ def test_gemm_level_apply(precision, precond, n1, n2):
         fde.fde_destroy(h)
 
 
-@pytest.mark.parametrize("precision", [fde.FDE_PREC_BF16, fde.FDE_PREC_FP16])
+@pytest.mark.parametrize("precision", [fde.FDE_PREC_BF16, fde.FDE_PREC_FP16, fde.FDE_PREC_BF16X3])
 def test_mixed_solve_converges_to_fp64_residual(precision):
     # the reduced-precision V-cycle only preconditions: the FP64 FGMRES still
     # drives the true residual below rtol, and the solution matches the oracle's
     import torch
     from oracle.krylov import fgmres
     from oracle import multigrid as mg
-    case = Case(inputs.perturbed_power_law(), 255, precision=precision, rtol=1e-10)
+    case = Case(inputs.perturbed_power_law(), 255, precision=precision, rtol=1e-10,
+                toeplitz_path=fde.FDE_PATH_GEMM)
     h = case.handle()
     try:
         B = case.oracle_rhs()
