@@ -116,7 +116,7 @@ class ClockSampler:
 class Workload:
     """Device-resident inputs of the time loop and one solver handle."""
 
-    def __init__(self, precision, path=None, outer=None):
+    def __init__(self, precision, path=None, outer=None, precond=None, cycles=1):
         import torch
         from paper_1706_06844_gb300 import fde
         self.fde, self.torch = fde, torch
@@ -127,7 +127,8 @@ class Workload:
         a1, b1, a2, b2 = prob.domain
         kw = dict(alpha=prob.alpha, beta=prob.beta, qx=prob.qx, qy=prob.qy, a1=a1, b1=b1,
                   a2=a2, b2=b2, n1=n, n2=n, dt=self.dt, rtol=RTOL, restart=RESTART, maxit=2000,
-                  precond=fde.FDE_PRECOND_MG_SG, precision=precision)
+                  precond=fde.FDE_PRECOND_MG_SG if precond is None else precond,
+                  precision=precision, cycles=cycles)
         if path is not None:
             kw["toeplitz_path"] = path
         if outer is not None:
@@ -359,6 +360,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["bf16", "fp16", "fp32", "bf16x3"])
     ap.add_argument("--outer", default="df32", choices=["df32", "fp64"])
+    ap.add_argument("--precond", default="sg", choices=["sg", "redisc", "p2"],
+                    help="structured-Galerkin V-cycle, rediscretised V-cycle (P_MGM) or the "
+                         "band preconditioner P_2 with a Galerkin V-cycle")
+    ap.add_argument("--cycles", type=int, default=1, help="V-cycles per preconditioner application")
     args = ap.parse_args()
     if args.kernel:
         kernel_micro(args.kernel, args.reps)
@@ -385,7 +390,9 @@ def main():
     mixed = {"bf16": fde.FDE_PREC_BF16, "fp16": fde.FDE_PREC_FP16, "fp32": fde.FDE_PREC_FP32,
              "bf16x3": fde.FDE_PREC_BF16X3}[args.precision]
     outer = fde.FDE_OUTER_DF32 if args.outer == "df32" else fde.FDE_OUTER_FP64
-    w = Workload(mixed, outer=outer)
+    precond = {"sg": fde.FDE_PRECOND_MG_SG, "redisc": fde.FDE_PRECOND_MG_REDISC,
+               "p2": fde.FDE_PRECOND_P2}[args.precond]
+    w = Workload(mixed, outer=outer, precond=precond, cycles=args.cycles)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         ms, wall, its, launches = time_steps(w, args.steps, args.warmup, dist)
     if dist:
@@ -417,8 +424,15 @@ def main():
                 "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": f"f64 Krylov + {args.precision} V-cycle products", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": N_GRID, "restart": RESTART, "rtol": RTOL,
-                           "precond": "MG_SG",
+                "config": {"workload": WORKLOAD.replace(
+                               "structured-Galerkin V-cycle",
+                               {"sg": "structured-Galerkin V-cycle",
+                                "redisc": "rediscretised V-cycle (P_MGM)",
+                                "p2": "band preconditioner P_2 with a Galerkin V-cycle"}[args.precond]),
+                           "n": N_GRID, "restart": RESTART, "rtol": RTOL,
+                           "precond": {"sg": "MG_SG", "redisc": "MG_REDISC",
+                                       "p2": "P2"}[args.precond],
+                           "cycles": args.cycles,
                            "precision": f"{args.precision} V-cycle products (FP32 vectors), "
                                         f"{args.outer} FFT outer apply",
                            "l2": "inputs larger than L2 (Krylov basis 31 x 33.5 MB)",

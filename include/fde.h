@@ -52,6 +52,9 @@ extern "C" {
 #define FDE_PRECOND_NONE       0  /* plain GMRES */
 #define FDE_PRECOND_MG_SG      1  /* V-cycle, structured Galerkin coarse operators, R = P^T */
 #define FDE_PRECOND_MG_REDISC  2  /* V-cycle, rediscretised coarse operators, R = P^T / 4 (P_MGM, Sec. 4.2) */
+#define FDE_PRECOND_P2         3  /* band preconditioner P_2 (Sec. 4.3): Laplacian (alpha = beta = 2)
+                                     five-point operator with the problem's coefficients, one
+                                     Galerkin V-cycle (nine-point coarse stencils, R = P^T) */
 
 /* arithmetic of the preconditioner (the outer Krylov method is always FP64) */
 #define FDE_PREC_FP64          0  /* V-cycle in FP64 ("plain FP64" solver) */
@@ -93,6 +96,9 @@ typedef struct fde_params {
   int    precision;        /* FDE_PREC_* */
   int    toeplitz_path;    /* FDE_PATH_* */
   int    outer;            /* FDE_OUTER_* */
+  int    cycles;           /* V-cycles per preconditioner application (0 or 1: one; at most 4);
+                              cycle k + 1 corrects the residual of cycle k (Sec. 5.1 tries two
+                              for P_2) */
 } fde_params;
 
 typedef struct fde_stats {
@@ -106,7 +112,7 @@ typedef struct fde_handle fde_handle;
 
 /* Fill *p with defaults: alpha = beta = 1.5, q = 0, unit square, n = 63,
  * dt = h, rtol 1e-8, FGMRES(30), maxit 1000, MG_SG, nu = (1, 1), omega 0.7,
- * coarsest 8, FP64, AUTO path, FP64 outer apply. */
+ * coarsest 8, FP64, AUTO path, FP64 outer apply, one V-cycle. */
 void fde_default_params(fde_params* p);
 
 /* Create a solver for one grid (Sec. 2).  Checks the parameters, allocates

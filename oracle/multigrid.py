@@ -186,11 +186,11 @@ def exact_galerkin(K0, n1, n2, coarsest=8):
         px, py = prolongation_1d(m1), prolongation_1d(m2)
         Px.append(px)
         Py.append(py)
-        P = np.kron(py, px)
         if sp.issparse(K):
-            Ps = sp.csr_matrix(P)
+            Ps = sp.kron(sp.csr_matrix(py), sp.csr_matrix(px)).tocsr()
             K = (Ps.T @ K @ Ps).tocsr()
         else:
+            P = np.kron(py, px)
             K = P.T @ K @ P
         m1, m2 = coarse_size(m1), coarse_size(m2)
     return Hierarchy(levels, Px, Py, 1.0)

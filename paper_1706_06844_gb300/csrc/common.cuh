@@ -133,6 +133,29 @@ cudaError_t launch_coarse_inverse(const double* tx, const double* ty, int n1, in
 template <typename T>
 cudaError_t launch_coarse_solve(const double* inv, int N, const T* b, T* x, cudaStream_t st);
 
+// ---- nine-point stencil levels (P_2 of Sec. 4.3; layout S[o * N + j * n1 + i],
+// o = 3 (dy + 1) + (dx + 1), coefficients reaching outside the grid are zero)
+// level 0: P_2 = c I + (D+ + D-)(I (x) A2) + sigma (E+ + E-)(A2 (x) I), A2 = tridiag(-1, 2, -1)
+cudaError_t launch_p2_fields(const double* dp, const double* dm, const double* ep,
+                             const double* em, int n1, int n2, double c, double sigma, double* S,
+                             cudaStream_t st);
+// Galerkin coarse stencil P^T K P (bilinear P), fine n1 x n2 -> coarse m1 x m2 (FP64)
+cudaError_t launch_galerkin9(const double* Sf, int n1, int n2, double* Sc, int m1, int m2,
+                             cudaStream_t st);
+// ST = (T) S (skipped when ST is null), W = omega / diag
+template <typename T>
+cudaError_t launch_stencil_convert(const double* S, size_t N, double omega, T* ST, T* W,
+                                   cudaStream_t st);
+// mode 0: Y = K X; 1: Y = B - K X; 2: Y = X + W (B - K X). Y must not alias X.
+template <typename T>
+cudaError_t launch_stencil_apply(int mode, bool five, const T* S, int n1, int n2, const T* X,
+                                 const T* B, const T* W, T* Y, cudaStream_t st);
+template <typename T>
+cudaError_t launch_add(size_t N, const T* A, const T* B, T* Y, cudaStream_t st);
+// explicit inverse of a stencil level's dense operator (N = n1 n2 <= 1024; work 2 N^2)
+cudaError_t launch_stencil_inverse(const double* S, int n1, int n2, double* work, double* inv,
+                                   int* info, cudaStream_t st);
+
 // ---- Krylov (FP64)
 // partial dots: part[i * nb + blk] = sum over block chunk of V_i . w  (i < k)
 cudaError_t launch_dots(const double* V, size_t ldv, int k, const double* w, size_t N,

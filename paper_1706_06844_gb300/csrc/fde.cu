@@ -10,6 +10,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -195,6 +196,7 @@ struct MG : MGBase {
   int* info = nullptr;
   double rscale = 1.0;
   bool sg = true;
+  T *acc_x = nullptr, *acc_b = nullptr;  // further V-cycles: iterate and second rhs buffer
 
   int create(fde_handle* h) {
     const fde_params& p = h->p;
@@ -294,6 +296,10 @@ struct MG : MGBase {
     RCHK(h->alloc(&cwork, C.N * C.N * 2));
     for (int k = 0; k < 4; ++k) RCHK(h->alloc(&cf[k], C.N));
     RCHK(h->alloc(&info, 4));
+    if (p.cycles > 1) {
+      RCHK(h->alloc(&acc_x, lv[0].N));
+      RCHK(h->alloc(&acc_b, lv[0].N));
+    }
     return FDE_OK;
   }
 
@@ -427,6 +433,20 @@ struct MG : MGBase {
     Lv& L = lv[0];
     LCHK((launch_convert<double, T>(L.N, r, 1.0, L.b, h->st)));
     RCHK(cycle(h, 0));
+    const int cycles = h->p.cycles > 1 ? h->p.cycles : 1;
+    if (cycles > 1) {
+      // stationary iteration: z_{k+1} = z_k + V(r - K_0 z_k); r stays in `rhs`
+      T* rhs = L.b;
+      std::swap(L.b, acc_b);
+      for (int k = 1; k < cycles; ++k) {
+        CCHK(cudaMemcpyAsync(acc_x, L.x, L.N * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+        RCHK(products(h, 0, acc_x, L.kx));
+        LCHK(launch_level_epilogue<T>(1, L.N, L.kx, rhs, acc_x, L.W, L.b, h->st));
+        RCHK(cycle(h, 0));
+        LCHK(launch_add<T>(L.N, acc_x, L.x, L.x, h->st));
+      }
+      std::swap(L.b, acc_b);
+    }
     LCHK((launch_convert<T, double>(L.N, L.x, 1.0, z, h->st)));
     return FDE_OK;
   }
@@ -465,6 +485,171 @@ struct MG : MGBase {
     }
     LCHK((launch_convert<double, T>(L.N, x, 1.0, L.x, h->st)));
     RCHK(products(h, l, L.x, L.kx));
+    LCHK((launch_convert<T, double>(L.N, L.kx, 1.0, y, h->st)));
+    return FDE_OK;
+  }
+};
+
+// ============================================================================
+// P_2 (Sec. 4.3): five-point band operator with a Galerkin V-cycle. Every
+// level is a nine-point stencil (kernels_stencil.cu): level 0 is P_2 itself,
+// level l + 1 is P^T K_l P computed in FP64, the coarsest is inverted densely.
+
+template <typename T>
+struct StencilMG : MGBase {
+  struct Lv {
+    int n1, n2;
+    size_t N;
+    double* S64 = nullptr;  // FP64 stencil (Galerkin products, coarsest inverse)
+    T *S = nullptr, *W = nullptr, *x = nullptr, *b = nullptr, *kx = nullptr;
+  };
+  std::vector<Lv> lv;
+  double *inv = nullptr, *cwork = nullptr;
+  int* info = nullptr;
+  T *acc_x = nullptr, *acc_b = nullptr;
+
+  int create(fde_handle* h) {
+    const fde_params& p = h->p;
+    int m1 = h->n1, m2 = h->n2;
+    for (;;) {
+      Lv L;
+      L.n1 = m1;
+      L.n2 = m2;
+      L.N = (size_t)m1 * m2;
+      lv.push_back(L);
+      n1s.push_back(m1);
+      n2s.push_back(m2);
+      if (m1 <= p.coarsest_n || m2 <= p.coarsest_n) break;
+      if (!(m1 & 1) || !(m2 & 1))
+        return h->fail(FDE_ERR_UNSUPPORTED,
+                       "multigrid needs odd level sizes down to the coarsest grid (got %d x %d)",
+                       m1, m2);
+      m1 = (m1 - 1) / 2;
+      m2 = (m2 - 1) / 2;
+    }
+    if (lv.back().N > 1024)
+      return h->fail(FDE_ERR_UNSUPPORTED, "coarsest grid %d x %d exceeds 1024 unknowns",
+                     lv.back().n1, lv.back().n2);
+    for (size_t l = 0; l < lv.size(); ++l) {
+      Lv& L = lv[l];
+      RCHK(h->alloc(&L.S64, 9 * L.N));
+      RCHK(h->alloc(&L.x, L.N));
+      RCHK(h->alloc(&L.b, L.N));
+      RCHK(h->alloc(&L.kx, L.N));
+      RCHK(h->alloc(&L.W, L.N));
+      if (std::is_same<T, double>::value) L.S = reinterpret_cast<T*>(L.S64);
+      else RCHK(h->alloc(&L.S, 9 * L.N));
+    }
+    const Lv& C = lv.back();
+    RCHK(h->alloc(&inv, C.N * C.N));
+    RCHK(h->alloc(&cwork, C.N * C.N * 2));
+    RCHK(h->alloc(&info, 4));
+    if (p.cycles > 1) {
+      RCHK(h->alloc(&acc_x, lv[0].N));
+      RCHK(h->alloc(&acc_b, lv[0].N));
+    }
+    return FDE_OK;
+  }
+
+  int setup(fde_handle* h) override {
+    cudaStream_t st = h->st;
+    LCHK(launch_p2_fields(h->dpN, h->dmN, h->epN, h->emN, h->n1, h->n2, h->c, h->sigma,
+                          lv[0].S64, st));
+    for (size_t l = 1; l < lv.size(); ++l)
+      LCHK(launch_galerkin9(lv[l - 1].S64, lv[l - 1].n1, lv[l - 1].n2, lv[l].S64, lv[l].n1,
+                            lv[l].n2, st));
+    for (size_t l = 0; l < lv.size(); ++l) {
+      Lv& L = lv[l];
+      if (std::is_same<T, double>::value) {
+        // S aliases S64: only the Jacobi weights
+        LCHK((launch_stencil_convert<T>(L.S64, L.N, h->p.omega, nullptr, L.W, st)));
+      } else {
+        LCHK((launch_stencil_convert<T>(L.S64, L.N, h->p.omega, L.S, L.W, st)));
+      }
+    }
+    Lv& C = lv.back();
+    LCHK(launch_stencil_inverse(C.S64, C.n1, C.n2, cwork, inv, info, st));
+    int hinfo = 0;
+    CCHK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CCHK(cudaStreamSynchronize(st));
+    if (hinfo != 0) return h->fail(FDE_ERR_NONFINITE, "coarsest-grid matrix is singular");
+    return FDE_OK;
+  }
+
+  int apply(fde_handle* h, size_t l, int mode, const T* x, const T* b, T* y) {
+    Lv& L = lv[l];
+    const int pi = h->pbeg(FDE_KCLASS_LEVEL_APPLY);
+    LCHK(launch_stencil_apply<T>(mode, l == 0, L.S, L.n1, L.n2, x, b, L.W, y, h->st));
+    h->pend(pi);
+    return FDE_OK;
+  }
+
+  int cycle(fde_handle* h, size_t l) {
+    Lv& L = lv[l];
+    const fde_params& p = h->p;
+    cudaStream_t st = h->st;
+    if (l + 1 == lv.size()) {
+      const int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+      LCHK(launch_coarse_solve<T>(inv, (int)L.N, L.b, L.x, st));
+      h->pend(pi);
+      return FDE_OK;
+    }
+    int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+    if (p.nu_pre >= 1) LCHK(launch_mul<T>(L.N, L.W, L.b, L.x, st));
+    else CCHK(cudaMemsetAsync(L.x, 0, L.N * sizeof(T), st));
+    h->pend(pi);
+    for (int s = 1; s < p.nu_pre; ++s) {  // Jacobi sweeps ping-pong between x and kx
+      RCHK(apply(h, l, 2, L.x, L.b, L.kx));
+      std::swap(L.x, L.kx);
+    }
+    RCHK(apply(h, l, 1, L.x, L.b, L.kx));  // r = b - K x
+    pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+    LCHK(launch_restrict<T>(L.kx, L.n1, L.n2, 1.0, lv[l + 1].b, st));  // R = P^T
+    h->pend(pi);
+    RCHK(cycle(h, l + 1));
+    pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+    LCHK(launch_prolong_add<T>(lv[l + 1].x, L.n1, L.n2, L.x, st));
+    h->pend(pi);
+    for (int s = 0; s < p.nu_post; ++s) {
+      RCHK(apply(h, l, 2, L.x, L.b, L.kx));
+      std::swap(L.x, L.kx);
+    }
+    return FDE_OK;
+  }
+
+  int vcycle(fde_handle* h, const double* r, double* z) override {
+    Lv& L = lv[0];
+    LCHK((launch_convert<double, T>(L.N, r, 1.0, L.b, h->st)));
+    RCHK(cycle(h, 0));
+    const int cycles = h->p.cycles > 1 ? h->p.cycles : 1;
+    if (cycles > 1) {
+      // stationary iteration: z_{k+1} = z_k + V(r - K_0 z_k); r stays in `rhs`
+      T* rhs = L.b;
+      std::swap(L.b, acc_b);
+      for (int k = 1; k < cycles; ++k) {
+        CCHK(cudaMemcpyAsync(acc_x, L.x, L.N * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+        RCHK(apply(h, 0, 1, acc_x, rhs, L.b));
+        RCHK(cycle(h, 0));
+        LCHK(launch_add<T>(L.N, acc_x, L.x, L.x, h->st));
+      }
+      std::swap(L.b, acc_b);
+    }
+    LCHK((launch_convert<T, double>(L.N, L.x, 1.0, z, h->st)));
+    return FDE_OK;
+  }
+
+  int level_apply(fde_handle* h, int l, const double* x, double* y) override {
+    if (l < 0 || l >= (int)lv.size()) return h->fail(FDE_ERR_ARG, "level %d out of range", l);
+    Lv& L = lv[l];
+    if (l + 1 == (int)lv.size()) {
+      // the coarsest level applies its FP64 stencil (the cycle uses its inverse)
+      LCHK(launch_stencil_apply<double>(0, false, L.S64, L.n1, L.n2, x, nullptr, nullptr, y,
+                                        h->st));
+      return FDE_OK;
+    }
+    LCHK((launch_convert<double, T>(L.N, x, 1.0, L.x, h->st)));
+    LCHK(launch_stencil_apply<T>(0, l == 0, L.S, L.n1, L.n2, L.x, nullptr, nullptr, L.kx,
+                                 h->st));
     LCHK((launch_convert<T, double>(L.N, L.kx, 1.0, y, h->st)));
     return FDE_OK;
   }
@@ -657,6 +842,7 @@ void fde_default_params(fde_params* p) {
   p->precision = FDE_PREC_FP64;
   p->toeplitz_path = FDE_PATH_AUTO;
   p->outer = FDE_OUTER_FP64;
+  p->cycles = 1;
 }
 
 static int validate(const fde_params* p, std::string& why) {
@@ -671,7 +857,8 @@ static int validate(const fde_params* p, std::string& why) {
   if (!(p->rtol > 0.0) || !(p->rtol < 1.0)) return bad("rtol must be in (0, 1)");
   if (p->restart < 1 || p->restart > 64) return bad("restart must be in [1, 64]");
   if (p->maxit < 1) return bad("maxit must be >= 1");
-  if (p->precond < FDE_PRECOND_NONE || p->precond > FDE_PRECOND_MG_REDISC) return bad("unknown precond");
+  if (p->precond < FDE_PRECOND_NONE || p->precond > FDE_PRECOND_P2) return bad("unknown precond");
+  if (p->cycles < 0 || p->cycles > 4) return bad("cycles must be in [0, 4]");
   if (p->nu_pre < 0 || p->nu_pre > 4 || p->nu_post < 0 || p->nu_post > 4) return bad("nu in [0, 4]");
   if (!(p->omega > 0.0 && p->omega < 2.0)) return bad("omega must be in (0, 2)");
   if (p->coarsest_n < 1) return bad("coarsest_n must be >= 1");
@@ -766,7 +953,17 @@ int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
     RCHK(h->alloc(&h->hdev, p.restart + 4));
     RCHK(h->alloc(&h->h2dev, p.restart + 4));
     RCHK(h->alloc(&h->ydev, p.restart + 4));
-    if (p.precond != FDE_PRECOND_NONE) {
+    if (p.precond == FDE_PRECOND_P2) {
+      if (p.precision == FDE_PREC_FP64) {
+        auto* mg = new StencilMG<double>();
+        h->mg.reset(mg);
+        RCHK(mg->create(h));
+      } else {
+        auto* mg = new StencilMG<float>();
+        h->mg.reset(mg);
+        RCHK(mg->create(h));
+      }
+    } else if (p.precond != FDE_PRECOND_NONE) {
       if (p.precision == FDE_PREC_FP64) {
         auto* mg = new MG<double>();
         h->mg.reset(mg);

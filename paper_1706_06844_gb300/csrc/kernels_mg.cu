@@ -339,42 +339,14 @@ cudaError_t launch_level_fields(const double* dp, const double* dm, const double
   return cudaGetLastError();
 }
 
-// Dense coarsest operator
-//   K = c (By (x) Bx) + D+ (By (x) Ax) + D- (By (x) Ax^T) + E+ (Ay (x) Bx) + E- (Ay^T (x) Bx)
-// (E+- already scaled by sigma), inverted by Gauss-Jordan elimination with
-// partial pivoting in FP64 (one block; N <= 1024).
-__global__ void coarse_inverse_kernel(const double* __restrict__ tx, const double* __restrict__ ty,
-                                      int n1, int n2, double bx0, double bx1, double by0,
-                                      double by1, double c, const double* __restrict__ dp,
-                                      const double* __restrict__ dm,
-                                      const double* __restrict__ ep,
-                                      const double* __restrict__ em, double* A, double* inv,
-                                      int* info) {
-  const int N = n1 * n2, W2 = 2 * N;
+// Gauss-Jordan elimination with partial pivoting in FP64 on the augmented
+// N x 2N matrix [K | I] held in A (one block of 256 threads; N <= 1024): the
+// right half becomes K^{-1}, copied to inv. info = 1 if a pivot is zero.
+__device__ void gauss_jordan_block(double* A, int N, double* inv, int* info) {
+  const int W2 = 2 * N;
   __shared__ double red_v[256];
   __shared__ int red_i[256];
   __shared__ int piv_s;
-  auto T1 = [](const double* t, int n, int a, int b) -> double {  // Toeplitz entry (a, b)
-    const int d = a - b;
-    return (d >= -1 && d <= n - 1) ? t[d + 1] : 0.0;
-  };
-  auto B1 = [](double b0, double b1, int a, int b) -> double {
-    return a == b ? b0 : ((a - b == 1 || b - a == 1) ? b1 : 0.0);
-  };
-  for (int e = threadIdx.x; e < N * W2; e += blockDim.x) {
-    const int r = e / W2, col = e % W2;
-    double v;
-    if (col < N) {
-      const int j = r / n1, i = r % n1, jj = col / n1, ii = col % n1;
-      const double byv = B1(by0, by1, j, jj), bxv = B1(bx0, bx1, i, ii);
-      v = c * byv * bxv + dp[r] * byv * T1(tx, n1, i, ii) + dm[r] * byv * T1(tx, n1, ii, i) +
-          ep[r] * T1(ty, n2, j, jj) * bxv + em[r] * T1(ty, n2, jj, j) * bxv;
-    } else {
-      v = (col - N == r) ? 1.0 : 0.0;
-    }
-    A[e] = v;
-  }
-  __syncthreads();
   int ok = 1;
   for (int k = 0; k < N; ++k) {
     double best = -1.0;
@@ -425,6 +397,41 @@ __global__ void coarse_inverse_kernel(const double* __restrict__ tx, const doubl
   if (threadIdx.x == 0) *info = ok ? 0 : 1;
 }
 
+// Dense coarsest operator
+//   K = c (By (x) Bx) + D+ (By (x) Ax) + D- (By (x) Ax^T) + E+ (Ay (x) Bx) + E- (Ay^T (x) Bx)
+// (E+- already scaled by sigma), inverted by Gauss-Jordan elimination.
+__global__ void coarse_inverse_kernel(const double* __restrict__ tx, const double* __restrict__ ty,
+                                      int n1, int n2, double bx0, double bx1, double by0,
+                                      double by1, double c, const double* __restrict__ dp,
+                                      const double* __restrict__ dm,
+                                      const double* __restrict__ ep,
+                                      const double* __restrict__ em, double* A, double* inv,
+                                      int* info) {
+  const int N = n1 * n2, W2 = 2 * N;
+  auto T1 = [](const double* t, int n, int a, int b) -> double {  // Toeplitz entry (a, b)
+    const int d = a - b;
+    return (d >= -1 && d <= n - 1) ? t[d + 1] : 0.0;
+  };
+  auto B1 = [](double b0, double b1, int a, int b) -> double {
+    return a == b ? b0 : ((a - b == 1 || b - a == 1) ? b1 : 0.0);
+  };
+  for (int e = threadIdx.x; e < N * W2; e += blockDim.x) {
+    const int r = e / W2, col = e % W2;
+    double v;
+    if (col < N) {
+      const int j = r / n1, i = r % n1, jj = col / n1, ii = col % n1;
+      const double byv = B1(by0, by1, j, jj), bxv = B1(bx0, bx1, i, ii);
+      v = c * byv * bxv + dp[r] * byv * T1(tx, n1, i, ii) + dm[r] * byv * T1(tx, n1, ii, i) +
+          ep[r] * T1(ty, n2, j, jj) * bxv + em[r] * T1(ty, n2, jj, j) * bxv;
+    } else {
+      v = (col - N == r) ? 1.0 : 0.0;
+    }
+    A[e] = v;
+  }
+  __syncthreads();
+  gauss_jordan_block(A, N, inv, info);
+}
+
 cudaError_t launch_coarse_inverse(const double* tx, const double* ty, int n1, int n2,
                                   double bx0, double bx1, double by0, double by1, double c,
                                   const double* dp, const double* dm, const double* ep,
@@ -432,6 +439,34 @@ cudaError_t launch_coarse_inverse(const double* tx, const double* ty, int n1, in
                                   cudaStream_t st) {
   coarse_inverse_kernel<<<1, 256, 0, st>>>(tx, ty, n1, n2, bx0, bx1, by0, by1, c, dp, dm, ep, em,
                                            work, inv, info);
+  return cudaGetLastError();
+}
+
+// inverse of the dense N x N operator of a nine-point stencil level (stored by
+// rows, see kernels_stencil.cu): assemble [K | I], then Gauss-Jordan
+__global__ void stencil_inverse_kernel(const double* __restrict__ S, int n1, int n2, double* A,
+                                       double* inv, int* info) {
+  const int N = n1 * n2, W2 = 2 * N;
+  for (int e = threadIdx.x; e < N * W2; e += blockDim.x) {
+    const int r = e / W2, col = e % W2;
+    double v;
+    if (col < N) {
+      const int dj = col / n1 - r / n1, di = col % n1 - r % n1;
+      v = (dj >= -1 && dj <= 1 && di >= -1 && di <= 1)
+              ? S[(size_t)((dj + 1) * 3 + di + 1) * N + r]
+              : 0.0;
+    } else {
+      v = (col - N == r) ? 1.0 : 0.0;
+    }
+    A[e] = v;
+  }
+  __syncthreads();
+  gauss_jordan_block(A, N, inv, info);
+}
+
+cudaError_t launch_stencil_inverse(const double* S, int n1, int n2, double* work, double* inv,
+                                   int* info, cudaStream_t st) {
+  stencil_inverse_kernel<<<1, 256, 0, st>>>(S, n1, n2, work, inv, info);
   return cudaGetLastError();
 }
 

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libfde.so")
 
 FDE_OK, FDE_ERR_ARG, FDE_ERR_NOT_CONVERGED, FDE_ERR_NONFINITE = 0, 1, 2, 3
 FDE_ERR_CUDA, FDE_ERR_TIMEOUT, FDE_ERR_UNSUPPORTED = 4, 5, 6
-FDE_PRECOND_NONE, FDE_PRECOND_MG_SG, FDE_PRECOND_MG_REDISC = 0, 1, 2
+FDE_PRECOND_NONE, FDE_PRECOND_MG_SG, FDE_PRECOND_MG_REDISC, FDE_PRECOND_P2 = 0, 1, 2, 3
 FDE_PREC_FP64, FDE_PREC_FP32, FDE_PREC_BF16, FDE_PREC_FP16, FDE_PREC_BF16X3 = 0, 1, 2, 3, 4
 FDE_PATH_AUTO, FDE_PATH_GEMM, FDE_PATH_FFT, FDE_PATH_DIRECT = 0, 1, 2, 3
 FDE_OUTER_FP64, FDE_OUTER_DF32 = 0, 1
@@ -33,7 +33,7 @@ class fde_params(ctypes.Structure):
                 ("precond", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("omega", ctypes.c_double), ("coarsest_n", ctypes.c_int),
                 ("precision", ctypes.c_int), ("toeplitz_path", ctypes.c_int),
-                ("outer", ctypes.c_int)]
+                ("outer", ctypes.c_int), ("cycles", ctypes.c_int)]
 
 
 class fde_stats(ctypes.Structure):

@@ -73,6 +73,8 @@ class Case:
         from oracle import multigrid as mg
         p = self.params
         c, s = self.sc["c"], self.sc["sigma"]
+        if p.precond == fde.FDE_PRECOND_P2:
+            return mg.band_p2(self.n1, self.n2, c, s, self.coef_new, p.coarsest_n)
         if p.precond == fde.FDE_PRECOND_MG_SG:
             return mg.structured_galerkin(self.wx, self.wy, self.n1, self.n2, c, s,
                                           self.coef_new, p.coarsest_n)

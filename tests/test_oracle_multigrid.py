@@ -170,3 +170,98 @@ def test_rediscretised_level_is_scheme_on_coarse_grid():
     M1 = assemble_M(toeplitz_A(wx, nc), toeplitz_A(wy, nc), s1["c"], s1["sigma"], *cfc)
     np.testing.assert_allclose(hier.levels[1].dense(), (s1["r"] / s0["r"]) * M1, rtol=1e-13, atol=1e-14)
     assert hier.rscale == 0.25
+
+
+# ----------------------------------------------------------------------------
+# P_2 (Sec. 4.3): the band preconditioner and its Galerkin hierarchy
+
+def test_p2_constant_coefficients_spectrum():
+    # unit coefficients: P_2 = c I + 2 (I (x) L) + 2 sigma (L (x) I) with L the
+    # Dirichlet Laplacian tridiag(-1, 2, -1), eigenvalues 4 sin^2(k pi / (2 (n + 1)))
+    n1, n2, c, sigma = 9, 6, 0.37, 1.9
+    ones = np.ones((n2, n1))
+    K = mg.band_p2_matrix(n1, n2, c, sigma, (ones, ones, ones, ones)).toarray()
+    lam = lambda n: 4 * np.sin(np.arange(1, n + 1) * np.pi / (2 * (n + 1))) ** 2
+    ev = (c + 2 * lam(n1)[None, :] + 2 * sigma * lam(n2)[:, None]).ravel()
+    np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(K)), np.sort(ev), rtol=1e-12)
+    # five nonzero diagonals (Sec. 4.3), at offsets 0, +-1 and +-n1
+    offs = {j - i for i, j in zip(*np.nonzero(K))}
+    assert offs == {0, 1, -1, n1, -n1}
+
+
+def test_p2_galerkin_level_constant_coefficients_closed_form():
+    # for linear interpolation P: P^T P = B = tridiag(1/4, 3/2, 1/4) and
+    # P^T L P = L / 2 (the coarse Laplacian), so with unit coefficients level 1
+    # is c (B (x) B) + (B (x) L) + sigma (L (x) B): a nine-point stencil
+    n, c, sigma = 15, 0.41, 1.3
+    ones = np.ones((n, n))
+    h = mg.band_p2(n, n, c, sigma, (ones, ones, ones, ones))
+    nc = 7
+    B = 1.5 * np.eye(nc) + 0.25 * (np.eye(nc, k=1) + np.eye(nc, k=-1))
+    L = 2 * np.eye(nc) - np.eye(nc, k=1) - np.eye(nc, k=-1)
+    K1 = c * np.kron(B, B) + np.kron(B, L) + sigma * np.kron(L, B)
+    np.testing.assert_allclose(h.levels[1].dense(), K1, rtol=1e-13, atol=1e-14)
+    assert len(h.levels) == 2 and h.rscale == 1.0
+
+
+def test_p2_galerkin_level_is_nine_point_with_variable_coefficients():
+    n = 31
+    cf = tuple(rng.uniform(0.5, 2, (n, n)) for _ in range(4))
+    h = mg.band_p2(n, n, 0.3, 1.7, cf)
+    for lev in h.levels[1:]:
+        K = lev.dense()
+        r, q = np.nonzero(K)
+        dj = q // lev.n1 - r // lev.n1
+        di = q % lev.n1 - r % lev.n1
+        assert np.abs(dj).max() == 1 and np.abs(di).max() == 1
+        assert np.all(np.diag(K) > 0)
+
+
+@pytest.mark.parametrize("idx", [0, 1])
+def test_p2_exact_inverse_counts_table1(idx):
+    # Table 1's column for P_2 solved directly (Sec. 5.1): left GMRES(20), tol 1e-7
+    import json
+    import os
+    import scipy.sparse.linalg as spla
+    from paper_1706_06844_gb300 import inputs
+    from oracle.operator import cn_scalars, rhs
+    from oracle.krylov import gmres_left
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+    t1 = gold["table1_example1"]
+    n = t1["n"][idx]
+    pb = inputs.example1()
+    X, Y, hx, hy = pb.grid(n, n)
+    dt = 1.0 / n
+    wx, wy = wsgd_weights(pb.alpha, n), wsgd_weights(pb.beta, n)
+    sc = cn_scalars(pb.alpha, pb.beta, hx, hy, dt)
+    c, s = sc["c"], sc["sigma"]
+    U = pb.exact(X, Y, 0.0)
+    its = []
+    for m in range(1, n + 1):
+        co, cn = pb.coefficients(X, Y, (m - 1) * dt), pb.coefficients(X, Y, m * dt)
+        B = rhs(U, wx, wy, c, s, *co, pb.source(X, Y, (m - 0.5) * dt), hx, pb.alpha)
+        lu = spla.splu(mg.band_p2_matrix(n, n, c, s, cn).tocsc())
+        prec = lambda R: lu.solve(np.asarray(R).ravel()).reshape(n, n)
+        U, k, rel, ok = gmres_left(lambda Z: apply_M(Z, wx, wy, c, s, *cn), B, prec, 20, 1e-7)
+        its.append(k)
+    assert abs(np.mean(its) - t1["p2_exact"][idx]) <= 1.0, its
+
+
+def test_p2_two_cycles_beat_one():
+    # Sec. 5.1: two V-cycles per application of P_2 cut the GMRES count
+    from oracle.timeloop import make_preconditioner
+    n = 63
+    al, be = 1.8, 1.6
+    wx, wy = wsgd_weights(al, n), wsgd_weights(be, n)
+    X, Y = np.meshgrid(np.arange(1, n + 1) / (n + 1), np.arange(1, n + 1) / (n + 1))
+    cf = (1 + X, 2 - X, 1 + Y, 2 - Y)
+    sc = {"c": 0.2, "sigma": 1.1}
+    A = lambda Z: apply_M(Z, wx, wy, 0.2, 1.1, *cf)
+    b = rng.standard_normal((n, n))
+    counts = []
+    for cycles in (1, 2):
+        prec, _ = make_preconditioner("p2", al, be, wx, wy, n, n, sc, cf, omega=1.0, cycles=cycles)
+        x, its, rel, ok = fgmres(A, b, prec, 60, 1e-8)
+        assert ok
+        counts.append(its)
+    assert counts[1] < counts[0], counts
