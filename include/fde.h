@@ -198,6 +198,33 @@ int fde_profile_query(fde_handle* h, int kclass, long long* launches, double* ms
 /* Total kernels this handle has launched. */
 long long fde_launch_count(const fde_handle* h);
 
+/* Batch of independent problems (Sec. 2's scheme on each, sizes, orders and
+ * coefficients may all differ), stepped concurrently: up to 16 host worker
+ * threads, each with its own CUDA stream, run disjoint subsets of the
+ * problems (largest first).  params[0..count) are copied; problem i gets a
+ * handle of its own (fde_batch_handle) on which the caller sets coefficients
+ * or state as for a single problem.  Work of fde_batch_step starts after the
+ * work already enqueued on `stream` and `stream` waits for all of it before
+ * anything enqueued later; the call returns when every solve has finished.
+ * The batch owns its handles; do not destroy them separately.  Errors:
+ * FDE_ERR_ARG (null params, count <= 0), or the first failing problem's
+ * fde_create status; message via fde_last_error(NULL). */
+typedef struct fde_batch fde_batch;
+int fde_batch_create(const fde_params* params, int count, void* stream, fde_batch** out);
+void fde_batch_destroy(fde_batch* b);
+int fde_batch_size(const fde_batch* b);
+/* Handle of problem i (NULL when i is out of range). */
+fde_handle* fde_batch_handle(fde_batch* b, int i);
+/* One CN step of every problem i: fde_step(handle i, u_prev[i], v_half[i],
+ * u_next[i], st + i).  The three arrays hold `count` DEVICE pointers (host
+ * arrays of device pointers); st may be NULL or hold `count` entries.  Every
+ * problem is stepped even when another fails; returns FDE_OK or the status of
+ * the lowest-numbered failing problem (fde_last_error(NULL) names it, and
+ * fde_batch_status gives each problem's own status). */
+int fde_batch_step(fde_batch* b, const double* const* u_prev, const double* const* v_half,
+                   double* const* u_next, fde_stats* st);
+int fde_batch_status(const fde_batch* b, int i);
+
 /* y = M x (Eq. M) with the given coefficients (device arrays d+, d-, e+, e-,
  * n2 x n1, as for fde_set_coefficients) in FP64, WITHOUT a handle and WITHOUT
  * allocating device memory: for callers that cannot allocate GPU memory (the

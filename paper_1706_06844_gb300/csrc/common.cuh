@@ -160,9 +160,10 @@ cudaError_t launch_stencil_inverse(const double* S, int n1, int n2, double* work
 // partial dots: part[i * nb + blk] = sum over block chunk of V_i . w  (i < k)
 cudaError_t launch_dots(const double* V, size_t ldv, int k, const double* w, size_t N,
                         double* part, int nb, cudaStream_t st);
-// w -= sum_i h_i V_i, then partial dots of the new w with V_i (i < k) and (slot k) with itself
+// w -= sum_i h_i V_i (i < k); mode 1: partial sums of |w_new|^2 into part[blk];
+// mode 2 (k <= 16): partial dots V_i . w_new into part[i * nb + blk]
 cudaError_t launch_axpy_dots(const double* V, size_t ldv, int k, const double* h, double* w,
-                             size_t N, double* part, int nb, int with_dots, cudaStream_t st);
+                             size_t N, double* part, int nb, int mode, cudaStream_t st);
 // out[i] = sum_b part[i * nb + b] (+ out[i] if add), i < k (one block)
 cudaError_t launch_reduce(const double* part, int k, int nb, double* out, int add,
                           cudaStream_t st);

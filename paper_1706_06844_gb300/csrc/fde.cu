@@ -747,12 +747,18 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
       double* w = h->V + (size_t)(j + 1) * N;
       RCHK(precond(h, Vj, Zj));
       RCHK(outer_apply(h, Zj, w, false));
-      // classical Gram-Schmidt, twice (CGS2)
+      // classical Gram-Schmidt, twice (CGS2); for 9 <= j + 1 <= 16 the first
+      // subtraction and the second projection share one pass over V (measured
+      // faster there; outside that range the two separate passes are)
       int pi = h->pbeg(FDE_KCLASS_KRYLOV);
       LCHK(launch_dots(h->V, N, j + 1, w, N, h->part, h->nb, h->st));
       LCHK(launch_reduce(h->part, j + 1, h->nb, h->hdev, 0, h->st));
-      LCHK(launch_axpy_dots(h->V, N, j + 1, h->hdev, w, N, h->part, h->nb, 0, h->st));
-      LCHK(launch_dots(h->V, N, j + 1, w, N, h->part, h->nb, h->st));
+      if (j + 1 >= 9 && j + 1 <= 16) {
+        LCHK(launch_axpy_dots(h->V, N, j + 1, h->hdev, w, N, h->part, h->nb, 2, h->st));
+      } else {
+        LCHK(launch_axpy_dots(h->V, N, j + 1, h->hdev, w, N, h->part, h->nb, 0, h->st));
+        LCHK(launch_dots(h->V, N, j + 1, w, N, h->part, h->nb, h->st));
+      }
       LCHK(launch_reduce(h->part, j + 1, h->nb, h->h2dev, 0, h->st));
       LCHK(launch_reduce(h->part, j + 1, h->nb, h->hdev, 1, h->st));
       LCHK(launch_axpy_dots(h->V, N, j + 1, h->h2dev, w, N, h->part, h->nb, 1, h->st));

@@ -62,7 +62,7 @@ cudaError_t launch_dots(const double* V, size_t ldv, int k, const double* w, siz
   return cudaGetLastError();
 }
 
-// w -= sum_{i<k} h_i V_i ; with_dots: also partial sums of w_new . w_new into part[0]
+// w -= sum_{i<k} h_i V_i ; with_norm: also partial sums of w_new . w_new into part[blk]
 __global__ void __launch_bounds__(KT) axpy_kernel(const double* __restrict__ V, size_t ldv, int k,
                                                   const double* __restrict__ h, double* w,
                                                   size_t N, double* part, int nb, int with_norm) {
@@ -85,10 +85,56 @@ __global__ void __launch_bounds__(KT) axpy_kernel(const double* __restrict__ V, 
   }
 }
 
+// w <- w - sum_{i<k} h_i V_i, then partial dots V_i . w_new (k <= KMAX): the
+// k values V_i[e] are loaded once into registers and used by both steps, so
+// the subtraction of the first Gram-Schmidt pass and the projection of the
+// second read V from memory once.
+template <int KMAX>
+__global__ void __launch_bounds__(KT) axpy_proj_kernel(const double* __restrict__ V, size_t ldv,
+                                                       int k, const double* __restrict__ h,
+                                                       double* w, size_t N, double* part, int nb) {
+  __shared__ double hs[KMAX];
+  __shared__ double red[KMAX * (KT / 32) + KMAX];
+  for (int i = threadIdx.x; i < KMAX; i += KT) hs[i] = i < k ? h[i] : 0.0;
+  __syncthreads();
+  const size_t chunk = (N + nb - 1) / nb;
+  const size_t lo = blockIdx.x * chunk, hi = lo + chunk < N ? lo + chunk : N;
+  double acc[KMAX];
+#pragma unroll
+  for (int g = 0; g < KMAX; ++g) acc[g] = 0.0;
+  for (size_t e = lo + threadIdx.x; e < hi; e += KT) {
+    double v[KMAX];
+#pragma unroll
+    for (int g = 0; g < KMAX; ++g) v[g] = g < k ? V[(size_t)g * ldv + e] : 0.0;
+    double we = w[e];
+#pragma unroll
+    for (int g = 0; g < KMAX; ++g) we -= hs[g] * v[g];
+    w[e] = we;
+#pragma unroll
+    for (int g = 0; g < KMAX; ++g) acc[g] += v[g] * we;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < KMAX; ++g) {
+    const double t = warp_sum(acc[g]);
+    if (lane == 0) red[g * (KT / 32) + wid] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double t = 0.0;
+    for (int q = 0; q < KT / 32; ++q) t += red[threadIdx.x * (KT / 32) + q];
+    part[(size_t)threadIdx.x * nb + blockIdx.x] = t;
+  }
+}
+
 cudaError_t launch_axpy_dots(const double* V, size_t ldv, int k, const double* h, double* w,
-                             size_t N, double* part, int nb, int with_norm, cudaStream_t st) {
-  if (k > 128) return cudaErrorInvalidValue;
-  axpy_kernel<<<nb, KT, 0, st>>>(V, ldv, k, h, w, N, part, nb, with_norm);
+                             size_t N, double* part, int nb, int mode, cudaStream_t st) {
+  if (k > 128 || (mode == 2 && k > 16)) return cudaErrorInvalidValue;
+  if (mode == 2) {
+    axpy_proj_kernel<16><<<nb, KT, 0, st>>>(V, ldv, k, h, w, N, part, nb);
+  } else {
+    axpy_kernel<<<nb, KT, 0, st>>>(V, ldv, k, h, w, N, part, nb, mode);
+  }
   return cudaGetLastError();
 }
 

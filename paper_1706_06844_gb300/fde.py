@@ -68,6 +68,14 @@ SIGNATURES = {
     "fde_launch_count": (ctypes.c_longlong, [_VP]),
     "fde_apply_noalloc": (ctypes.c_int, [ctypes.POINTER(fde_params), _DP, _DP, _DP, _DP, _DP,
                                          _DP, _VP]),
+    "fde_batch_create": (ctypes.c_int, [ctypes.POINTER(fde_params), ctypes.c_int, _VP,
+                                        ctypes.POINTER(_VP)]),
+    "fde_batch_destroy": (None, [_VP]),
+    "fde_batch_size": (ctypes.c_int, [_VP]),
+    "fde_batch_handle": (_VP, [_VP, ctypes.c_int]),
+    "fde_batch_step": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                      ctypes.POINTER(_VP), ctypes.POINTER(fde_stats)]),
+    "fde_batch_status": (ctypes.c_int, [_VP, ctypes.c_int]),
 }
 
 
@@ -235,3 +243,50 @@ def params(**kw):
             raise KeyError(k)
         setattr(p, k, v)
     return p
+
+
+# ---------------------------------------------------------------- batches
+
+def fde_batch_create(params_list, stream=0):
+    """One batch over a list of fde_params (copied)."""
+    n = len(params_list)
+    arr = (fde_params * n)(*params_list)
+    b = _VP()
+    rc = lib().fde_batch_create(arr, n, ctypes.c_void_p(stream), ctypes.byref(b))
+    if rc != FDE_OK:
+        raise FDEError(rc, lib().fde_last_error(None).decode())
+    return b
+
+
+def fde_batch_destroy(b):
+    lib().fde_batch_destroy(b)
+
+
+def fde_batch_size(b):
+    return lib().fde_batch_size(b)
+
+
+def fde_batch_handle(b, i):
+    h = lib().fde_batch_handle(b, i)
+    if not h:
+        raise FDEError(FDE_ERR_ARG, f"no problem {i} in the batch")
+    return _VP(h)
+
+
+def fde_batch_status(b, i):
+    return lib().fde_batch_status(b, i)
+
+
+def fde_batch_step(b, u_prev, v_half, u_next, allow_not_converged=False):
+    """Step every problem: u_prev, v_half, u_next are sequences of device
+    arrays (one per problem). Returns the list of fde_stats."""
+    n = fde_batch_size(b)
+    if not (len(u_prev) == len(v_half) == len(u_next) == n):
+        raise FDEError(FDE_ERR_ARG, f"expected {n} arrays per argument")
+    P = lambda xs: (_VP * n)(*[_ptr(x) for x in xs])
+    st = (fde_stats * n)()
+    rc = lib().fde_batch_step(b, P(u_prev), P(v_half), P(u_next), st)
+    ok = (FDE_OK, FDE_ERR_NOT_CONVERGED) if allow_not_converged else (FDE_OK,)
+    if rc not in ok:
+        raise FDEError(rc, lib().fde_last_error(None).decode())
+    return list(st)

@@ -46,3 +46,19 @@ def test_argument_errors_without_gpu():
         with pytest.raises(fde.FDEError) as e:
             fde.fde_create(fde.params(**kw))
         assert e.value.code == fde.FDE_ERR_ARG, kw
+    for kw in [dict(cycles=5), dict(cycles=-1)]:
+        with pytest.raises(fde.FDEError) as e:
+            fde.fde_create(fde.params(**kw))
+        assert e.value.code == fde.FDE_ERR_ARG, kw
+
+
+def test_batch_argument_errors_without_gpu():
+    # fde_batch_create rejects an empty batch before any CUDA call
+    b = ctypes.c_void_p()
+    assert fde.lib().fde_batch_create(None, 1, None, ctypes.byref(b)) == fde.FDE_ERR_ARG
+    p = (fde.fde_params * 1)(fde.fde_default_params())
+    assert fde.lib().fde_batch_create(p, 0, None, ctypes.byref(b)) == fde.FDE_ERR_ARG
+    assert not b.value
+    assert fde.fde_batch_size(None) == 0
+    assert fde.fde_batch_status(None, 0) == fde.FDE_ERR_ARG
+    assert fde.lib().fde_batch_step(None, None, None, None, None) == fde.FDE_ERR_ARG
