@@ -347,6 +347,91 @@ def kernel_micro(kind, reps):
     w.close()
 
 
+BATCH_COUNT = 256
+BATCH_METRIC = "CN-WSGD problem-steps/s, 256 independent problems (n in {63,127,255,511}), rtol 1e-8"
+BATCH_WORKLOAD = ("256 problems, seed 1706069: n uniform over {63,127,255,511}, alpha, beta ~ "
+                  "U(1.1,1.9), WSGD q in {0,-1} (-1 below gamma_0), coefficients exp(ln2 psi) in "
+                  "[0.5,2] with psi a smooth seeded field, dt=h, FGMRES(30) + structured-Galerkin "
+                  "FP32 V-cycle, double-float outer apply, rtol 1e-8")
+
+
+def run_batch(args, rank, world, dist):
+    """Every rank steps its share of the 256 problems (no data-path collective);
+    value = all problem-steps of all ranks / the slowest rank's time."""
+    import torch
+    from paper_1706_06844_gb300 import fde, inputs, shard
+    probs = inputs.random_batch(BATCH_COUNT)
+    mine = shard.shard([shard.problem_cost(n, n) for n, _ in probs], rank, world)
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    params, coef, u, base, dts = [], [], [], [], []
+    for i in mine:
+        n, pb = probs[i]
+        X, Y, hx, hy = pb.grid(n, n)
+        a1, b1, a2, b2 = pb.domain
+        params.append(fde.params(alpha=pb.alpha, beta=pb.beta, qx=pb.qx, qy=pb.qy, a1=a1, b1=b1,
+                                 a2=a2, b2=b2, n1=n, n2=n, dt=hx, rtol=RTOL, restart=RESTART,
+                                 maxit=2000, precond=fde.FDE_PRECOND_MG_SG,
+                                 precision=fde.FDE_PREC_FP32, outer=fde.FDE_OUTER_DF32))
+        coef.append([d(f) for f in pb.coefficients(X, Y, 0.0)])
+        u.append(d(pb.exact(X, Y, 0.0)))
+        # time-independent coefficients: the manufactured source is exp(-t) v(0)
+        base.append(d(pb.source(X, Y, 0.0)))
+        dts.append(hx)
+    b = fde.fde_batch_create(params)
+    for k in range(len(mine)):
+        h = fde.fde_batch_handle(b, k)
+        fde.fde_set_coefficients(h, fde.FDE_COEF_NEW, *coef[k])
+        fde.fde_set_coefficients(h, fde.FDE_COEF_OLD, *coef[k])
+    total = args.warmup + args.steps
+    src = [[base[k] * float(np.exp(-(m - 0.5) * dts[k])) for k in range(len(mine))]
+           for m in range(1, total + 1)]
+    nxt = [torch.empty_like(x) for x in u]
+    its = []
+
+    def step(m):
+        nonlocal u, nxt
+        st = fde.fde_batch_step(b, u, src[m - 1], nxt)
+        its.append(sum(s.iterations for s in st))
+        u, nxt = nxt, u
+
+    for m in range(1, args.warmup + 1):
+        step(m)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ev0.record()
+        t0 = time.perf_counter()
+        for m in range(args.warmup + 1, total + 1):
+            step(m)
+        ev1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    from paper_1706_06844_gb300 import shard as sh
+    ms = sh.max_over_ranks(ev0.elapsed_time(ev1), dist)
+    units = sh.sum_over_ranks(len(mine) * args.steps, dist)
+    launches = sum(fde.fde_launch_count(fde.fde_batch_handle(b, k)) for k in range(len(mine)))
+    fde.fde_batch_destroy(b)
+    if rank == 0:
+        line = {"metric": BATCH_METRIC, "value": round(units / (ms * 1e-3), 3),
+                "unit": "problem-steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f64 Krylov + fp32 V-cycle", "data": "synthetic",
+                "config": {"workload": BATCH_WORKLOAD, "problems": BATCH_COUNT,
+                           "parallelism": f"problems sharded over {world} rank(s), 16 host "
+                                          f"worker streams per rank",
+                           "l2": "inputs larger than L2 (256 problems' Krylov bases)"},
+                "inner_iterations_per_batch_step_rank0": its[args.warmup:],
+                "wall_s": round(wall, 3), "gpu_launches_rank0_total": int(launches),
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", default=None, choices=["gemm", "gemm3", "fft32", "fft64", "fftdf"],
@@ -364,6 +449,9 @@ def main():
                     help="structured-Galerkin V-cycle, rediscretised V-cycle (P_MGM) or the "
                          "band preconditioner P_2 with a Galerkin V-cycle")
     ap.add_argument("--cycles", type=int, default=1, help="V-cycles per preconditioner application")
+    ap.add_argument("--workload", default="n2047", choices=["n2047", "batch256"],
+                    help="n2047: the single 2047 x 2047 problem (replicated over ranks); "
+                         "batch256: 256 independent problems sharded over ranks")
     args = ap.parse_args()
     if args.kernel:
         kernel_micro(args.kernel, args.reps)
@@ -385,8 +473,13 @@ def main():
             dist.destroy_process_group()
         return
     import torch
-    from paper_1706_06844_gb300 import fde
+    from paper_1706_06844_gb300 import fde, shard
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if args.workload == "batch256":
+        run_batch(args, rank, world, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
     mixed = {"bf16": fde.FDE_PREC_BF16, "fp16": fde.FDE_PREC_FP16, "fp32": fde.FDE_PREC_FP32,
              "bf16x3": fde.FDE_PREC_BF16X3}[args.precision]
     outer = fde.FDE_OUTER_DF32 if args.outer == "df32" else fde.FDE_OUTER_FP64
@@ -395,10 +488,7 @@ def main():
     w = Workload(mixed, outer=outer, precond=precond, cycles=args.cycles)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         ms, wall, its, launches = time_steps(w, args.steps, args.warmup, dist)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(ms, dist)
     value = world * args.steps / (ms * 1e-3)
     e2e_v, h2d, d2h = e2e_steps(w, max(2, min(args.steps, 4)))
     roof = roofline(w, 2, args.outer)

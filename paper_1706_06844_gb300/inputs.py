@@ -101,13 +101,23 @@ class Problem:
         a1, b1, a2, b2 = self.domain
         p, al, be = self.p, self.alpha, self.beta
         et = self.amp * np.exp(-t)
-        Xb, Yb = bubble(X, a1, b1, p), bubble(Y, a2, b2, p)
+        g = _axes(X, Y)
+        if g is not None:
+            # grid input: every factor depends on x or y alone; evaluate it on the
+            # axis and broadcast (the same values as on the full grid)
+            xs, ys = g
+            Xe = lambda f, *a: np.broadcast_to(f(xs, *a)[None, :], X.shape)
+            Ye = lambda f, *a: np.broadcast_to(f(ys, *a)[:, None], X.shape)
+        else:
+            Xe = lambda f, *a: f(X, *a)
+            Ye = lambda f, *a: f(Y, *a)
+        Xb, Yb = Xe(bubble, a1, b1, p), Ye(bubble, a2, b2, p)
         dp, dm, ep, em = self.coefficients(X, Y, t)
         return (-et * Xb * Yb
-                - dp * et * Yb * bubble_dleft(X, a1, b1, p, al)
-                - dm * et * Yb * bubble_dright(X, a1, b1, p, al)
-                - ep * et * Xb * bubble_dleft(Y, a2, b2, p, be)
-                - em * et * Xb * bubble_dright(Y, a2, b2, p, be))
+                - dp * et * Yb * Xe(bubble_dleft, a1, b1, p, al)
+                - dm * et * Yb * Xe(bubble_dright, a1, b1, p, al)
+                - ep * et * Xb * Ye(bubble_dleft, a2, b2, p, be)
+                - em * et * Xb * Ye(bubble_dright, a2, b2, p, be))
 
 
 # ----------------------------------------------------------------------------
@@ -159,6 +169,16 @@ def example3():
 _GAMMA0 = (-1.0 + np.sqrt(17.0)) / 2.0
 
 
+def _axes(X, Y):
+    """(x, y) 1-D axes when X, Y are a meshgrid (x along rows, y down columns), else None."""
+    X, Y = np.asarray(X), np.asarray(Y)
+    if X.ndim != 2 or X.shape != Y.shape:
+        return None
+    if not (np.all(X == X[:1, :]) and np.all(Y == Y[:, :1])):
+        return None
+    return X[0, :], Y[:, 0]
+
+
 def _shift_q(alpha, beta):
     return 0 if min(alpha, beta) >= _GAMMA0 else -1
 
@@ -192,6 +212,16 @@ def smooth_modes(seed, n_modes=8, kmax=4):
     ps = rng.uniform(0.0, 2 * np.pi, n_modes)
 
     def raw(x, y):
+        g = _axes(x, y)
+        if g is not None:
+            # grid input: the same products from the 1-D factors, broadcast
+            xs, ys = g
+            out = np.zeros(np.broadcast(x, y).shape)
+            for i in range(n_modes):
+                sx = np.sin(np.pi * k1[i] * xs + th[i])[None, :]
+                sy = np.sin(np.pi * k2[i] * ys + ps[i])[:, None]
+                out = out + a[i] * sx * sy
+            return out
         out = 0.0 * (x + y)
         for i in range(n_modes):
             out = out + a[i] * np.sin(np.pi * k1[i] * x + th[i]) * np.sin(np.pi * k2[i] * y + ps[i])
