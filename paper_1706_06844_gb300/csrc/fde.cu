@@ -47,6 +47,7 @@ struct MGBase;
 struct fde_handle {
   fde_params p{};
   cudaStream_t st = nullptr;
+  cudaStream_t cap_st = nullptr;  // private stream on which V-cycles are captured into graphs
   std::string err;
   long long launches = 0;
   int n1 = 0, n2 = 0;
@@ -167,12 +168,59 @@ struct fde_handle {
 // multigrid hierarchy
 
 struct MGBase {
-  virtual ~MGBase() {}
+  virtual ~MGBase() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
   virtual int setup(fde_handle* h) = 0;  // from h->dpN.. (FP64, unscaled)
   virtual int vcycle(fde_handle* h, const double* r, double* z) = 0;
   virtual int level_apply(fde_handle* h, int l, const double* x, double* y) = 0;
+  // one V-cycle on the finest level's (b -> x) buffers: a fixed sequence of
+  // launches on fixed buffers, so it can be replayed from a CUDA graph
+  virtual int cycle_root(fde_handle* h) = 0;
   std::vector<int> n1s, n2s;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_launches = 0;
+  bool graph_off = false;
+
+  // The first call captures the cycle's ~8 launches per level on the handle's
+  // private stream and instantiates a graph; every call then launches that
+  // graph on the handle's stream (one launch instead of dozens of small ones
+  // on the coarse levels). With kernel profiling on, the cycle runs eagerly.
+  int run_cycle(fde_handle* h);
 };
+
+int MGBase::run_cycle(fde_handle* h) {
+  if (h->prof || graph_off || !h->cap_st) return cycle_root(h);
+  if (!graph) {
+    cudaStream_t user = h->st;
+    const long long l0 = h->launches;
+    CCHK(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
+    h->st = h->cap_st;
+    const int rc = cycle_root(h);
+    h->st = user;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cap_st, &g);
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei =
+        (rc == FDE_OK && e == cudaSuccess) ? cudaGraphInstantiate(&ex, g, 0) : cudaErrorUnknown;
+    if (g) cudaGraphDestroy(g);
+    const long long captured = h->launches - l0;
+    h->launches = l0;
+    if (rc != FDE_OK || ei != cudaSuccess) {
+      // capture refused (a call that cannot be captured) or the cycle failed:
+      // run eagerly from now on, which also reports a genuine error
+      cudaGetLastError();
+      graph_off = true;
+      h->err.clear();
+      return cycle_root(h);
+    }
+    graph = ex;
+    graph_launches = captured;
+  }
+  CCHK(cudaGraphLaunch(graph, h->st));
+  h->launches += graph_launches;
+  return FDE_OK;
+}
 
 template <typename T>
 struct MG : MGBase {
@@ -429,23 +477,24 @@ struct MG : MGBase {
     return FDE_OK;
   }
 
+  int cycle_root(fde_handle* h) override { return cycle(h, 0); }
+
   int vcycle(fde_handle* h, const double* r, double* z) override {
     Lv& L = lv[0];
     LCHK((launch_convert<double, T>(L.N, r, 1.0, L.b, h->st)));
-    RCHK(cycle(h, 0));
+    RCHK(run_cycle(h));
     const int cycles = h->p.cycles > 1 ? h->p.cycles : 1;
     if (cycles > 1) {
-      // stationary iteration: z_{k+1} = z_k + V(r - K_0 z_k); r stays in `rhs`
-      T* rhs = L.b;
-      std::swap(L.b, acc_b);
+      // stationary iteration z_{k+1} = z_k + V(r - K_0 z_k): r is kept in acc_b,
+      // each cycle reads its right-hand side from L.b and leaves z in L.x
+      CCHK(cudaMemcpyAsync(acc_b, L.b, L.N * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
       for (int k = 1; k < cycles; ++k) {
         CCHK(cudaMemcpyAsync(acc_x, L.x, L.N * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
         RCHK(products(h, 0, acc_x, L.kx));
-        LCHK(launch_level_epilogue<T>(1, L.N, L.kx, rhs, acc_x, L.W, L.b, h->st));
-        RCHK(cycle(h, 0));
+        LCHK(launch_level_epilogue<T>(1, L.N, L.kx, acc_b, acc_x, L.W, L.b, h->st));
+        RCHK(run_cycle(h));
         LCHK(launch_add<T>(L.N, acc_x, L.x, L.x, h->st));
       }
-      std::swap(L.b, acc_b);
     }
     LCHK((launch_convert<T, double>(L.N, L.x, 1.0, z, h->st)));
     return FDE_OK;
@@ -584,57 +633,65 @@ struct StencilMG : MGBase {
     return FDE_OK;
   }
 
-  int cycle(fde_handle* h, size_t l) {
+  // V-cycle on level l from x = 0; *out receives the buffer (x or kx of the
+  // level) that holds the result: Jacobi sweeps ping-pong between the two, in
+  // the same order on every call
+  int cycle(fde_handle* h, size_t l, T** out) {
     Lv& L = lv[l];
     const fde_params& p = h->p;
     cudaStream_t st = h->st;
+    T *x = L.x, *t = L.kx;
     if (l + 1 == lv.size()) {
       const int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
-      LCHK(launch_coarse_solve<T>(inv, (int)L.N, L.b, L.x, st));
+      LCHK(launch_coarse_solve<T>(inv, (int)L.N, L.b, x, st));
       h->pend(pi);
+      *out = x;
       return FDE_OK;
     }
     int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
-    if (p.nu_pre >= 1) LCHK(launch_mul<T>(L.N, L.W, L.b, L.x, st));
-    else CCHK(cudaMemsetAsync(L.x, 0, L.N * sizeof(T), st));
+    if (p.nu_pre >= 1) LCHK(launch_mul<T>(L.N, L.W, L.b, x, st));
+    else CCHK(cudaMemsetAsync(x, 0, L.N * sizeof(T), st));
     h->pend(pi);
-    for (int s = 1; s < p.nu_pre; ++s) {  // Jacobi sweeps ping-pong between x and kx
-      RCHK(apply(h, l, 2, L.x, L.b, L.kx));
-      std::swap(L.x, L.kx);
+    for (int s = 1; s < p.nu_pre; ++s) {
+      RCHK(apply(h, l, 2, x, L.b, t));
+      std::swap(x, t);
     }
-    RCHK(apply(h, l, 1, L.x, L.b, L.kx));  // r = b - K x
+    RCHK(apply(h, l, 1, x, L.b, t));  // r = b - K x
     pi = h->pbeg(FDE_KCLASS_MG_OTHER);
-    LCHK(launch_restrict<T>(L.kx, L.n1, L.n2, 1.0, lv[l + 1].b, st));  // R = P^T
+    LCHK(launch_restrict<T>(t, L.n1, L.n2, 1.0, lv[l + 1].b, st));  // R = P^T
     h->pend(pi);
-    RCHK(cycle(h, l + 1));
+    T* xc = nullptr;
+    RCHK(cycle(h, l + 1, &xc));
     pi = h->pbeg(FDE_KCLASS_MG_OTHER);
-    LCHK(launch_prolong_add<T>(lv[l + 1].x, L.n1, L.n2, L.x, st));
+    LCHK(launch_prolong_add<T>(xc, L.n1, L.n2, x, st));
     h->pend(pi);
     for (int s = 0; s < p.nu_post; ++s) {
-      RCHK(apply(h, l, 2, L.x, L.b, L.kx));
-      std::swap(L.x, L.kx);
+      RCHK(apply(h, l, 2, x, L.b, t));
+      std::swap(x, t);
     }
+    *out = x;
     return FDE_OK;
   }
+
+  T* root_out = nullptr;  // finest-level buffer holding a cycle's result
+  int cycle_root(fde_handle* h) override { return cycle(h, 0, &root_out); }
 
   int vcycle(fde_handle* h, const double* r, double* z) override {
     Lv& L = lv[0];
     LCHK((launch_convert<double, T>(L.N, r, 1.0, L.b, h->st)));
-    RCHK(cycle(h, 0));
+    RCHK(run_cycle(h));
     const int cycles = h->p.cycles > 1 ? h->p.cycles : 1;
     if (cycles > 1) {
-      // stationary iteration: z_{k+1} = z_k + V(r - K_0 z_k); r stays in `rhs`
-      T* rhs = L.b;
-      std::swap(L.b, acc_b);
+      // stationary iteration z_{k+1} = z_k + V(r - K_0 z_k): r is kept in acc_b
+      CCHK(cudaMemcpyAsync(acc_b, L.b, L.N * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
       for (int k = 1; k < cycles; ++k) {
-        CCHK(cudaMemcpyAsync(acc_x, L.x, L.N * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
-        RCHK(apply(h, 0, 1, acc_x, rhs, L.b));
-        RCHK(cycle(h, 0));
-        LCHK(launch_add<T>(L.N, acc_x, L.x, L.x, h->st));
+        CCHK(cudaMemcpyAsync(acc_x, root_out, L.N * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+        RCHK(apply(h, 0, 1, acc_x, acc_b, L.b));
+        RCHK(run_cycle(h));
+        LCHK(launch_add<T>(L.N, acc_x, root_out, root_out, h->st));
       }
-      std::swap(L.b, acc_b);
     }
-    LCHK((launch_convert<T, double>(L.N, L.x, 1.0, z, h->st)));
+    LCHK((launch_convert<T, double>(L.N, root_out, 1.0, z, h->st)));
     return FDE_OK;
   }
 
@@ -911,6 +968,7 @@ int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
   const size_t N = h->N;
   int rc = FDE_OK;
   auto setup = [&]() -> int {
+    CCHK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
     RCHK(h->alloc(&h->wx, p.n1 + 2));
     RCHK(h->alloc(&h->wy, p.n2 + 2));
     RCHK(h->alloc(&h->tx0, p.n1 + 2));
@@ -998,6 +1056,7 @@ void fde_destroy(fde_handle* h) {
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
   h->mg.reset();
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
   for (void* q : h->allocs) cudaFree(q);
   for (auto& pe : h->pending) {
     cudaEventDestroy(pe.a);

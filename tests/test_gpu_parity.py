@@ -244,3 +244,31 @@ def test_error_paths():
         assert e.value.code == fde.FDE_ERR_ARG
     finally:
         fde.fde_destroy(h)
+
+
+@pytest.mark.parametrize("precond,precision,path", [
+    (fde.FDE_PRECOND_MG_SG, fde.FDE_PREC_FP32, fde.FDE_PATH_AUTO),
+    (fde.FDE_PRECOND_MG_SG, fde.FDE_PREC_BF16X3, fde.FDE_PATH_GEMM),
+    (fde.FDE_PRECOND_MG_REDISC, fde.FDE_PREC_FP64, fde.FDE_PATH_AUTO),
+    (fde.FDE_PRECOND_P2, fde.FDE_PREC_FP32, fde.FDE_PATH_AUTO)])
+@pytest.mark.parametrize("cycles", [1, 2])
+def test_graph_replay_equals_eager_cycle(precond, precision, path, cycles):
+    # the V-cycle is captured into a CUDA graph on first use and replayed;
+    # with kernel profiling on it runs eagerly: all runs give identical bits
+    import torch
+    case = Case(inputs.perturbed_power_law(), 255, precond=precond, precision=precision,
+                toeplitz_path=path, cycles=cycles)
+    h = case.handle()
+    try:
+        R = dev(np.random.default_rng(9).standard_normal((255, 255)))
+        outs = []
+        for prof in (0, 0, 1, 0):
+            fde.fde_profile_enable(h, prof)
+            z = torch.empty_like(R)
+            fde.fde_vcycle(h, R, z)
+            torch.cuda.synchronize()
+            outs.append(host(z))
+        for o in outs[1:]:
+            np.testing.assert_array_equal(o, outs[0])
+    finally:
+        fde.fde_destroy(h)
