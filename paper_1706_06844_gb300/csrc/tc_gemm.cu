@@ -59,6 +59,11 @@ struct Cfg {
   // + 256 B barriers + the generator copies (gen_bytes(n) per term, after the barriers)
   static constexpr size_t FIXED = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
 };
+// epilogue staging (DIR 0: transposed accumulators + operand batches; DIR 1:
+// operand blocks) must fit in the pipeline stages it reuses
+static_assert(8 * (2 * 32 * 33 + 3 * 16 * 32) * 4 <= 3 * 1 * (128 * 64 * 2 + 256 * 64 * 2), "NT=1 DIR0");
+static_assert(8 * (2 * 32 * 33 + 3 * 32 * 32) * 4 <= 2 * 2 * (128 * 64 * 2 + 256 * 64 * 2), "NT=2 DIR0");
+static_assert(8 * (3 * 32 * 32) * 4 <= 2 * 2 * (128 * 64 * 2 + 256 * 64 * 2), "DIR1");
 // padded generator length and the bytes of its forward + reversed copies
 __host__ __device__ constexpr int gen_len(int n) { return (n + GEN_PAD + 7) / 8 * 8; }
 __host__ __device__ constexpr size_t gen_bytes(int n) { return (size_t)2 * gen_len(n) * 2; }
@@ -150,6 +155,13 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    bar)
                : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst_smem, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst_smem)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
@@ -343,6 +355,43 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
     // ------------------------------------------------------------ synthesis
     const int w = warp - 2;  // 0..NSYN-1
     {
+      // DRAM is idle while the tensor cores run: pull this warp's epilogue
+      // operands (its 32 rows or columns x 128 of the tile) into L2 now, so the
+      // epilogue reads them from L2 instead of waiting on DRAM
+      const int g = warp & 3;
+      const int c_lo = (w >> 2) * (BN / 2);
+      auto pf = [](const float* a) { asm volatile("prefetch.global.L2 [%0];" ::"l"(a)); };
+      if (DIR == 0) {
+        // rows rbase + lane, columns out0 + c_lo .. + 127: four 128-byte lines per row
+        const int row = m0 + g * 32 + lane;
+        if (row < kp.n2) {
+          const int c0i = out0 + c_lo;
+          const int c1i = min(kp.n1, c0i + BN / 2) - 1;
+          if (c0i <= c1i) {
+            const size_t rb = (size_t)row * kp.n1;
+            for (int c = c0i; c <= c1i + 31; c += 32) {
+              const size_t e = rb + min(c, c1i);
+              pf(kp.c0 + e);
+              pf(kp.c1 + e);
+              if (kp.M) pf(kp.M + e);
+            }
+          }
+        }
+      } else {
+        // rows out0 + c_lo .. + 127, columns m0 + g * 32 .. + 31: one line per row
+        const int col = min(m0 + g * 32, kp.n1 - 1);
+        for (int r = lane; r < BN / 2; r += 32) {
+          const int row = out0 + c_lo + r;
+          if (row < kp.n2) {
+            const size_t e = (size_t)row * kp.n1 + col;
+            pf(kp.c0 + e);
+            pf(kp.c1 + e);
+            pf(kp.out + e);
+          }
+        }
+      }
+    }
+    {
       JobIter it{out0, nk};
       int acc, k0, delta, n = 0;
       while (!*abort_flag && it.next(acc, k0, delta)) {
@@ -416,10 +465,24 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
     fence_after();
     if (ok && !*abort_flag) {
       const uint32_t tl = tmem + ((uint32_t)(g * 32) << 16);
+      // The freed pipeline stages hold the epilogue's operands: each lane
+      // copies its elements of a block with 4-byte cp.async (rows of a length
+      // that is no multiple of 16 bytes rule out bulk copies), so all of a
+      // block's loads are in flight together, and reads them back itself.
+      const float* __restrict__ c0 = kp.c0;
+      const float* __restrict__ c1 = kp.c1;
+      float* __restrict__ out = kp.out;
       if (DIR == 0) {
-        // lanes are grid rows: stage through shared memory so lane = column
+        // lanes are grid rows in TMEM: stage through shared memory so lane = column
         float* stg = reinterpret_cast<float*>(base) + w * (2 * 32 * 33);
+        constexpr int RB = NT == 2 ? 32 : 16;  // rows per batch of copies (fits the stages)
+        float* opd = reinterpret_cast<float*>(base) + NSYN * (2 * 32 * 33) + w * (3 * RB * 32);
+        const float* __restrict__ Mm = kp.M;
+        const int rbase = m0 + g * 32;
+        const int nr = kp.n2 - rbase < 32 ? kp.n2 - rbase : 32;
         for (int cb = c_lo; cb < c_hi; cb += 32) {
+          const int col = out0 + cb + lane;
+          const bool live = col < kp.n1;
 #pragma unroll
           for (int a = 0; a < 2; ++a) {
             float v[32];
@@ -429,66 +492,55 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
             for (int q = 0; q < 32; ++q) stg[(a * 32 + lane) * 33 + q] = v[q];
           }
           __syncwarp();
-          const int col = out0 + cb + lane;
-          if (col < kp.n1) {
-            // all loads of the chunk first (the output may alias nothing, but the
-            // compiler cannot know), then the stores
-            const float* __restrict__ c0 = kp.c0;
-            const float* __restrict__ c1 = kp.c1;
-            const float* __restrict__ Mm = kp.M;
-            float* __restrict__ out = kp.out;
-            const int rbase = m0 + g * 32;
-            const int nr = kp.n2 - rbase < 32 ? kp.n2 - rbase : 32;
-            float p0[32], p1[32], pm[32];
 #pragma unroll
-            for (int rr = 0; rr < 32; ++rr) {
-              const size_t idx = (size_t)(rbase + rr) * kp.n1 + col;
-              p0[rr] = rr < nr ? __ldg(c0 + idx) : 0.f;
-              p1[rr] = rr < nr ? __ldg(c1 + idx) : 0.f;
-              pm[rr] = (rr < nr && Mm) ? __ldg(Mm + idx) : 0.f;
-            }
-#pragma unroll
-            for (int rr = 0; rr < 32; ++rr) {
-              if (rr < nr) {
-                const size_t idx = (size_t)(rbase + rr) * kp.n1 + col;
-                out[idx] = kp.inv_scale * (p0[rr] * stg[rr * 33 + lane] +
-                                           p1[rr] * stg[(32 + rr) * 33 + lane]) +
-                           kp.cm * pm[rr];
+          for (int h = 0; h < 32; h += RB) {
+            if (live)
+              for (int rr = 0; rr < RB && h + rr < nr; ++rr) {
+                const size_t idx = (size_t)(rbase + h + rr) * kp.n1 + col;
+                cp_async4(opd + (0 * RB + rr) * 32 + lane, c0 + idx);
+                cp_async4(opd + (1 * RB + rr) * 32 + lane, c1 + idx);
+                if (Mm) cp_async4(opd + (2 * RB + rr) * 32 + lane, Mm + idx);
               }
-            }
+            cp_async_wait_all();
+            if (live)
+              for (int rr = 0; rr < RB && h + rr < nr; ++rr) {
+                const size_t idx = (size_t)(rbase + h + rr) * kp.n1 + col;
+                const float m = Mm ? opd[(2 * RB + rr) * 32 + lane] : 0.f;
+                out[idx] = kp.inv_scale * (opd[(0 * RB + rr) * 32 + lane] * stg[(h + rr) * 33 + lane] +
+                                           opd[(1 * RB + rr) * 32 + lane] *
+                                               stg[(32 + h + rr) * 33 + lane]) +
+                           kp.cm * m;
+              }
           }
           __syncwarp();
         }
       } else {
         // lanes are grid columns i; TMEM columns are grid rows j
+        float* opd = reinterpret_cast<float*>(base) + w * (3 * 32 * 32);
         const int col = m0 + g * 32 + lane;
+        const bool live = col < kp.n1;
         for (int cb = c_lo; cb < c_hi; cb += 32) {
+          const int nr = kp.n2 - (out0 + cb) < 32 ? kp.n2 - (out0 + cb) : 32;
+          if (live)
+            for (int q = 0; q < nr; ++q) {
+              const size_t idx = (size_t)(out0 + cb + q) * kp.n1 + col;
+              cp_async4(opd + (0 * 32 + q) * 32 + lane, c0 + idx);
+              cp_async4(opd + (1 * 32 + q) * 32 + lane, c1 + idx);
+              cp_async4(opd + (2 * 32 + q) * 32 + lane, out + idx);
+            }
           float a0[32], a1[32];
           tmem_ld32(tl + cb, a0);
           tmem_ld32(tl + BN + cb, a1);
           tmem_wait_ld();
-          if (col < kp.n1) {
-            const float* __restrict__ c0 = kp.c0;
-            const float* __restrict__ c1 = kp.c1;
-            float* __restrict__ out = kp.out;
-            const int nr = kp.n2 - (out0 + cb) < 32 ? kp.n2 - (out0 + cb) : 32;
+          cp_async_wait_all();
+          if (live) {
 #pragma unroll
-            for (int h = 0; h < 32; h += 16) {  // two halves keep the loads in registers
-              float q0[16], q1[16], qo[16];
-#pragma unroll
-              for (int q = 0; q < 16; ++q) {
-                const size_t idx = (size_t)(out0 + cb + h + q) * kp.n1 + col;
-                const bool v = h + q < nr;
-                q0[q] = v ? __ldg(c0 + idx) : 0.f;
-                q1[q] = v ? __ldg(c1 + idx) : 0.f;
-                qo[q] = v ? out[idx] : 0.f;
-              }
-#pragma unroll
-              for (int q = 0; q < 16; ++q) {
-                if (h + q < nr) {
-                  const size_t idx = (size_t)(out0 + cb + h + q) * kp.n1 + col;
-                  out[idx] = qo[q] + kp.inv_scale * (q0[q] * a0[h + q] + q1[q] * a1[h + q]);
-                }
+            for (int q = 0; q < 32; ++q) {
+              if (q < nr) {
+                const size_t idx = (size_t)(out0 + cb + q) * kp.n1 + col;
+                out[idx] = opd[(2 * 32 + q) * 32 + lane] +
+                           kp.inv_scale * (opd[(0 * 32 + q) * 32 + lane] * a0[q] +
+                                           opd[(1 * 32 + q) * 32 + lane] * a1[q]);
               }
             }
           }
