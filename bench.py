@@ -443,7 +443,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["bf16", "fp16", "fp32", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16", "fp16", "fp32", "bf16x3"])
     ap.add_argument("--outer", default="df32", choices=["df32", "fp64"])
     ap.add_argument("--precond", default="sg", choices=["sg", "redisc", "p2"],
                     help="structured-Galerkin V-cycle, rediscretised V-cycle (P_MGM) or the "

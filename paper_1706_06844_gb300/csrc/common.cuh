@@ -41,19 +41,29 @@ __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
 // and S2 (A^T) were built by build_spectra for the same L.  M, cp, cm may be
 // null (term omitted; null cp/cm means 1).  T: storage type, R: FFT arithmetic.
 // C: storage type of the coefficient fields (T, or df for the double-float path).
+// When two padded length-L buffers of cx<R> exceed shared memory (L = 8192 for
+// 16-byte complex values) the pass keeps one buffer and parks the forward
+// spectrum in `ws` (global memory, ws_elems cx<R> entries, at least L per
+// concurrently resident CTA; cudaErrorInvalidValue if too small).
 template <typename T, typename R, typename C>
 cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int logL,
                             const cx<R>* S1, const cx<R>* S2, const cx<R>* tw,
                             const C* cp, const C* cm, const T* M, double cmass,
-                            T* Y, int accumulate, cudaStream_t st);
+                            T* Y, int accumulate, cudaStream_t st, cx<R>* ws = nullptr,
+                            size_t ws_elems = 0);
+// shared-memory bytes a pass of length 2^logL in cx<R> needs with two buffers
+size_t fft_pass_two_buffer_bytes(int logL, size_t cx_bytes);
 
 // Spectra of the circulant embeddings (length L = 2^logL >= 2n - 1) of A and A^T,
 // A = [t_{i-k}], generator t_d at t[d+1] for d = -1..n-1, scaled by scale/L and
 // stored in bit-reversed order.  Also fills (when tw is non-null) the twiddle
 // table of length L - 1: tw[half - 1 + pos] = e^{-2 pi i pos/(2 half)}.
+// For L whose twiddles do not fit in shared memory beside the transform
+// (L = 8192), `tw_scratch` (L - 1 entries of global memory) holds them.
 template <typename R>
 cudaError_t launch_build_spectra(const double* t, int n, int logL, double scale, cx<R>* S1,
-                                 cx<R>* S2, cx<R>* tw, cudaStream_t st);
+                                 cx<R>* S2, cx<R>* tw, cudaStream_t st,
+                                 cx<double>* tw_scratch = nullptr);
 
 // Direct summation version of launch_fft_pass (same contract), A given by the
 // generator t (length n + 1, t_d at t[d+1]).

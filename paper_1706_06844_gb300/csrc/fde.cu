@@ -71,6 +71,11 @@ struct fde_handle {
   double *epNsT = nullptr, *emNsT = nullptr, *epOsT = nullptr, *emOsT = nullptr;
   df *cfNT[2] = {nullptr, nullptr}, *cfOT[2] = {nullptr, nullptr};
   double *xT = nullptr, *yT = nullptr;  // transposed operand / result of the column pass
+  // FFT passes whose two length-L buffers exceed shared memory (L = 8192 with
+  // 16-byte complex values) park spectra here; also the twiddle scratch of
+  // their spectra builds
+  cx<double>* fft_ws = nullptr;
+  size_t fft_ws_elems = 0;
   bool have_new = false, have_old = false;
 
   std::unique_ptr<MGBase> mg;
@@ -315,9 +320,9 @@ struct MG : MGBase {
       if (path == FDE_PATH_FFT) {
         L.logLx = ceil_log2(2L * L.n1 - 1);
         L.logLy = ceil_log2(2L * L.n2 - 1);
-        const size_t smx = 2 * ((size_t)1 << L.logLx) * sizeof(cx<T>);
-        const size_t smy = 2 * ((size_t)1 << L.logLy) * sizeof(cx<T>);
-        if (smx > 227 * 1024 || smy > 227 * 1024)
+        const int lmax = std::max(L.logLx, L.logLy);
+        if (fft_pass_two_buffer_bytes(lmax, sizeof(cx<T>)) > 227 * 1024 &&
+            h->fft_ws_elems < ((size_t)152 << lmax))
           return h->fail(FDE_ERR_UNSUPPORTED, "FFT length too large for shared memory");
         RCHK(h->alloc(&L.S1x, (size_t)1 << L.logLx));
         RCHK(h->alloc(&L.S2x, (size_t)1 << L.logLx));
@@ -336,7 +341,25 @@ struct MG : MGBase {
         const int prec = p.precision == FDE_PREC_BF16 ? tc::kBF16
                          : p.precision == FDE_PREC_FP16 ? tc::kFP16 : tc::kBF16X3;
         int r = tc::level_create(&L.gemm, L.n1, L.n2, prec, sg && l > 0);
-        if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core level allocation failed (%d)", r);
+        if (r == 13 && p.toeplitz_path == FDE_PATH_AUTO) {
+          // the generator copies do not fit beside the pipeline: FFT products
+          tc::level_destroy(&L.gemm);
+          L.path = FDE_PATH_FFT;
+          L.logLx = ceil_log2(2L * L.n1 - 1);
+          L.logLy = ceil_log2(2L * L.n2 - 1);
+          RCHK(h->alloc(&L.S1x, (size_t)1 << L.logLx));
+          RCHK(h->alloc(&L.S2x, (size_t)1 << L.logLx));
+          RCHK(h->alloc(&L.twx, (size_t)1 << L.logLx));
+          RCHK(h->alloc(&L.epT, L.N));
+          RCHK(h->alloc(&L.emT, L.N));
+          RCHK(h->alloc(&L.xT, L.N));
+          RCHK(h->alloc(&L.yT, L.N));
+          RCHK(h->alloc(&L.S1y, (size_t)1 << L.logLy));
+          RCHK(h->alloc(&L.S2y, (size_t)1 << L.logLy));
+          RCHK(h->alloc(&L.twy, (size_t)1 << L.logLy));
+        } else if (r != 0) {
+          return h->fail(FDE_ERR_UNSUPPORTED, "tensor-core level allocation failed (%d)", r);
+        }
       }
     }
     const Lv& C = lv.back();
@@ -376,8 +399,8 @@ struct MG : MGBase {
       if (L.path == FDE_PATH_FFT && l + 1 < lv.size()) {
         LCHK(launch_transpose<T>(L.ep, L.n2, L.n1, L.epT, 0, st));
         LCHK(launch_transpose<T>(L.em, L.n2, L.n1, L.emT, 0, st));
-        LCHK(launch_build_spectra<T>(L.tx, L.n1, L.logLx, 1.0, L.S1x, L.S2x, L.twx, st));
-        LCHK(launch_build_spectra<T>(L.ty, L.n2, L.logLy, 1.0, L.S1y, L.S2y, L.twy, st));
+        LCHK(launch_build_spectra<T>(L.tx, L.n1, L.logLx, 1.0, L.S1x, L.S2x, L.twx, st, h->fft_ws));
+        LCHK(launch_build_spectra<T>(L.ty, L.n2, L.logLy, 1.0, L.S1y, L.S2y, L.twy, st, h->fft_ws));
       } else if (L.path == FDE_PATH_DIRECT && l + 1 < lv.size()) {
         LCHK((launch_convert<double, T>(L.n1 + 1, L.tx, 1.0, L.txT, st)));
         LCHK((launch_convert<double, T>(L.n2 + 1, L.ty, 1.0, L.tyT, st)));
@@ -418,11 +441,13 @@ struct MG : MGBase {
     }
     const int pi = h->pbeg(FDE_KCLASS_LEVEL_APPLY);
     if (L.path == FDE_PATH_FFT) {
+      cx<T>* ws = reinterpret_cast<cx<T>*>(h->fft_ws);
+      const size_t wse = h->fft_ws_elems * sizeof(cx<double>) / sizeof(cx<T>);
       LCHK((launch_fft_pass<T, T, T>(xin_x, 1, L.n1, L.n2, L.n1, L.logLx, L.S1x, L.S2x, L.twx, L.dp,
-                                  L.dm, M, cm, kx, 0, st)));
+                                  L.dm, M, cm, kx, 0, st, ws, wse)));
       LCHK(launch_transpose<T>(xin_y, L.n2, L.n1, L.xT, 0, st));
       LCHK((launch_fft_pass<T, T, T>(L.xT, 1, L.n2, L.n1, L.n2, L.logLy, L.S1y, L.S2y, L.twy,
-                                     L.epT, L.emT, nullptr, 0.0, L.yT, 0, st)));
+                                     L.epT, L.emT, nullptr, 0.0, L.yT, 0, st, ws, wse)));
       LCHK(launch_transpose<T>(L.yT, L.n1, L.n2, kx, 1, st));
     } else if (L.path == FDE_PATH_DIRECT) {
       LCHK(launch_direct_pass<T>(xin_x, 1, L.n1, L.n2, L.n1, L.txT, L.dp, L.dm, M, cm, kx, 0, st));
@@ -719,15 +744,17 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
   if (h->p.outer == FDE_OUTER_DF32) {
     df* const* cf = old ? h->cfO : h->cfN;
     int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
+    cx<df>* ws = reinterpret_cast<cx<df>*>(h->fft_ws);
     LCHK((launch_fft_pass<double, df, df>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1xd, h->S2xd,
-                                          h->twxd, cf[0], cf[1], x, h->c, y, 0, h->st)));
+                                          h->twxd, cf[0], cf[1], x, h->c, y, 0, h->st, ws,
+                                          h->fft_ws_elems)));
     h->pend(pi);
     df* const* cfT = old ? h->cfOT : h->cfNT;
     LCHK(launch_transpose<double>(x, h->n2, h->n1, h->xT, 0, h->st));
     pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
     LCHK((launch_fft_pass<double, df, df>(h->xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1yd,
                                           h->S2yd, h->twyd, cfT[0], cfT[1], nullptr, 0.0, h->yT, 0,
-                                          h->st)));
+                                          h->st, ws, h->fft_ws_elems)));
     h->pend(pi);
     LCHK(launch_transpose<double>(h->yT, h->n1, h->n2, y, 1, h->st));
     return FDE_OK;
@@ -738,7 +765,8 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
   const double* em = old ? h->emOs : h->emNs;
   int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
   LCHK((launch_fft_pass<double, double, double>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x, h->S2x,
-                                        h->twx, dp, dm, x, h->c, y, 0, h->st)));
+                                        h->twx, dp, dm, x, h->c, y, 0, h->st, h->fft_ws,
+                                        h->fft_ws_elems)));
   h->pend(pi);
   const double* epT = old ? h->epOsT : h->epNsT;
   const double* emT = old ? h->emOsT : h->emNsT;
@@ -746,7 +774,7 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
   pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
   LCHK((launch_fft_pass<double, double, double>(h->xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1y,
                                                 h->S2y, h->twy, epT, emT, nullptr, 0.0, h->yT, 0,
-                                                h->st)));
+                                                h->st, h->fft_ws, h->fft_ws_elems)));
   h->pend(pi);
   LCHK(launch_transpose<double>(h->yT, h->n1, h->n2, y, 1, h->st));
   return FDE_OK;
@@ -929,8 +957,8 @@ static int validate(const fde_params* p, std::string& why) {
   if (p->toeplitz_path < FDE_PATH_AUTO || p->toeplitz_path > FDE_PATH_DIRECT) return bad("unknown toeplitz_path");
   if (p->outer != FDE_OUTER_FP64 && p->outer != FDE_OUTER_DF32) return bad("unknown outer");
   const int L1 = ceil_log2(2L * p->n1 - 1), L2 = ceil_log2(2L * p->n2 - 1);
-  if (L1 > 12 || L2 > 12) {
-    snprintf(buf, sizeof(buf), "FP64 FFT apply supports n <= 2048 (got %d x %d)", p->n1, p->n2);
+  if (L1 > 13 || L2 > 13) {
+    snprintf(buf, sizeof(buf), "FP64 FFT apply supports n <= 4096 (got %d x %d)", p->n1, p->n2);
     why = buf;
     return FDE_ERR_UNSUPPORTED;
   }
@@ -979,14 +1007,21 @@ int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
     LCHK(launch_generator_from_weights(h->wy, p.n2, 1.0, h->ty0, h->st));
     h->logLx = ceil_log2(2L * p.n1 - 1);
     h->logLy = ceil_log2(2L * p.n2 - 1);
+    {
+      const int lmax = std::max(h->logLx, h->logLy);
+      if (fft_pass_two_buffer_bytes(lmax, sizeof(cx<double>)) > 227 * 1024) {
+        h->fft_ws_elems = (size_t)152 << lmax;  // one CTA per SM, L entries each
+        RCHK(h->alloc(&h->fft_ws, h->fft_ws_elems));
+      }
+    }
     RCHK(h->alloc(&h->S1x, (size_t)1 << h->logLx));
     RCHK(h->alloc(&h->S2x, (size_t)1 << h->logLx));
     RCHK(h->alloc(&h->twx, (size_t)1 << h->logLx));
     RCHK(h->alloc(&h->S1y, (size_t)1 << h->logLy));
     RCHK(h->alloc(&h->S2y, (size_t)1 << h->logLy));
     RCHK(h->alloc(&h->twy, (size_t)1 << h->logLy));
-    LCHK(launch_build_spectra<double>(h->tx0, p.n1, h->logLx, 1.0, h->S1x, h->S2x, h->twx, h->st));
-    LCHK(launch_build_spectra<double>(h->ty0, p.n2, h->logLy, 1.0, h->S1y, h->S2y, h->twy, h->st));
+    LCHK(launch_build_spectra<double>(h->tx0, p.n1, h->logLx, 1.0, h->S1x, h->S2x, h->twx, h->st, h->fft_ws));
+    LCHK(launch_build_spectra<double>(h->ty0, p.n2, h->logLy, 1.0, h->S1y, h->S2y, h->twy, h->st, h->fft_ws));
     if (p.outer == FDE_OUTER_DF32) {
       RCHK(h->alloc(&h->S1xd, (size_t)1 << h->logLx));
       RCHK(h->alloc(&h->S2xd, (size_t)1 << h->logLx));
@@ -994,8 +1029,8 @@ int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
       RCHK(h->alloc(&h->S1yd, (size_t)1 << h->logLy));
       RCHK(h->alloc(&h->S2yd, (size_t)1 << h->logLy));
       RCHK(h->alloc(&h->twyd, (size_t)1 << h->logLy));
-      LCHK(launch_build_spectra<df>(h->tx0, p.n1, h->logLx, 1.0, h->S1xd, h->S2xd, h->twxd, h->st));
-      LCHK(launch_build_spectra<df>(h->ty0, p.n2, h->logLy, 1.0, h->S1yd, h->S2yd, h->twyd, h->st));
+      LCHK(launch_build_spectra<df>(h->tx0, p.n1, h->logLx, 1.0, h->S1xd, h->S2xd, h->twxd, h->st, h->fft_ws));
+      LCHK(launch_build_spectra<df>(h->ty0, p.n2, h->logLy, 1.0, h->S1yd, h->S2yd, h->twyd, h->st, h->fft_ws));
       for (int k = 0; k < 4; ++k) {
         RCHK(h->alloc(&h->cfN[k], N));
         RCHK(h->alloc(&h->cfO[k], N));

@@ -117,8 +117,8 @@ __device__ void fft_dif(cx<R>* a, int logL, const cx<R>* __restrict__ tw) {
   }
 }
 
-// inverse transform (unnormalised) of two arrays, in place,
-// bit-reversed order -> natural order
+// inverse transform (unnormalised) of two arrays (or of `a` alone when c is
+// null), in place, bit-reversed order -> natural order
 template <typename R>
 __device__ void fft_dit_inv2(cx<R>* a, cx<R>* c, int logL, const cx<R>* __restrict__ tw) {
   int s = 0;
@@ -127,7 +127,8 @@ __device__ void fft_dit_inv2(cx<R>* a, cx<R>* c, int logL, const cx<R>* __restri
     const int q = rem >= 4 ? 4 : (rem >= 2 ? 2 : 1);
     const int h = 1 << s;
     const int ngroups = 1 << (logL - q);
-    for (int gg = threadIdx.x; gg < 2 * ngroups; gg += blockDim.x) {
+    const int total = c ? 2 * ngroups : ngroups;  // c may be null: one array
+    for (int gg = threadIdx.x; gg < total; gg += blockDim.x) {
       cx<R>* arr = gg < ngroups ? a : c;
       const int g = gg < ngroups ? gg : gg - ngroups;
       const int pos = g & (h - 1);
@@ -194,12 +195,107 @@ fft_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int lo
   }
 }
 
+// The same pass with one shared buffer: the forward spectrum of a pair is
+// parked in this CTA's slice of `ws`, the A-product is transformed back and
+// written, then the A^T-product is formed from the parked spectrum and added.
+template <typename T, typename R, typename C>
+__global__ void __launch_bounds__(512)
+fft_pass_seq_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int logL,
+                    const cx<R>* __restrict__ S1, const cx<R>* __restrict__ S2,
+                    const cx<R>* __restrict__ tw, const C* __restrict__ cp,
+                    const C* __restrict__ cm, const T* __restrict__ M, double cmass_d, T* Y,
+                    int accumulate, cx<R>* __restrict__ ws) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = 1 << logL;
+  const R cmass = R(cmass_d);
+  cx<R>* a = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* spec = ws + (size_t)blockIdx.x * L;
+  const int npairs = (nvec + 1) >> 1;
+  for (int pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
+    const int va = 2 * pair;
+    const bool hasb = va + 1 < nvec;
+    const size_t oa = (size_t)va * vs, ob = oa + vs;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+      cx<R> z = {R(0), R(0)};
+      if (i < n) {
+        z.re = R(X[oa + (size_t)i * es]);
+        if (hasb) z.im = R(X[ob + (size_t)i * es]);
+      }
+      a[pad(i)] = z;
+    }
+    __syncthreads();
+    fft_dif(a, logL, tw);
+    for (int p = threadIdx.x; p < L; p += blockDim.x) {
+      const cx<R> z = a[pad(p)];
+      spec[p] = z;
+      a[pad(p)] = cmul(z, S1[p]);
+    }
+    __syncthreads();
+    fft_dit_inv2<R>(a, nullptr, logL, tw);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const size_t ia = oa + (size_t)i * es;
+      const cx<R> ya_ = a[pad(i)];
+      R y = ya_.re * coef<R, C>(cp, ia);
+      if (M) y += cmass * R(M[ia]);
+      if (accumulate) y += R(Y[ia]);
+      Y[ia] = T(y);
+      if (hasb) {
+        const size_t ib = ob + (size_t)i * es;
+        R yb = ya_.im * coef<R, C>(cp, ib);
+        if (M) yb += cmass * R(M[ib]);
+        if (accumulate) yb += R(Y[ib]);
+        Y[ib] = T(yb);
+      }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < L; p += blockDim.x) a[pad(p)] = cmul(spec[p], S2[p]);
+    __syncthreads();
+    fft_dit_inv2<R>(a, nullptr, logL, tw);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const size_t ia = oa + (size_t)i * es;
+      const cx<R> yc_ = a[pad(i)];
+      Y[ia] = T(R(Y[ia]) + yc_.re * coef<R, C>(cm, ia));
+      if (hasb) {
+        const size_t ib = ob + (size_t)i * es;
+        Y[ib] = T(R(Y[ib]) + yc_.im * coef<R, C>(cm, ib));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+size_t fft_pass_two_buffer_bytes(int logL, size_t cx_bytes) {
+  return 2 * (size_t)padded_len(1 << logL) * cx_bytes;
+}
+
 template <typename T, typename R, typename C>
 cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int logL,
                             const cx<R>* S1, const cx<R>* S2, const cx<R>* tw, const C* cp,
                             const C* cm, const T* M, double cmass, T* Y, int accumulate,
-                            cudaStream_t st) {
+                            cudaStream_t st, cx<R>* ws, size_t ws_elems) {
   const int L = 1 << logL;
+  const int threads = L / 2 < 512 ? L / 2 : 512;
+  const int npairs = (nvec + 1) / 2;
+  if (fft_pass_two_buffer_bytes(logL, sizeof(cx<R>)) > 227 * 1024) {
+    const size_t smem1 = (size_t)padded_len(L) * sizeof(cx<R>);
+    if (smem1 > 227 * 1024) return cudaErrorInvalidValue;
+    static bool attr1 = false;
+    if (!attr1) {
+      cudaError_t e = cudaFuncSetAttribute(fft_pass_seq_kernel<T, R, C>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           227 * 1024);
+      if (e != cudaSuccess) return e;
+      attr1 = true;
+    }
+    const int per_sm = (int)((227 * 1024) / (smem1 + 1024));
+    int grid = 152 * (per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm));
+    if (grid > npairs) grid = npairs;
+    if (!ws || ws_elems / (size_t)L < 1) return cudaErrorInvalidValue;
+    if ((size_t)grid > ws_elems / (size_t)L) grid = (int)(ws_elems / (size_t)L);
+    fft_pass_seq_kernel<T, R, C><<<grid, threads, smem1, st>>>(
+        X, es, vs, nvec, n, logL, S1, S2, tw, cp, cm, M, cmass, Y, accumulate, ws);
+    return cudaGetLastError();
+  }
   const size_t smem = 2 * (size_t)padded_len(L) * sizeof(cx<R>);
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
@@ -208,8 +304,6 @@ cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int log
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int threads = L / 2 < 512 ? L / 2 : 512;
-  const int npairs = (nvec + 1) / 2;
   const int per_sm = (int)((227 * 1024) / (smem + 1024));
   int grid = 152 * (per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm));
   if (grid > npairs) grid = npairs;
@@ -221,13 +315,15 @@ cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int log
 // ---------------------------------------------------------------- spectra
 template <typename R>
 __global__ void build_spectra_kernel(const double* __restrict__ t, int n, int logL, double scale,
-                                     cx<R>* S1, cx<R>* S2, cx<R>* twout) {
+                                     cx<R>* S1, cx<R>* S2, cx<R>* twout, cx<double>* tw_global) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 1 << logL;
   cx<double>* a = reinterpret_cast<cx<double>*>(smem_raw);
-  cx<double>* tw = a + padded_len(L);
+  // tw_global (when set) was filled by twiddle_kernel in an earlier launch: a
+  // table written and read within one launch could meet stale read-only-cache lines
+  cx<double>* tw = tw_global ? tw_global : a + padded_len(L);
   // tw[half - 1 + pos] = exp(-2 pi i pos / (2 half)), half = 1, 2, 4, ..., L/2
-  for (int k = threadIdx.x; k < L - 1; k += blockDim.x) {
+  for (int k = threadIdx.x; k < L - 1 && !tw_global; k += blockDim.x) {
     const int lh = 31 - __clz(k + 1);  // half = 2^lh <= k + 1 < 2 half
     const int half = 1 << lh, pos = k + 1 - half;
     double s, c;
@@ -235,6 +331,8 @@ __global__ void build_spectra_kernel(const double* __restrict__ t, int n, int lo
     tw[k] = {c, s};
     if (twout) twout[k] = to_cx<R>(tw[k]);
   }
+  if (tw_global && twout)
+    for (int k = threadIdx.x; k < L - 1; k += blockDim.x) twout[k] = to_cx<R>(tw[k]);
   // z = h1 + i h2: h1 embeds A (h1[d mod L] = t_d, d = -1..n-1) and h2 embeds
   // A^T (h2[m mod L] = t_{-m}, m = -(n-1)..1); L >= 2n - 1 keeps them apart.
   for (int m = threadIdx.x; m < L; m += blockDim.x) {
@@ -259,15 +357,33 @@ __global__ void build_spectra_kernel(const double* __restrict__ t, int n, int lo
   }
 }
 
+__global__ void twiddle_kernel(int L, cx<double>* tw) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L - 1; k += gridDim.x * blockDim.x) {
+    const int lh = 31 - __clz(k + 1);
+    const int half = 1 << lh, pos = k + 1 - half;
+    double s, c;
+    sincospi(-(double)pos / (double)half, &s, &c);
+    tw[k] = {c, s};
+  }
+}
+
 template <typename R>
 cudaError_t launch_build_spectra(const double* t, int n, int logL, double scale, cx<R>* S1,
-                                 cx<R>* S2, cx<R>* tw, cudaStream_t st) {
+                                 cx<R>* S2, cx<R>* tw, cudaStream_t st, cx<double>* tw_scratch) {
   const int L = 1 << logL;
-  const size_t smem = (size_t)(padded_len(L) + L) * sizeof(cx<double>);
+  size_t smem = (size_t)(padded_len(L) + L) * sizeof(cx<double>);
+  cx<double>* twg = nullptr;
+  if (smem > 227 * 1024) {  // twiddles in global memory
+    if (!tw_scratch) return cudaErrorInvalidValue;
+    twg = tw_scratch;
+    smem = (size_t)padded_len(L) * sizeof(cx<double>);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    twiddle_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, twg);
+  }
   cudaError_t e = cudaFuncSetAttribute(build_spectra_kernel<R>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
-  build_spectra_kernel<R><<<1, 512, smem, st>>>(t, n, logL, scale, S1, S2, tw);
+  build_spectra_kernel<R><<<1, 512, smem, st>>>(t, n, logL, scale, S1, S2, tw, twg);
   return cudaGetLastError();
 }
 
@@ -320,23 +436,26 @@ cudaError_t launch_direct_pass(const T* X, int es, int vs, int nvec, int n, cons
 template cudaError_t launch_fft_pass<double, double, double>(
     const double*, int, int, int, int, int, const cx<double>*, const cx<double>*,
     const cx<double>*, const double*, const double*, const double*, double, double*, int,
-    cudaStream_t);
+    cudaStream_t, cx<double>*, size_t);
 template cudaError_t launch_fft_pass<float, float, float>(const float*, int, int, int, int, int,
                                                           const cx<float>*, const cx<float>*,
                                                           const cx<float>*, const float*,
                                                           const float*, const float*, double,
-                                                          float*, int, cudaStream_t);
+                                                          float*, int, cudaStream_t, cx<float>*,
+                                                          size_t);
 template cudaError_t launch_fft_pass<double, df, df>(const double*, int, int, int, int, int,
                                                      const cx<df>*, const cx<df>*,
                                                      const cx<df>*, const df*, const df*,
                                                      const double*, double, double*, int,
-                                                     cudaStream_t);
+                                                     cudaStream_t, cx<df>*, size_t);
 template cudaError_t launch_build_spectra<df>(const double*, int, int, double, cx<df>*, cx<df>*,
-                                              cx<df>*, cudaStream_t);
+                                              cx<df>*, cudaStream_t, cx<double>*);
 template cudaError_t launch_build_spectra<double>(const double*, int, int, double, cx<double>*,
-                                                  cx<double>*, cx<double>*, cudaStream_t);
+                                                  cx<double>*, cx<double>*, cudaStream_t,
+                                                  cx<double>*);
 template cudaError_t launch_build_spectra<float>(const double*, int, int, double, cx<float>*,
-                                                 cx<float>*, cx<float>*, cudaStream_t);
+                                                 cx<float>*, cx<float>*, cudaStream_t,
+                                                 cx<double>*);
 template cudaError_t launch_direct_pass<double>(const double*, int, int, int, int, const double*,
                                                 const double*, const double*, const double*,
                                                 double, double*, int, cudaStream_t);
