@@ -99,13 +99,23 @@ typedef struct fde_params {
   int    cycles;           /* V-cycles per preconditioner application (0 or 1: one; at most 4);
                               cycle k + 1 corrects the residual of cycle k (Sec. 5.1 tries two
                               for P_2) */
+  int    relax;            /* 1: relaxed Krylov matvec -- once the FGMRES residual estimate is
+                              within FDE_RELAX_FACTOR of rtol ||b||, M z is evaluated in FP32
+                              (inexact Krylov: a matvec error of eta ||M|| ||z|| perturbs the
+                              residual by at most about eta times the current residual); the
+                              right-hand side and every true residual stay FP64-accurate, so
+                              the stopping test is unchanged.  0 (default): every matvec
+                              FP64-accurate, as in the paper's GMRES. */
 } fde_params;
+
+#define FDE_RELAX_FACTOR 1000.0
 
 typedef struct fde_stats {
   int    iterations;       /* inner FGMRES steps (= preconditioner applications) */
   int    restarts;         /* restart cycles begun */
   int    converged;        /* 1 if the true residual met rtol */
   double rel_residual;     /* ||b - M x||_2 / ||b||_2 at exit, true residual in FP64 */
+  int    relaxed;          /* Krylov matvecs evaluated in FP32 (fde_params.relax) */
 } fde_stats;
 
 typedef struct fde_handle fde_handle;

@@ -70,6 +70,11 @@ struct fde_handle {
   // transposed (n1 x n2) copies of sigma e+- for the column pass: FP64 and double-float
   double *epNsT = nullptr, *emNsT = nullptr, *epOsT = nullptr, *emOsT = nullptr;
   df *cfNT[2] = {nullptr, nullptr}, *cfOT[2] = {nullptr, nullptr};
+  // FP32 copies for the relaxed Krylov matvec (fde_params.relax): spectra and
+  // the t^(m) coefficients {dp, dm} and transposed {sigma ep, sigma em}
+  cx<float> *S1x32 = nullptr, *S2x32 = nullptr, *S1y32 = nullptr, *S2y32 = nullptr,
+            *twx32 = nullptr, *twy32 = nullptr;
+  float *cf32[2] = {nullptr, nullptr}, *cf32T[2] = {nullptr, nullptr};
   double *xT = nullptr, *yT = nullptr;  // transposed operand / result of the column pass
   // FFT passes whose two length-L buffers exceed shared memory (L = 8192 with
   // 16-byte complex values) park spectra here; also the twiddle scratch of
@@ -780,6 +785,23 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
   return FDE_OK;
 }
 
+// y = M^(m) x with FP32 arithmetic on FP64 data (relaxed Krylov matvec)
+static int outer_apply32(fde_handle* h, const double* x, double* y) {
+  cx<float>* ws = reinterpret_cast<cx<float>*>(h->fft_ws);
+  const size_t wse = h->fft_ws_elems * 2;
+  int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
+  LCHK((launch_fft_pass<double, float, float>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x32,
+                                              h->S2x32, h->twx32, h->cf32[0], h->cf32[1], x,
+                                              h->c, y, 0, h->st, ws, wse)));
+  LCHK(launch_transpose<double>(x, h->n2, h->n1, h->xT, 0, h->st));
+  LCHK((launch_fft_pass<double, float, float>(h->xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1y32,
+                                              h->S2y32, h->twy32, h->cf32T[0], h->cf32T[1],
+                                              nullptr, 0.0, h->yT, 0, h->st, ws, wse)));
+  LCHK(launch_transpose<double>(h->yT, h->n1, h->n2, y, 1, h->st));
+  h->pend(pi);
+  return FDE_OK;
+}
+
 static int norm2(fde_handle* h, const double* x, double* dev_out, double* host_out) {
   int pi = h->pbeg(FDE_KCLASS_KRYLOV);
   LCHK(launch_sumsq(x, h->N, h->part, h->nb, h->st));
@@ -804,7 +826,7 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
   const fde_params& p = h->p;
   const size_t N = h->N;
   const int m = p.restart;
-  fde_stats st{0, 0, 0, 0.0};
+  fde_stats st{0, 0, 0, 0.0, 0};
   double bnorm = 0.0;
   RCHK(norm2(h, b, h->hdev, &bnorm));
   CCHK(cudaMemsetAsync(x, 0, N * sizeof(double), h->st));
@@ -831,7 +853,13 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
       double* Zj = h->Z + (size_t)j * N;
       double* w = h->V + (size_t)(j + 1) * N;
       RCHK(precond(h, Vj, Zj));
-      RCHK(outer_apply(h, Zj, w, false));
+      // relaxed matvec once the residual estimate |g_j| is near the target
+      if (p.relax && std::fabs(g[j]) <= FDE_RELAX_FACTOR * tol) {
+        RCHK(outer_apply32(h, Zj, w));
+        st.relaxed++;
+      } else {
+        RCHK(outer_apply(h, Zj, w, false));
+      }
       // classical Gram-Schmidt, twice (CGS2); for 9 <= j + 1 <= 16 the first
       // subtraction and the second projection share one pass over V (measured
       // faster there; outside that range the two separate passes are)
@@ -950,6 +978,7 @@ static int validate(const fde_params* p, std::string& why) {
   if (p->maxit < 1) return bad("maxit must be >= 1");
   if (p->precond < FDE_PRECOND_NONE || p->precond > FDE_PRECOND_P2) return bad("unknown precond");
   if (p->cycles < 0 || p->cycles > 4) return bad("cycles must be in [0, 4]");
+  if (p->relax != 0 && p->relax != 1) return bad("relax must be 0 or 1");
   if (p->nu_pre < 0 || p->nu_pre > 4 || p->nu_post < 0 || p->nu_post > 4) return bad("nu in [0, 4]");
   if (!(p->omega > 0.0 && p->omega < 2.0)) return bad("omega must be in (0, 2)");
   if (p->coarsest_n < 1) return bad("coarsest_n must be >= 1");
@@ -1040,6 +1069,22 @@ int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
         RCHK(h->alloc(&h->cfOT[k], N));
       }
     }
+    if (p.relax) {
+      RCHK(h->alloc(&h->S1x32, (size_t)1 << h->logLx));
+      RCHK(h->alloc(&h->S2x32, (size_t)1 << h->logLx));
+      RCHK(h->alloc(&h->twx32, (size_t)1 << h->logLx));
+      RCHK(h->alloc(&h->S1y32, (size_t)1 << h->logLy));
+      RCHK(h->alloc(&h->S2y32, (size_t)1 << h->logLy));
+      RCHK(h->alloc(&h->twy32, (size_t)1 << h->logLy));
+      LCHK(launch_build_spectra<float>(h->tx0, p.n1, h->logLx, 1.0, h->S1x32, h->S2x32, h->twx32,
+                                       h->st, h->fft_ws));
+      LCHK(launch_build_spectra<float>(h->ty0, p.n2, h->logLy, 1.0, h->S1y32, h->S2y32, h->twy32,
+                                       h->st, h->fft_ws));
+      for (int k = 0; k < 2; ++k) {
+        RCHK(h->alloc(&h->cf32[k], N));
+        RCHK(h->alloc(&h->cf32T[k], N));
+      }
+    }
     double** fields[] = {&h->dpN, &h->dmN, &h->epN, &h->emN, &h->epNs, &h->emNs,
                          &h->dpO, &h->dmO, &h->epOs, &h->emOs, &h->tmp, &h->bwork,
                          &h->hu, &h->hv, &h->hx_out, &h->u_last, &h->epNsT, &h->emNsT,
@@ -1127,6 +1172,12 @@ int fde_set_coefficients(fde_handle* h, int which, const double* dp, const doubl
       LCHK(launch_to_df(N, em, h->sigma, h->cfN[3], h->st));
       LCHK(launch_to_df(N, h->epNsT, 1.0, h->cfNT[0], h->st));
       LCHK(launch_to_df(N, h->emNsT, 1.0, h->cfNT[1], h->st));
+    }
+    if (h->p.relax) {
+      LCHK((launch_convert<double, float>(N, dp, 1.0, h->cf32[0], h->st)));
+      LCHK((launch_convert<double, float>(N, dm, 1.0, h->cf32[1], h->st)));
+      LCHK((launch_convert<double, float>(N, h->epNsT, 1.0, h->cf32T[0], h->st)));
+      LCHK((launch_convert<double, float>(N, h->emNsT, 1.0, h->cf32T[1], h->st)));
     }
     h->have_new = true;
     if (h->mg) RCHK(h->mg->setup(h));

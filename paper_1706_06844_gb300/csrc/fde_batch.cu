@@ -146,7 +146,7 @@ int fde_batch_step(fde_batch* b, const double* const* u_prev, const double* cons
     pool.emplace_back([b, w, u_prev, v_half, u_next, st]() {
       cudaSetDevice(b->device);
       for (int i : b->work[w]) {
-        fde_stats s{0, 0, 0, 0.0};
+        fde_stats s{0, 0, 0, 0.0, 0};
         b->rc[i] = fde_step(b->h[i], u_prev[i], v_half[i], u_next[i], &s);
         if (st) st[i] = s;
       }

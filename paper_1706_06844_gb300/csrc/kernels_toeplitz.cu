@@ -443,6 +443,10 @@ template cudaError_t launch_fft_pass<float, float, float>(const float*, int, int
                                                           const float*, const float*, double,
                                                           float*, int, cudaStream_t, cx<float>*,
                                                           size_t);
+template cudaError_t launch_fft_pass<double, float, float>(
+    const double*, int, int, int, int, int, const cx<float>*, const cx<float>*, const cx<float>*,
+    const float*, const float*, const double*, double, double*, int, cudaStream_t, cx<float>*,
+    size_t);
 template cudaError_t launch_fft_pass<double, df, df>(const double*, int, int, int, int, int,
                                                      const cx<df>*, const cx<df>*,
                                                      const cx<df>*, const df*, const df*,

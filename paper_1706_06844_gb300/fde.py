@@ -33,12 +33,13 @@ class fde_params(ctypes.Structure):
                 ("precond", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("omega", ctypes.c_double), ("coarsest_n", ctypes.c_int),
                 ("precision", ctypes.c_int), ("toeplitz_path", ctypes.c_int),
-                ("outer", ctypes.c_int), ("cycles", ctypes.c_int)]
+                ("outer", ctypes.c_int), ("cycles", ctypes.c_int), ("relax", ctypes.c_int)]
 
 
 class fde_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
-                ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+                ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("relaxed", ctypes.c_int)]
 
 
 _lib = None

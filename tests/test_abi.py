@@ -46,7 +46,7 @@ def test_argument_errors_without_gpu():
         with pytest.raises(fde.FDEError) as e:
             fde.fde_create(fde.params(**kw))
         assert e.value.code == fde.FDE_ERR_ARG, kw
-    for kw in [dict(cycles=5), dict(cycles=-1)]:
+    for kw in [dict(cycles=5), dict(cycles=-1), dict(relax=2)]:
         with pytest.raises(fde.FDEError) as e:
             fde.fde_create(fde.params(**kw))
         assert e.value.code == fde.FDE_ERR_ARG, kw

@@ -272,3 +272,31 @@ def test_graph_replay_equals_eager_cycle(precond, precision, path, cycles):
             np.testing.assert_array_equal(o, outs[0])
     finally:
         fde.fde_destroy(h)
+
+
+@pytest.mark.parametrize("precision,path", [(fde.FDE_PREC_FP32, fde.FDE_PATH_AUTO),
+                                            (fde.FDE_PREC_BF16X3, fde.FDE_PATH_GEMM)])
+def test_relaxed_matvec_meets_the_same_true_residual(precision, path):
+    # with relax = 1 the late Krylov matvecs run in FP32; the oracle's FP64
+    # true residual of the result still meets rtol, and the iteration count
+    # stays within one of the exact-matvec solve
+    import torch
+    its = {}
+    for relax in (1, 0):
+        case = Case(inputs.perturbed_power_law(), 255, precision=precision, toeplitz_path=path,
+                    outer=fde.FDE_OUTER_DF32, rtol=1e-10, relax=relax)
+        h = case.handle()
+        try:
+            B = case.oracle_rhs()
+            x = torch.empty_like(dev(B))
+            st = fde.fde_solve(h, dev(B), x)
+            res = np.linalg.norm(B - case.oracle_apply(host(x))) / np.linalg.norm(B)
+            assert st.converged == 1 and res <= 1.05e-10, (relax, res)
+            its[relax] = st.iterations
+            if relax:
+                assert st.relaxed > 0
+            else:
+                assert st.relaxed == 0
+        finally:
+            fde.fde_destroy(h)
+    assert its[1] <= its[0] + 1, its
