@@ -121,7 +121,8 @@ class ClockSampler:
 class Workload:
     """Device-resident inputs of the time loop and one solver handle."""
 
-    def __init__(self, precision, path=None, outer=None, precond=None, cycles=1, relax=0):
+    def __init__(self, precision, path=None, outer=None, precond=None, cycles=1, relax=0,
+                 solver=0, warm=0):
         import torch
         from paper_1706_06844_gb300 import fde
         self.fde, self.torch = fde, torch
@@ -133,7 +134,7 @@ class Workload:
         kw = dict(alpha=prob.alpha, beta=prob.beta, qx=prob.qx, qy=prob.qy, a1=a1, b1=b1,
                   a2=a2, b2=b2, n1=n, n2=n, dt=self.dt, rtol=RTOL, restart=RESTART, maxit=2000,
                   precond=fde.FDE_PRECOND_MG_SG if precond is None else precond,
-                  precision=precision, cycles=cycles, relax=relax)
+                  precision=precision, cycles=cycles, relax=relax, solver=solver, warm=warm)
         if path is not None:
             kw["toeplitz_path"] = path
         if outer is not None:
@@ -241,7 +242,8 @@ def roofline(w, steps, outer):
     res = {}
     for k, name in [(fde.FDE_KCLASS_OUTER_APPLY, "outer_apply"),
                     (fde.FDE_KCLASS_LEVEL_APPLY, "level_apply"),
-                    (fde.FDE_KCLASS_KRYLOV, "krylov"), (fde.FDE_KCLASS_MG_OTHER, "mg_other")]:
+                    (fde.FDE_KCLASS_KRYLOV, "krylov"), (fde.FDE_KCLASS_MG_OTHER, "mg_other"),
+                    (fde.FDE_KCLASS_OUTER_FP32, "outer_apply_fp32")]:
         res[name] = fde.fde_profile_query(w.h, k)
     fde.fde_profile_enable(w.h, 0)
     work = fft_pass_work(N_GRID, outer)
@@ -458,6 +460,10 @@ def main():
                     help="1: FP32 Krylov matvecs once the residual estimate is within 1000x of "
                          "the target (the exit test stays on the FP64-accurate true residual); "
                          "0: every matvec FP64-accurate")
+    ap.add_argument("--solver", default="fgmres", choices=["fgmres", "mg"],
+                    help="mg: multigrid as the solver (x <- x + V(b - M x)) instead of FGMRES")
+    ap.add_argument("--warm", type=int, default=0, choices=[0, 1],
+                    help="1: start every step's solve from u^(m-1) (the paper starts from zero)")
     ap.add_argument("--workload", default="n2047", choices=["n2047", "batch256"],
                     help="n2047: the single 2047 x 2047 problem (replicated over ranks); "
                          "batch256: 256 independent problems sharded over ranks")
@@ -494,7 +500,9 @@ def main():
     outer = fde.FDE_OUTER_DF32 if args.outer == "df32" else fde.FDE_OUTER_FP64
     precond = {"sg": fde.FDE_PRECOND_MG_SG, "redisc": fde.FDE_PRECOND_MG_REDISC,
                "p2": fde.FDE_PRECOND_P2}[args.precond]
-    w = Workload(mixed, outer=outer, precond=precond, cycles=args.cycles, relax=args.relax)
+    solver = fde.FDE_SOLVER_MG if args.solver == "mg" else fde.FDE_SOLVER_FGMRES
+    w = Workload(mixed, outer=outer, precond=precond, cycles=args.cycles, relax=args.relax,
+                 solver=solver, warm=args.warm)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         ms, wall, its, launches = time_steps(w, args.steps, args.warmup, dist)
     ms = shard.max_over_ranks(ms, dist)
@@ -505,7 +513,8 @@ def main():
     exact = None
     if args.relax and not args.no_fp64:
         # the same mixed-precision solver with every Krylov matvec FP64-accurate
-        wx_ = Workload(mixed, outer=outer, precond=precond, cycles=args.cycles, relax=0)
+        wx_ = Workload(mixed, outer=outer, precond=precond, cycles=args.cycles, relax=0,
+                       solver=solver, warm=args.warm)
         kx = max(4, args.steps // 2)
         msx, _, itsx, _ = time_steps(wx_, kx, args.warmup, None)
         exact = {"value": round(kx / (msx * 1e-3), 4), "unit": "steps/s",
@@ -542,6 +551,7 @@ def main():
                            "precond": {"sg": "MG_SG", "redisc": "MG_REDISC",
                                        "p2": "P2"}[args.precond],
                            "cycles": args.cycles, "relaxed_matvec": bool(args.relax),
+                           "solver": args.solver, "warm_start": bool(args.warm),
                            "precision": f"{args.precision} V-cycle products (FP32 vectors), "
                                         f"{args.outer} FFT outer apply",
                            "l2": "inputs larger than L2 (Krylov basis 31 x 33.5 MB)",

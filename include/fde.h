@@ -106,7 +106,16 @@ typedef struct fde_params {
                               right-hand side and every true residual stay FP64-accurate, so
                               the stopping test is unchanged.  0 (default): every matvec
                               FP64-accurate, as in the paper's GMRES. */
+  int    solver;           /* FDE_SOLVER_FGMRES (default) or FDE_SOLVER_MG: multigrid as the
+                              solver itself, x <- x + V(b - M x) until the true residual meets
+                              rtol (Sec. 1 and Sec. 4.3: the multigrid method can run without a
+                              Krylov wrapper); restart is ignored, maxit caps the cycles */
+  int    warm;             /* 1: fde_step starts the solve from u_prev instead of zero (the
+                              paper starts from zero, Sec. 5) */
 } fde_params;
+
+#define FDE_SOLVER_FGMRES 0
+#define FDE_SOLVER_MG     1
 
 #define FDE_RELAX_FACTOR 1000.0
 
@@ -202,7 +211,8 @@ int fde_set_state(fde_handle* h, int m);
 #define FDE_KCLASS_LEVEL_APPLY  1  /* preconditioner Toeplitz products */
 #define FDE_KCLASS_KRYLOV       2  /* Arnoldi / update / norm kernels */
 #define FDE_KCLASS_MG_OTHER     3  /* smoother, transfers, coarse solve */
-#define FDE_KCLASS_COUNT        4
+#define FDE_KCLASS_OUTER_FP32   4  /* relaxed (FP32) Krylov matvecs, whole apply */
+#define FDE_KCLASS_COUNT        5
 int fde_profile_enable(fde_handle* h, int on);
 int fde_profile_query(fde_handle* h, int kclass, long long* launches, double* ms);
 /* Total kernels this handle has launched. */

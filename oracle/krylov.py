@@ -1,6 +1,7 @@
 """Restarted GMRES, as used for every linear solve of Sec. 5 (restart length,
 relative-residual tolerance, zero initial guess), in its flexible
-right-preconditioned form.
+right-preconditioned form; and multigrid used on its own as the solver
+(Sec. 1 and Sec. 4.3 note that the method can run without a Krylov wrapper).
 
 Arnoldi by modified Gram-Schmidt, least squares by Givens rotations, and the
 true residual ||b - M x|| recomputed at every restart.  The iteration count is
@@ -82,3 +83,22 @@ def gmres_left(apply_A, b, precond, restart=20, rtol=1e-7, maxit=10000):
     x, its, rel, ok = fgmres(lambda v: PA(np.asarray(v).ravel()).reshape(shape), pb, None,
                              restart, rtol, maxit)
     return x, its, rel, ok
+
+
+def mg_solve(apply_A, b, vcycle, rtol=1e-8, maxit=1000, x0=None):
+    """Multigrid as a stand-alone solver: the stationary iteration
+    x_{k+1} = x_k + V(b - A x_k), V one V-cycle from a zero initial guess, until
+    ||b - A x|| <= rtol ||b||.  Returns (x, cycles, relative residual, converged)."""
+    b = np.asarray(b, dtype=np.float64)
+    bnorm = np.linalg.norm(b)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    if bnorm == 0.0:
+        return x, 0, 0.0, True
+    k = 0
+    while True:
+        r = b - apply_A(x)
+        rel = np.linalg.norm(r) / bnorm
+        if rel <= rtol or k >= maxit:
+            return x, k, rel, bool(rel <= rtol)
+        x = x + vcycle(r)
+        k += 1

@@ -96,8 +96,8 @@ struct fde_handle {
   bool prof = false;
   std::vector<ProfEvent> pending;
   std::vector<cudaEvent_t> pool;
-  long long prof_launches[FDE_KCLASS_COUNT] = {0, 0, 0, 0};
-  double prof_ms[FDE_KCLASS_COUNT] = {0, 0, 0, 0};
+  long long prof_launches[FDE_KCLASS_COUNT] = {};
+  double prof_ms[FDE_KCLASS_COUNT] = {};
 
   int fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -789,7 +789,7 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
 static int outer_apply32(fde_handle* h, const double* x, double* y) {
   cx<float>* ws = reinterpret_cast<cx<float>*>(h->fft_ws);
   const size_t wse = h->fft_ws_elems * 2;
-  int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
+  int pi = h->pbeg(FDE_KCLASS_OUTER_FP32);
   LCHK((launch_fft_pass<double, float, float>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x32,
                                               h->S2x32, h->twx32, h->cf32[0], h->cf32[1], x,
                                               h->c, y, 0, h->st, ws, wse)));
@@ -822,24 +822,85 @@ static int precond(fde_handle* h, const double* v, double* z) {
   return h->mg->vcycle(h, v, z);
 }
 
-static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_out) {
+// Multigrid as the solver (fde_params.solver = FDE_SOLVER_MG): the stationary
+// iteration x <- x + V(b - M x) with the FP64-accurate residual as the test.
+static int solve_mg(fde_handle* h, const double* b, double* x, fde_stats* st_out,
+                    const double* x0) {
+  const fde_params& p = h->p;
+  const size_t N = h->N;
+  fde_stats st{0, 1, 0, 0.0, 0};
+  double bnorm = 0.0;
+  RCHK(norm2(h, b, h->hdev, &bnorm));
+  if (!std::isfinite(bnorm)) return h->fail(FDE_ERR_NONFINITE, "right-hand side is not finite");
+  if (x0) CCHK(cudaMemcpyAsync(x, x0, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  else CCHK(cudaMemsetAsync(x, 0, N * sizeof(double), h->st));
+  const double tol = p.rtol * bnorm;
+  int status = FDE_ERR_NOT_CONVERGED;
+  for (;;) {
+    // r = b - M x (r = b while x = 0)
+    if (x0 || st.iterations > 0) {
+      RCHK(outer_apply(h, x, h->tmp, false));
+      LCHK(launch_sub(N, b, h->tmp, h->tmp, h->st));
+    } else {
+      CCHK(cudaMemcpyAsync(h->tmp, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    }
+    double rn = 0.0;
+    RCHK(norm2(h, h->tmp, h->h2dev, &rn));
+    if (!std::isfinite(rn)) return h->fail(FDE_ERR_NONFINITE, "non-finite residual");
+    st.rel_residual = bnorm > 0.0 ? rn / bnorm : 0.0;
+    if (rn <= tol) {
+      status = FDE_OK;
+      st.converged = 1;
+      break;
+    }
+    if (st.iterations >= p.maxit) break;
+    RCHK(precond(h, h->tmp, h->Z));
+    LCHK(launch_lincomb(N, 1.0, x, 1.0, h->Z, 0.0, nullptr, x, h->st));
+    st.iterations++;
+  }
+  if (st_out) *st_out = st;
+  if (status == FDE_ERR_NOT_CONVERGED)
+    h->fail(FDE_ERR_NOT_CONVERGED, "not converged: %d cycles, relative residual %.3e",
+            st.iterations, st.rel_residual);
+  return status;
+}
+
+static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_out,
+                      const double* x0) {
   const fde_params& p = h->p;
   const size_t N = h->N;
   const int m = p.restart;
   fde_stats st{0, 0, 0, 0.0, 0};
   double bnorm = 0.0;
   RCHK(norm2(h, b, h->hdev, &bnorm));
-  CCHK(cudaMemsetAsync(x, 0, N * sizeof(double), h->st));
   if (!std::isfinite(bnorm)) return h->fail(FDE_ERR_NONFINITE, "right-hand side is not finite");
   if (bnorm == 0.0) {
+    CCHK(cudaMemsetAsync(x, 0, N * sizeof(double), h->st));
     st.converged = 1;
     if (st_out) *st_out = st;
     CCHK(cudaStreamSynchronize(h->st));
     return FDE_OK;
   }
-  // V_0 = b / ||b||
-  LCHK(launch_scale_inv(N, b, h->hdev, h->V, h->st));
   double beta = bnorm;
+  if (x0) {
+    // warm start: FGMRES on the correction, from r_0 = b - M x_0
+    CCHK(cudaMemcpyAsync(x, x0, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    RCHK(outer_apply(h, x, h->tmp, false));
+    LCHK(launch_sub(N, b, h->tmp, h->tmp, h->st));
+    RCHK(norm2(h, h->tmp, h->h2dev, &beta));
+    if (!std::isfinite(beta)) return h->fail(FDE_ERR_NONFINITE, "non-finite residual");
+    st.rel_residual = beta / bnorm;
+    if (beta <= p.rtol * bnorm) {
+      st.converged = 1;
+      if (st_out) *st_out = st;
+      return FDE_OK;
+    }
+    LCHK(launch_scale_inv(N, h->tmp, h->h2dev, h->V, h->st));
+  } else {
+    CCHK(cudaMemsetAsync(x, 0, N * sizeof(double), h->st));
+    // V_0 = b / ||b||
+    LCHK(launch_scale_inv(N, b, h->hdev, h->V, h->st));
+  }
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), col(m + 2), y(m);
   const double tol = p.rtol * bnorm;
   int status = FDE_ERR_NOT_CONVERGED;
@@ -979,6 +1040,10 @@ static int validate(const fde_params* p, std::string& why) {
   if (p->precond < FDE_PRECOND_NONE || p->precond > FDE_PRECOND_P2) return bad("unknown precond");
   if (p->cycles < 0 || p->cycles > 4) return bad("cycles must be in [0, 4]");
   if (p->relax != 0 && p->relax != 1) return bad("relax must be 0 or 1");
+  if (p->solver != FDE_SOLVER_FGMRES && p->solver != FDE_SOLVER_MG) return bad("unknown solver");
+  if (p->solver == FDE_SOLVER_MG && p->precond == FDE_PRECOND_NONE)
+    return bad("the multigrid solver needs a multigrid precond");
+  if (p->warm != 0 && p->warm != 1) return bad("warm must be 0 or 1");
   if (p->nu_pre < 0 || p->nu_pre > 4 || p->nu_post < 0 || p->nu_post > 4) return bad("nu in [0, 4]");
   if (!(p->omega > 0.0 && p->omega < 2.0)) return bad("omega must be in (0, 2)");
   if (p->coarsest_n < 1) return bad("coarsest_n must be >= 1");
@@ -1260,7 +1325,8 @@ int fde_solve(fde_handle* h, const double* b, double* x, fde_stats* st) {
   if (!h) return FDE_ERR_ARG;
   if (!b || !x || b == x) return h->fail(FDE_ERR_ARG, "null or aliased pointer");
   if (!h->have_new) return h->fail(FDE_ERR_ARG, "FDE_COEF_NEW coefficients not set");
-  int r = solve_impl(h, b, x, st);
+  int r = h->p.solver == FDE_SOLVER_MG ? solve_mg(h, b, x, st, nullptr)
+                                       : solve_impl(h, b, x, st, nullptr);
   h->prof_collect();
   return r;
 }
@@ -1271,7 +1337,11 @@ int fde_step(fde_handle* h, const double* u_prev, const double* v_half, double* 
   if (!u_prev || !v_half || !u_next || u_prev == u_next)
     return h->fail(FDE_ERR_ARG, "null or aliased pointer");
   RCHK(fde_rhs(h, u_prev, v_half, h->bwork));
-  int r = fde_solve(h, h->bwork, u_next, st);
+  if (!h->have_new) return h->fail(FDE_ERR_ARG, "FDE_COEF_NEW coefficients not set");
+  const double* x0 = h->p.warm ? u_prev : nullptr;
+  int r = h->p.solver == FDE_SOLVER_MG ? solve_mg(h, h->bwork, u_next, st, x0)
+                                       : solve_impl(h, h->bwork, u_next, st, x0);
+  h->prof_collect();
   if (r == FDE_OK || r == FDE_ERR_NOT_CONVERGED) {
     CCHK(cudaMemcpyAsync(h->u_last, u_next, h->N * 8, cudaMemcpyDeviceToDevice, h->st));
     h->m++;

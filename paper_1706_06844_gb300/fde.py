@@ -18,8 +18,10 @@ FDE_PRECOND_NONE, FDE_PRECOND_MG_SG, FDE_PRECOND_MG_REDISC, FDE_PRECOND_P2 = 0, 
 FDE_PREC_FP64, FDE_PREC_FP32, FDE_PREC_BF16, FDE_PREC_FP16, FDE_PREC_BF16X3 = 0, 1, 2, 3, 4
 FDE_PATH_AUTO, FDE_PATH_GEMM, FDE_PATH_FFT, FDE_PATH_DIRECT = 0, 1, 2, 3
 FDE_OUTER_FP64, FDE_OUTER_DF32 = 0, 1
+FDE_SOLVER_FGMRES, FDE_SOLVER_MG = 0, 1
 FDE_COEF_NEW, FDE_COEF_OLD = 0, 1
 FDE_KCLASS_OUTER_APPLY, FDE_KCLASS_LEVEL_APPLY, FDE_KCLASS_KRYLOV, FDE_KCLASS_MG_OTHER = 0, 1, 2, 3
+FDE_KCLASS_OUTER_FP32, FDE_KCLASS_COUNT = 4, 5
 
 
 class fde_params(ctypes.Structure):
@@ -33,7 +35,8 @@ class fde_params(ctypes.Structure):
                 ("precond", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("omega", ctypes.c_double), ("coarsest_n", ctypes.c_int),
                 ("precision", ctypes.c_int), ("toeplitz_path", ctypes.c_int),
-                ("outer", ctypes.c_int), ("cycles", ctypes.c_int), ("relax", ctypes.c_int)]
+                ("outer", ctypes.c_int), ("cycles", ctypes.c_int), ("relax", ctypes.c_int),
+                ("solver", ctypes.c_int), ("warm", ctypes.c_int)]
 
 
 class fde_stats(ctypes.Structure):

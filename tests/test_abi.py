@@ -46,7 +46,8 @@ def test_argument_errors_without_gpu():
         with pytest.raises(fde.FDEError) as e:
             fde.fde_create(fde.params(**kw))
         assert e.value.code == fde.FDE_ERR_ARG, kw
-    for kw in [dict(cycles=5), dict(cycles=-1), dict(relax=2)]:
+    for kw in [dict(cycles=5), dict(cycles=-1), dict(relax=2), dict(solver=2), dict(warm=3),
+               dict(solver=1, precond=0)]:
         with pytest.raises(fde.FDEError) as e:
             fde.fde_create(fde.params(**kw))
         assert e.value.code == fde.FDE_ERR_ARG, kw

@@ -300,3 +300,50 @@ def test_relaxed_matvec_meets_the_same_true_residual(precision, path):
         finally:
             fde.fde_destroy(h)
     assert its[1] <= its[0] + 1, its
+
+
+@pytest.mark.parametrize("precision,tol", [(fde.FDE_PREC_FP64, 1), (fde.FDE_PREC_FP32, 2)])
+@pytest.mark.parametrize("precond", [fde.FDE_PRECOND_MG_SG, fde.FDE_PRECOND_P2])
+def test_multigrid_solver_matches_oracle(precision, tol, precond):
+    # multigrid as the solver: x <- x + V(b - M x) until the true residual meets
+    # rtol; the oracle's stationary iteration needs the same number of cycles
+    import torch
+    from oracle.krylov import mg_solve
+    from oracle import multigrid as mg
+    case = Case(inputs.perturbed_power_law(), 127, precond=precond, precision=precision,
+                solver=fde.FDE_SOLVER_MG, rtol=1e-9, maxit=400)
+    h = case.handle()
+    try:
+        B = case.oracle_rhs()
+        x = torch.empty_like(dev(B))
+        st = fde.fde_solve(h, dev(B), x)
+        res = np.linalg.norm(B - case.oracle_apply(host(x))) / np.linalg.norm(B)
+        assert st.converged == 1 and res <= 1.05e-9, res
+        hier = case.oracle_hierarchy()
+        xo, cyc, rel, ok = mg_solve(case.oracle_apply, B, lambda R: mg.vcycle(hier, R), 1e-9, 400)
+        assert ok and abs(st.iterations - cyc) <= tol, (st.iterations, cyc)
+    finally:
+        fde.fde_destroy(h)
+
+
+@pytest.mark.parametrize("solver", [fde.FDE_SOLVER_FGMRES, fde.FDE_SOLVER_MG])
+def test_warm_start_step(solver):
+    # warm = 1 starts each step's solve from u^(m-1): fewer iterations, the
+    # same true-residual tolerance (checked by the oracle's FP64 operator)
+    import torch
+    counts = {}
+    for warm in (0, 1):
+        case = Case(inputs.perturbed_power_law(), 127, precision=fde.FDE_PREC_FP32,
+                    solver=solver, warm=warm, rtol=1e-9, maxit=400)
+        h = case.handle()
+        try:
+            B = case.oracle_rhs()
+            u0 = dev(case.u0)
+            x = torch.empty_like(u0)
+            st = fde.fde_step(h, u0, dev(case.v), x)
+            res = np.linalg.norm(B - case.oracle_apply(host(x))) / np.linalg.norm(B)
+            assert st.converged == 1 and res <= 1.05e-9, (warm, res)
+            counts[warm] = st.iterations
+        finally:
+            fde.fde_destroy(h)
+    assert counts[1] < counts[0], counts

@@ -265,3 +265,62 @@ def test_p2_two_cycles_beat_one():
         assert ok
         counts.append(its)
     assert counts[1] < counts[0], counts
+
+
+# ----------------------------------------------------------------------------
+# multigrid as a stand-alone solver; warm starts
+
+def test_mg_solve_error_follows_the_tgm_iteration_matrix():
+    # two levels with an exact coarse solve: every cycle multiplies the error by
+    # TGM(S, P) (Sec. 4), so after k cycles e_k = T^k e_0 with T built from the
+    # matrices (independent of the recursive cycle code)
+    from oracle.krylov import mg_solve
+    n = 15
+    wx, wy = wsgd_weights(1.6, n), wsgd_weights(1.8, n)
+    cf = tuple(rng.uniform(0.5, 2, (n, n)) for _ in range(4))
+    K0 = assemble_M(toeplitz_A(wx, n), toeplitz_A(wy, n), 0.3, 1.1, *cf)
+    h = mg.exact_galerkin(K0, n, n)
+    P = np.kron(mg.prolongation_1d(n), mg.prolongation_1d(n))
+    T = mg.tgm_matrix(K0, P, 0.7, nu_pre=1, nu_post=1)
+    b = rng.standard_normal((n, n))
+    xs = np.linalg.solve(K0, b.ravel())
+    apply = lambda X: (K0 @ X.ravel()).reshape(n, n)
+    for k in (1, 2, 5):
+        x, cyc, rel, ok = mg_solve(apply, b, lambda R: mg.vcycle(h, R), rtol=0.0, maxit=k)
+        assert cyc == k
+        np.testing.assert_allclose(x.ravel() - xs, np.linalg.matrix_power(T, k) @ (-xs),
+                                   rtol=1e-9, atol=1e-12)
+
+
+def test_mg_solve_converges_to_direct_solve():
+    from oracle.krylov import mg_solve
+    n = 31
+    al, be = 1.5, 1.7
+    wx, wy = wsgd_weights(al, n, 1, -1), wsgd_weights(be, n, 1, -1)
+    X, Y = np.meshgrid(np.arange(1, n + 1) / (n + 1), np.arange(1, n + 1) / (n + 1))
+    cf = (1 + X ** al * Y, 1 + (1 - X) ** al * Y, 1 + Y ** be * X, 1 + (1 - Y) ** be * X)
+    hier = mg.structured_galerkin(wx, wy, n, n, 0.35, 1.8, cf)
+    A = lambda Z: apply_M(Z, wx, wy, 0.35, 1.8, *cf)
+    b = rng.standard_normal((n, n))
+    x, cyc, rel, ok = mg_solve(A, b, lambda R: mg.vcycle(hier, R), 1e-10, 500)
+    K = assemble_M(toeplitz_A(wx, n), toeplitz_A(wy, n), 0.35, 1.8, *cf)
+    assert ok and rel <= 1e-10
+    np.testing.assert_allclose(x.ravel(), np.linalg.solve(K, b.ravel()), rtol=0, atol=1e-8 * np.abs(x).max())
+    # a warm start at the solution needs no cycle; one near it needs fewer
+    x2, cyc2, _, ok2 = mg_solve(A, b, lambda R: mg.vcycle(hier, R), 1e-10, 500, x0=x)
+    assert ok2 and cyc2 == 0
+
+
+def test_fgmres_warm_start():
+    from oracle.timeloop import make_preconditioner
+    n = 31
+    wx, wy = wsgd_weights(1.5, n), wsgd_weights(1.7, n)
+    cf = tuple(rng.uniform(0.5, 2, (n, n)) for _ in range(4))
+    A = lambda Z: apply_M(Z, wx, wy, 0.35, 1.8, *cf)
+    prec, _ = make_preconditioner("sg", 1.5, 1.7, wx, wy, n, n, {"c": 0.35, "sigma": 1.8}, cf)
+    b = rng.standard_normal((n, n))
+    x, its, rel, ok = fgmres(A, b, prec, 30, 1e-10)
+    x0 = x + 1e-6 * rng.standard_normal((n, n))
+    xw, itsw, relw, okw = fgmres(A, b, prec, 30, 1e-10, x0=x0)
+    assert ok and okw and itsw < its
+    assert np.linalg.norm(A(xw) - b) <= 1.0001e-10 * np.linalg.norm(b)
