@@ -147,6 +147,7 @@ class Workload:
         self.u = [d(prob.exact(X, Y, 0.0)), torch.empty((n, n), dtype=torch.float64, device="cuda")]
         self.vsrc = {}
         self.m = 0
+        self.first = None
         self.d = d
 
     def source(self, m):
@@ -158,6 +159,8 @@ class Workload:
         self.m += 1
         st = self.fde.fde_step(self.h, self.u[0], self.source(self.m), self.u[1])
         self.u.reverse()
+        if self.m == 1:  # kept for the accuracy check against the oracle
+            self.first = self.u[0].cpu().numpy()
         return st
 
     def close(self):
@@ -270,10 +273,12 @@ def roofline(w, steps, outer):
             "share_of_profiled_time": {k: round(v[1] / total_ms, 4) for k, v in res.items()}}
 
 
-def cpu_baseline_sample():
+def cpu_baseline_sample(refine=False):
     """The FP64 oracle as it stands, timed on this host: one CN step at the
     bench grid (right-hand side + FGMRES(30) with the structured-Galerkin
-    V-cycle to rtol 1e-8), after a one-off hierarchy set-up that is not timed."""
+    V-cycle to rtol 1e-8), after a one-off hierarchy set-up that is not timed.
+    With refine, the oracle's solution is then driven on (untimed) to rtol
+    1e-12 and returned as the reference solution of step 1."""
     from oracle.wsgd import wsgd_weights
     from oracle.operator import cn_scalars, rhs_fft, apply_M_fft
     from oracle import multigrid as mg
@@ -291,9 +296,12 @@ def cpu_baseline_sample():
     V = prob.source(X, Y, 0.5 * dt)
     t0 = time.perf_counter()
     B = rhs_fft(U, wx, wy, c, s, *coef, V, hx, prob.alpha)
-    x, its, rel, ok = fgmres(lambda Z: apply_M_fft(Z, wx, wy, c, s, *coef), B,
-                             lambda R: mg.vcycle(hier, R), RESTART, RTOL)
+    A = lambda Z: apply_M_fft(Z, wx, wy, c, s, *coef)
+    x, its, rel, ok = fgmres(A, B, lambda R: mg.vcycle(hier, R), RESTART, RTOL)
     t = time.perf_counter() - t0
+    if refine:
+        xr, _, _, _ = fgmres(A, B, lambda R: mg.vcycle(hier, R), RESTART, 1e-12, x0=x)
+        return t, its, xr
     return t, its
 
 
@@ -509,6 +517,7 @@ def main():
     value = world * args.steps / (ms * 1e-3)
     e2e_v, h2d, d2h = e2e_steps(w, max(2, min(args.steps, 4)))
     roof = roofline(w, 2, args.outer)
+    first = w.first
     w.close()
     exact = None
     if args.relax and not args.no_fp64:
@@ -531,11 +540,17 @@ def main():
                 "note": "plain FP64 GPU solver: same FGMRES(30), FP64 V-cycle with FFT products"}
         w64.close()
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, k = cpu_baseline_sample()
+        t, k, xref = cpu_baseline_sample(refine=True)
         cpu = {"value": round(1.0 / t, 5), "unit": "steps/s", "cores": os.cpu_count(),
                "kind": "oracle", "sample": f"one CN step at n=2047 of the FP64 numpy oracle "
                                            f"({k} FGMRES iterations, {t:.1f} s)"}
+        err = float(np.linalg.norm(first - xref) / np.linalg.norm(xref))
+        accuracy = {"rel_l2_vs_oracle": err, "step": 1, "gpu_rtol": RTOL,
+                    "oracle": "FP64 numpy FGMRES + SG V-cycle driven to rtol 1e-12",
+                    "iterations_gpu": its[0] if its else None,
+                    "iterations_fp64_gpu": (fp64 or {}).get("iterations_per_step", [None])[0]}
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -560,7 +575,8 @@ def main():
                 "e2e": {"value": round(e2e_v, 4), "unit": "steps/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches), "roofline": roof, "clocks": clk.summary(),
-                "fp64_gpu": fp64, "exact_matvec": exact, "cpu_baseline": cpu}
+                "fp64_gpu": fp64, "exact_matvec": exact, "cpu_baseline": cpu,
+                "accuracy": accuracy}
         if fp64:
             line["speedup_vs_fp64_gpu"] = round(value / world / fp64["value"], 3)
         print(json.dumps(line), flush=True)

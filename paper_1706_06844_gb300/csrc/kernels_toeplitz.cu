@@ -48,7 +48,14 @@ __host__ __device__ constexpr int padded_len(int L) { return L + (L >> 4); }
 // One fused decimation-in-frequency pass: stages s .. s+q-1 (Q = 2^q points per
 // thread group, held in registers).  Group g covers the points
 // i0 + m h, m < Q, with h = L >> (s+q) the span of the last stage.
-template <int Q, typename R>
+// With h = 1 (UNIT: the last forward / first inverse pass) the twiddles of
+// spans 1 and 2, and half of those of span 4, are exactly 1 or -i: those
+// butterflies skip the multiply (multiplying by -i swaps and negates).
+template <typename R>
+__device__ __forceinline__ cx<R> mul_neg_i(cx<R> a) { return {a.im, -a.re}; }  // a * (-i)
+template <typename R>
+__device__ __forceinline__ cx<R> mul_i(cx<R> a) { return {-a.im, a.re}; }      // a * i
+template <int Q, bool UNIT, typename R>
 __device__ __forceinline__ void dif_group(cx<R>* a, int i0, int h, int pos,
                                           const cx<R>* __restrict__ tw) {
   cx<R> v[Q];
@@ -60,10 +67,17 @@ __device__ __forceinline__ void dif_group(cx<R>* a, int i0, int h, int pos,
 #pragma unroll
     for (int m = 0; m < Q; ++m) {
       if (m & sm) continue;
-      const cx<R> w = tw[span - 1 + pos + (m & (sm - 1)) * h];
       const cx<R> u = v[m], x = v[m + sm];
       v[m] = cadd(u, x);
-      v[m + sm] = cmul(csub(u, x), w);
+      const int k = m & (sm - 1);  // twiddle exponent within the span (pos = 0 when UNIT)
+      if (UNIT && (sm == 1 || k == 0)) {
+        v[m + sm] = csub(u, x);  // w = 1
+      } else if (UNIT && 2 * k == sm) {
+        v[m + sm] = mul_neg_i(csub(u, x));  // w = -i
+      } else {
+        const cx<R> w = tw[span - 1 + pos + k * h];
+        v[m + sm] = cmul(csub(u, x), w);
+      }
     }
   }
 #pragma unroll
@@ -72,7 +86,7 @@ __device__ __forceinline__ void dif_group(cx<R>* a, int i0, int h, int pos,
 
 // One fused decimation-in-time inverse pass: stages s .. s+q-1 (spans h .. 2^(q-1) h,
 // h = 2^s), conjugated twiddles.
-template <int Q, typename R>
+template <int Q, bool UNIT, typename R>
 __device__ __forceinline__ void dit_group(cx<R>* a, int i0, int h, int pos,
                                           const cx<R>* __restrict__ tw) {
   cx<R> v[Q];
@@ -84,8 +98,16 @@ __device__ __forceinline__ void dit_group(cx<R>* a, int i0, int h, int pos,
 #pragma unroll
     for (int m = 0; m < Q; ++m) {
       if (m & sm) continue;
-      const cx<R> w = tw[span - 1 + pos + (m & (sm - 1)) * h];
-      const cx<R> t = cmulc(v[m + sm], w);
+      const int k = m & (sm - 1);
+      cx<R> t;
+      if (UNIT && (sm == 1 || k == 0)) {
+        t = v[m + sm];  // conj(1) = 1
+      } else if (UNIT && 2 * k == sm) {
+        t = mul_i(v[m + sm]);  // conj(-i) = i
+      } else {
+        const cx<R> w = tw[span - 1 + pos + k * h];
+        t = cmulc(v[m + sm], w);
+      }
       const cx<R> u = v[m];
       v[m] = cadd(u, t);
       v[m + sm] = csub(u, t);
@@ -108,9 +130,15 @@ __device__ void fft_dif(cx<R>* a, int logL, const cx<R>* __restrict__ tw) {
     for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
       const int pos = g & (h - 1);
       const int i0 = ((g >> lh) << (lh + q)) + pos;
-      if (q == 4) dif_group<16>(a, i0, h, pos, tw);
-      else if (q == 2) dif_group<4>(a, i0, h, pos, tw);
-      else dif_group<2>(a, i0, h, pos, tw);
+      if (h == 1) {
+        if (q == 4) dif_group<16, true>(a, i0, h, pos, tw);
+        else if (q == 2) dif_group<4, true>(a, i0, h, pos, tw);
+        else dif_group<2, true>(a, i0, h, pos, tw);
+      } else {
+        if (q == 4) dif_group<16, false>(a, i0, h, pos, tw);
+        else if (q == 2) dif_group<4, false>(a, i0, h, pos, tw);
+        else dif_group<2, false>(a, i0, h, pos, tw);
+      }
     }
     __syncthreads();
     s += q;
@@ -133,9 +161,15 @@ __device__ void fft_dit_inv2(cx<R>* a, cx<R>* c, int logL, const cx<R>* __restri
       const int g = gg < ngroups ? gg : gg - ngroups;
       const int pos = g & (h - 1);
       const int i0 = ((g >> s) << (s + q)) + pos;
-      if (q == 4) dit_group<16>(arr, i0, h, pos, tw);
-      else if (q == 2) dit_group<4>(arr, i0, h, pos, tw);
-      else dit_group<2>(arr, i0, h, pos, tw);
+      if (h == 1) {
+        if (q == 4) dit_group<16, true>(arr, i0, h, pos, tw);
+        else if (q == 2) dit_group<4, true>(arr, i0, h, pos, tw);
+        else dit_group<2, true>(arr, i0, h, pos, tw);
+      } else {
+        if (q == 4) dit_group<16, false>(arr, i0, h, pos, tw);
+        else if (q == 2) dit_group<4, false>(arr, i0, h, pos, tw);
+        else dit_group<2, false>(arr, i0, h, pos, tw);
+      }
     }
     __syncthreads();
     s += q;
