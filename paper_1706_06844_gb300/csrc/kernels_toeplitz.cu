@@ -55,6 +55,15 @@ template <typename R>
 __device__ __forceinline__ cx<R> mul_neg_i(cx<R> a) { return {a.im, -a.re}; }  // a * (-i)
 template <typename R>
 __device__ __forceinline__ cx<R> mul_i(cx<R> a) { return {-a.im, a.re}; }      // a * i
+// The double-float passes already use every register the 512-thread block
+// allows; a second specialised copy of the butterflies pushes them into local
+// memory and costs more than the skipped multiplies save (measured), so they
+// keep the general path.
+template <typename R>
+constexpr bool kUnitPass = true;
+template <>
+constexpr bool kUnitPass<df> = false;
+
 template <int Q, bool UNIT, typename R>
 __device__ __forceinline__ void dif_group(cx<R>* a, int i0, int h, int pos,
                                           const cx<R>* __restrict__ tw) {
@@ -130,7 +139,7 @@ __device__ void fft_dif(cx<R>* a, int logL, const cx<R>* __restrict__ tw) {
     for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
       const int pos = g & (h - 1);
       const int i0 = ((g >> lh) << (lh + q)) + pos;
-      if (h == 1) {
+      if (h == 1 && kUnitPass<R>) {
         if (q == 4) dif_group<16, true>(a, i0, h, pos, tw);
         else if (q == 2) dif_group<4, true>(a, i0, h, pos, tw);
         else dif_group<2, true>(a, i0, h, pos, tw);
@@ -161,7 +170,7 @@ __device__ void fft_dit_inv2(cx<R>* a, cx<R>* c, int logL, const cx<R>* __restri
       const int g = gg < ngroups ? gg : gg - ngroups;
       const int pos = g & (h - 1);
       const int i0 = ((g >> s) << (s + q)) + pos;
-      if (h == 1) {
+      if (h == 1 && kUnitPass<R>) {
         if (q == 4) dit_group<16, true>(arr, i0, h, pos, tw);
         else if (q == 2) dit_group<4, true>(arr, i0, h, pos, tw);
         else dit_group<2, true>(arr, i0, h, pos, tw);
@@ -348,7 +357,8 @@ cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int log
 
 // ---------------------------------------------------------------- spectra
 template <typename R>
-__global__ void build_spectra_kernel(const double* __restrict__ t, int n, int logL, double scale,
+__global__ void __launch_bounds__(512)
+build_spectra_kernel(const double* __restrict__ t, int n, int logL, double scale,
                                      cx<R>* S1, cx<R>* S2, cx<R>* twout, cx<double>* tw_global) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 1 << logL;
