@@ -468,6 +468,9 @@ def main():
                     help="1: FP32 Krylov matvecs once the residual estimate is within 1000x of "
                          "the target (the exit test stays on the FP64-accurate true residual); "
                          "0: every matvec FP64-accurate")
+    ap.add_argument("--path", default="tune", choices=["tune", "auto", "gemm", "fft"],
+                    help="level product path: tune = time tensor-core vs FFT products per level "
+                         "at set-up and keep the faster; auto = fixed size rule")
     ap.add_argument("--solver", default="fgmres", choices=["fgmres", "mg"],
                     help="mg: multigrid as the solver (x <- x + V(b - M x)) instead of FGMRES")
     ap.add_argument("--warm", type=int, default=0, choices=[0, 1],
@@ -509,21 +512,28 @@ def main():
     precond = {"sg": fde.FDE_PRECOND_MG_SG, "redisc": fde.FDE_PRECOND_MG_REDISC,
                "p2": fde.FDE_PRECOND_P2}[args.precond]
     solver = fde.FDE_SOLVER_MG if args.solver == "mg" else fde.FDE_SOLVER_FGMRES
-    w = Workload(mixed, outer=outer, precond=precond, cycles=args.cycles, relax=args.relax,
-                 solver=solver, warm=args.warm)
+    path = {"tune": fde.FDE_PATH_TUNE, "auto": fde.FDE_PATH_AUTO, "gemm": fde.FDE_PATH_GEMM,
+            "fft": fde.FDE_PATH_FFT}[args.path]
+    if args.precision == "fp32" and path in (fde.FDE_PATH_TUNE, fde.FDE_PATH_GEMM):
+        path = fde.FDE_PATH_AUTO  # no tensor-core path in FP32
+    w = Workload(mixed, path=path, outer=outer, precond=precond, cycles=args.cycles,
+                 relax=args.relax, solver=solver, warm=args.warm)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         ms, wall, its, launches = time_steps(w, args.steps, args.warmup, dist)
     ms = shard.max_over_ranks(ms, dist)
     value = world * args.steps / (ms * 1e-3)
     e2e_v, h2d, d2h = e2e_steps(w, max(2, min(args.steps, 4)))
     roof = roofline(w, 2, args.outer)
+    names = {fde.FDE_PATH_GEMM: "gemm", fde.FDE_PATH_FFT: "fft", fde.FDE_PATH_DIRECT: "direct"}
+    level_paths = [names.get(fde.fde_level_path(w.h, l), "dense-inverse")
+                   for l in range(len(fde.fde_levels(w.h)))]
     first = w.first
     w.close()
     exact = None
     if args.relax and not args.no_fp64:
         # the same mixed-precision solver with every Krylov matvec FP64-accurate
-        wx_ = Workload(mixed, outer=outer, precond=precond, cycles=args.cycles, relax=0,
-                       solver=solver, warm=args.warm)
+        wx_ = Workload(mixed, path=path, outer=outer, precond=precond, cycles=args.cycles,
+                       relax=0, solver=solver, warm=args.warm)
         kx = max(4, args.steps // 2)
         msx, _, itsx, _ = time_steps(wx_, kx, args.warmup, None)
         exact = {"value": round(kx / (msx * 1e-3), 4), "unit": "steps/s",
@@ -567,6 +577,7 @@ def main():
                                        "p2": "P2"}[args.precond],
                            "cycles": args.cycles, "relaxed_matvec": bool(args.relax),
                            "solver": args.solver, "warm_start": bool(args.warm),
+                           "level_paths": level_paths,
                            "precision": f"{args.precision} V-cycle products (FP32 vectors), "
                                         f"{args.outer} FFT outer apply",
                            "l2": "inputs larger than L2 (Krylov basis 31 x 33.5 MB)",

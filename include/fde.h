@@ -70,6 +70,9 @@ extern "C" {
 #define FDE_PATH_GEMM          1  /* tcgen05 GEMM (BF16/FP16/BF16X3 only) */
 #define FDE_PATH_FFT           2  /* circulant-embedding FFT */
 #define FDE_PATH_DIRECT        3  /* direct summation */
+#define FDE_PATH_TUNE          4  /* BF16/FP16/BF16X3: on the first coefficient set-up every level
+                                     that can take both times its tensor-core and FFT products on
+                                     the device and keeps the faster (AUTO's rule elsewhere) */
 
 /* arithmetic of the FP64-accurate outer apply (Krylov matvec, true residual, rhs) */
 #define FDE_OUTER_FP64         0  /* FFT in FP64 */
@@ -177,6 +180,10 @@ int fde_level_apply(fde_handle* h, int level, const double* x, double* y);
 /* Number of multigrid levels and their sizes (arrays of length >= levels;
  * either may be NULL). */
 int fde_levels(const fde_handle* h, int* levels, int* n1s, int* n2s);
+/* Product path (FDE_PATH_GEMM / FFT / DIRECT) a Toeplitz multigrid level
+ * uses; -1 for the coarsest level (dense inverse), P_2 stencil levels, a
+ * handle without multigrid or an invalid level. */
+int fde_level_path(const fde_handle* h, int level);
 
 /* Copy the device-generated WSGD weights w_0..w_{count-1} of axis 0 (x,
  * alpha) or 1 (y, beta) to host memory. */

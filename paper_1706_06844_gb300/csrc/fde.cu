@@ -187,6 +187,7 @@ struct MGBase {
   // one V-cycle on the finest level's (b -> x) buffers: a fixed sequence of
   // launches on fixed buffers, so it can be replayed from a CUDA graph
   virtual int cycle_root(fde_handle* h) = 0;
+  virtual int level_path(int l) const { (void)l; return -1; }
   std::vector<int> n1s, n2s;
   cudaGraphExec_t graph = nullptr;
   long long graph_launches = 0;
@@ -240,6 +241,7 @@ struct MG : MGBase {
     double bx0 = 1, bx1 = 0, by0 = 1, by1 = 0;  // Galerkin mass tridiagonals
     double *tx = nullptr, *ty = nullptr;         // Toeplitz generators (FP64)
     int path = FDE_PATH_DIRECT;                  // FFT, DIRECT or GEMM
+    bool tune = false;                           // time GEMM vs FFT at the first setup
     int logLx = 0, logLy = 0;
     cx<T> *S1x = nullptr, *S2x = nullptr, *S1y = nullptr, *S2y = nullptr, *twx = nullptr,
           *twy = nullptr;
@@ -314,6 +316,14 @@ struct MG : MGBase {
       // product path of this level
       int path = p.toeplitz_path;
       const int nmin = std::min(L.n1, L.n2);
+      if (path == FDE_PATH_TUNE) {
+        if (lowp && nmin >= tc::kMinGemmN) {
+          path = FDE_PATH_GEMM;
+          L.tune = true;  // FFT data too, below; the first setup times both
+        } else {
+          path = FDE_PATH_AUTO;
+        }
+      }
       if (path == FDE_PATH_AUTO) {
         if (lowp && nmin >= tc::kAutoGemmN) path = FDE_PATH_GEMM;
         else path = nmin >= 127 ? FDE_PATH_FFT : FDE_PATH_DIRECT;
@@ -346,7 +356,8 @@ struct MG : MGBase {
         const int prec = p.precision == FDE_PREC_BF16 ? tc::kBF16
                          : p.precision == FDE_PREC_FP16 ? tc::kFP16 : tc::kBF16X3;
         int r = tc::level_create(&L.gemm, L.n1, L.n2, prec, sg && l > 0);
-        if (r == 13 && p.toeplitz_path == FDE_PATH_AUTO) {
+        if (r == 13 && (p.toeplitz_path == FDE_PATH_AUTO || L.tune)) {
+          L.tune = false;
           // the generator copies do not fit beside the pipeline: FFT products
           tc::level_destroy(&L.gemm);
           L.path = FDE_PATH_FFT;
@@ -364,6 +375,26 @@ struct MG : MGBase {
           RCHK(h->alloc(&L.twy, (size_t)1 << L.logLy));
         } else if (r != 0) {
           return h->fail(FDE_ERR_UNSUPPORTED, "tensor-core level allocation failed (%d)", r);
+        } else if (L.tune) {
+          // the FFT path's data, for the timing at the first setup
+          L.logLx = ceil_log2(2L * L.n1 - 1);
+          L.logLy = ceil_log2(2L * L.n2 - 1);
+          const int lmax = std::max(L.logLx, L.logLy);
+          if (fft_pass_two_buffer_bytes(lmax, sizeof(cx<T>)) > 227 * 1024 &&
+              h->fft_ws_elems < ((size_t)152 << lmax)) {
+            L.tune = false;  // FFT impossible here: GEMM it is
+          } else {
+            RCHK(h->alloc(&L.S1x, (size_t)1 << L.logLx));
+            RCHK(h->alloc(&L.S2x, (size_t)1 << L.logLx));
+            RCHK(h->alloc(&L.twx, (size_t)1 << L.logLx));
+            RCHK(h->alloc(&L.epT, L.N));
+            RCHK(h->alloc(&L.emT, L.N));
+            RCHK(h->alloc(&L.xT, L.N));
+            RCHK(h->alloc(&L.yT, L.N));
+            RCHK(h->alloc(&L.S1y, (size_t)1 << L.logLy));
+            RCHK(h->alloc(&L.S2y, (size_t)1 << L.logLy));
+            RCHK(h->alloc(&L.twy, (size_t)1 << L.logLy));
+          }
         }
       }
     }
@@ -401,12 +432,13 @@ struct MG : MGBase {
       LCHK(launch_level_fields<T>(h->dpN, h->dmN, h->epN, h->emN, h->n1, L.n1, L.n2, stride,
                                   h->sigma, h->c, L.bx0, L.by0, L.tx, L.ty, p.omega, L.dp, L.dm,
                                   L.ep, L.em, L.W, st));
-      if (L.path == FDE_PATH_FFT && l + 1 < lv.size()) {
+      if ((L.path == FDE_PATH_FFT || L.tune) && l + 1 < lv.size()) {
         LCHK(launch_transpose<T>(L.ep, L.n2, L.n1, L.epT, 0, st));
         LCHK(launch_transpose<T>(L.em, L.n2, L.n1, L.emT, 0, st));
         LCHK(launch_build_spectra<T>(L.tx, L.n1, L.logLx, 1.0, L.S1x, L.S2x, L.twx, st, h->fft_ws));
         LCHK(launch_build_spectra<T>(L.ty, L.n2, L.logLy, 1.0, L.S1y, L.S2y, L.twy, st, h->fft_ws));
-      } else if (L.path == FDE_PATH_DIRECT && l + 1 < lv.size()) {
+      }
+      if (L.path == FDE_PATH_DIRECT && l + 1 < lv.size()) {
         LCHK((launch_convert<double, T>(L.n1 + 1, L.tx, 1.0, L.txT, st)));
         LCHK((launch_convert<double, T>(L.n2 + 1, L.ty, 1.0, L.tyT, st)));
       } else if (L.path == FDE_PATH_GEMM && l + 1 < lv.size()) {
@@ -427,7 +459,49 @@ struct MG : MGBase {
     CCHK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
     CCHK(cudaStreamSynchronize(st));
     if (hinfo != 0) return h->fail(FDE_ERR_NONFINITE, "coarsest-grid matrix is singular");
+    RCHK(tune(h));
     return FDE_OK;
+  }
+
+  // FDE_PATH_TUNE: time each candidate level's GEMM and FFT products (one
+  // warm-up, three timed runs on the level's own buffers) and keep the faster
+  int tune(fde_handle* h) {
+    cudaStream_t st = h->st;
+    for (size_t l = 0; l + 1 < lv.size(); ++l) {
+      Lv& L = lv[l];
+      if (!L.tune) continue;
+      CCHK(cudaMemsetAsync(L.x, 0, L.N * sizeof(T), st));
+      float best = 0.f;
+      int best_path = FDE_PATH_GEMM;
+      const bool prof = h->prof;
+      h->prof = false;
+      for (int cand : {FDE_PATH_GEMM, FDE_PATH_FFT}) {
+        L.path = cand;
+        RCHK(products(h, l, L.x, L.kx));
+        cudaEvent_t e0 = h->ev(), e1 = h->ev();
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) RCHK(products(h, l, L.x, L.kx));
+        cudaEventRecord(e1, st);
+        CCHK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        h->pool.push_back(e0);
+        h->pool.push_back(e1);
+        if (cand == FDE_PATH_GEMM || ms < best) {
+          best = ms;
+          best_path = cand;
+        }
+      }
+      h->prof = prof;
+      L.path = best_path;
+      L.tune = false;
+    }
+    return FDE_OK;
+  }
+
+  int level_path(int l) const override {
+    if (l < 0 || l + 1 >= (int)lv.size()) return -1;
+    return lv[l].path;
   }
 
   // kx = K_l x (products + mass term)
@@ -1048,7 +1122,7 @@ static int validate(const fde_params* p, std::string& why) {
   if (!(p->omega > 0.0 && p->omega < 2.0)) return bad("omega must be in (0, 2)");
   if (p->coarsest_n < 1) return bad("coarsest_n must be >= 1");
   if (p->precision < FDE_PREC_FP64 || p->precision > FDE_PREC_BF16X3) return bad("unknown precision");
-  if (p->toeplitz_path < FDE_PATH_AUTO || p->toeplitz_path > FDE_PATH_DIRECT) return bad("unknown toeplitz_path");
+  if (p->toeplitz_path < FDE_PATH_AUTO || p->toeplitz_path > FDE_PATH_TUNE) return bad("unknown toeplitz_path");
   if (p->outer != FDE_OUTER_FP64 && p->outer != FDE_OUTER_DF32) return bad("unknown outer");
   const int L1 = ceil_log2(2L * p->n1 - 1), L2 = ceil_log2(2L * p->n2 - 1);
   if (L1 > 13 || L2 > 13) {
@@ -1307,6 +1381,11 @@ int fde_levels(const fde_handle* h, int* levels, int* n1s, int* n2s) {
     if (n2s) n2s[l] = h->mg ? h->mg->n2s[l] : h->n2;
   }
   return FDE_OK;
+}
+
+int fde_level_path(const fde_handle* h, int level) {
+  if (!h || !h->mg) return -1;
+  return h->mg->level_path(level);
 }
 
 int fde_weights(const fde_handle* hc, int axis, double* w_host, int count) {

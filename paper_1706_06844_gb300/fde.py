@@ -16,7 +16,7 @@ FDE_OK, FDE_ERR_ARG, FDE_ERR_NOT_CONVERGED, FDE_ERR_NONFINITE = 0, 1, 2, 3
 FDE_ERR_CUDA, FDE_ERR_TIMEOUT, FDE_ERR_UNSUPPORTED = 4, 5, 6
 FDE_PRECOND_NONE, FDE_PRECOND_MG_SG, FDE_PRECOND_MG_REDISC, FDE_PRECOND_P2 = 0, 1, 2, 3
 FDE_PREC_FP64, FDE_PREC_FP32, FDE_PREC_BF16, FDE_PREC_FP16, FDE_PREC_BF16X3 = 0, 1, 2, 3, 4
-FDE_PATH_AUTO, FDE_PATH_GEMM, FDE_PATH_FFT, FDE_PATH_DIRECT = 0, 1, 2, 3
+FDE_PATH_AUTO, FDE_PATH_GEMM, FDE_PATH_FFT, FDE_PATH_DIRECT, FDE_PATH_TUNE = 0, 1, 2, 3, 4
 FDE_OUTER_FP64, FDE_OUTER_DF32 = 0, 1
 FDE_SOLVER_FGMRES, FDE_SOLVER_MG = 0, 1
 FDE_COEF_NEW, FDE_COEF_OLD = 0, 1
@@ -60,6 +60,7 @@ SIGNATURES = {
     "fde_vcycle": (ctypes.c_int, [_VP, _DP, _DP]),
     "fde_level_apply": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
     "fde_levels": (ctypes.c_int, [_VP, _IP, _IP, _IP]),
+    "fde_level_path": (ctypes.c_int, [_VP, ctypes.c_int]),
     "fde_weights": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "fde_solve": (ctypes.c_int, [_VP, _DP, _DP, ctypes.POINTER(fde_stats)]),
     "fde_step": (ctypes.c_int, [_VP, _DP, _DP, _DP, ctypes.POINTER(fde_stats)]),
@@ -294,3 +295,7 @@ def fde_batch_step(b, u_prev, v_half, u_next, allow_not_converged=False):
     if rc not in ok:
         raise FDEError(rc, lib().fde_last_error(None).decode())
     return list(st)
+
+
+def fde_level_path(h, level):
+    return lib().fde_level_path(h, level)

@@ -88,3 +88,32 @@ def test_mixed_solve_converges_to_fp64_residual(precision):
         assert st.iterations <= its + 3, (st.iterations, its)
     finally:
         fde.fde_destroy(h)
+
+
+def test_tuned_paths_and_vcycle():
+    # FDE_PATH_TUNE times each candidate level's tensor-core and FFT products
+    # at the first set-up and keeps the faster; the cycle stays a BF16x3 cycle
+    import torch
+    from oracle import multigrid as mg
+    case = Case(inputs.perturbed_power_law(), 511, precision=fde.FDE_PREC_BF16X3,
+                toeplitz_path=fde.FDE_PATH_TUNE)
+    h = case.handle()
+    try:
+        levels = fde.fde_levels(h)
+        for l, (n1, n2) in enumerate(levels):
+            path = fde.fde_level_path(h, l)
+            if l == len(levels) - 1:
+                assert path == -1
+            elif min(n1, n2) >= 127:
+                assert path in (fde.FDE_PATH_GEMM, fde.FDE_PATH_FFT), (l, path)
+            else:
+                assert path == fde.FDE_PATH_DIRECT, (l, path)
+        hier = case.oracle_hierarchy()
+        R = np.random.default_rng(31).standard_normal((511, 511))
+        z = torch.empty_like(dev(R))
+        fde.fde_vcycle(h, dev(R), z)
+        torch.cuda.synchronize()
+        ref = mg.vcycle(hier, R, 0.7, 1, 1)
+        assert np.linalg.norm(host(z) - ref) <= 1e-3 * np.linalg.norm(ref)
+    finally:
+        fde.fde_destroy(h)
