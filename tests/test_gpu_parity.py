@@ -347,3 +347,39 @@ def test_warm_start_step(solver):
         finally:
             fde.fde_destroy(h)
     assert counts[1] < counts[0], counts
+
+
+@pytest.mark.parametrize("precision", [fde.FDE_PREC_FP64, fde.FDE_PREC_FP32])
+def test_time_dependent_coefficients_example2(precision):
+    # Example 2 (Sec. 5.2): coefficients change every step, so every step sets
+    # both coefficient levels and rebuilds the multigrid hierarchy on the
+    # device; the whole time loop (M = n = 31 steps to T = 1) follows the
+    # oracle's time loop step by step, and the final error against the exact
+    # solution equals the oracle's
+    import torch
+    from oracle import timeloop
+    prob = inputs.example2()
+    n = 31
+    ref = timeloop.run(prob, n, precond="sg", rtol=1e-12, record=True)
+    case = Case(prob, n, dt=1.0 / n, precision=precision, rtol=1e-10)
+    h = fde.fde_create(case.params)
+    try:
+        X, Y, hx, hy = prob.grid(n, n)
+        dt = 1.0 / n
+        ud = dev(prob.exact(X, Y, 0.0))
+        un = torch.empty_like(ud)
+        for m in range(1, n + 1):
+            cold = [dev(f) for f in prob.coefficients(X, Y, (m - 1) * dt)]
+            cnew = [dev(f) for f in prob.coefficients(X, Y, m * dt)]
+            fde.fde_set_coefficients(h, fde.FDE_COEF_OLD, *cold)
+            fde.fde_set_coefficients(h, fde.FDE_COEF_NEW, *cnew)
+            st = fde.fde_step(h, ud, dev(prob.source(X, Y, (m - 0.5) * dt)), un)
+            assert st.converged == 1
+            ug = host(un)
+            Uo = ref["history"][m - 1]
+            assert np.linalg.norm(ug - Uo) <= 1e-8 * np.linalg.norm(Uo), m
+            ud, un = un, ud
+        err = np.max(np.abs(prob.exact(X, Y, 1.0) - host(ud)))
+        np.testing.assert_allclose(err, ref["error_inf"], rtol=1e-6)
+    finally:
+        fde.fde_destroy(h)
