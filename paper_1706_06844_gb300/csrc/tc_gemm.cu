@@ -242,7 +242,11 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
   uint64_t* fullB = bars + C::STAGES;
   uint64_t* empty = bars + 2 * C::STAGES;
   uint64_t* accbar = bars + 3 * C::STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 3 * C::STAGES + 1);
+  // split precision: the low term of the Toeplitz operand gets its own "full"
+  // barrier, so the two products that need only the high term can start
+  // while the low term is still being synthesised
+  uint64_t* fullL = bars + 3 * C::STAGES + 1;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 4 * C::STAGES + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   // generator copies: term t at gsm + t * 2 * glen (16-bit units), forward then reversed
   uint16_t* gsm = reinterpret_cast<uint16_t*>(base + C::STAGES * C::STAGE_BYTES + 256);
@@ -268,6 +272,7 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(smem_u32(&fullA[s]), 1);
       mbar_init(smem_u32(&fullB[s]), NSYN);
+      mbar_init(smem_u32(&fullL[s]), NSYN);
       mbar_init(smem_u32(&empty[s]), 1);
     }
     mbar_init(smem_u32(accbar), 1);
@@ -331,20 +336,26 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
         if (!mbar_wait(smem_u32(&fullB[s]), ph, abort_flag)) break;
         fence_after();
         const uint32_t d = tmem + (uint32_t)(acc * BN);
+        // (A term, B term) pairs: hi*hi and lo*hi need only the high Toeplitz
+        // term; hi*lo waits for the low term
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          // (A term, B term) pairs: hi*hi, then lo*hi and hi*lo for the split
+        for (int p = 0; p < (NT == 1 ? 1 : 3); ++p) {
+          if (p == 2) {
+            if (!mbar_wait(smem_u32(&fullL[s]), ph, abort_flag)) break;
+            fence_after();
+          }
+          const int ta = p == 1 ? 1 : 0, tb = p == 2 ? 1 : 0;
+          const uint32_t aA = smem_u32(tileA(s, ta));
+          const uint32_t aB = smem_u32(tileB(s, tb));
 #pragma unroll
-          for (int p = 0; p < (NT == 1 ? 1 : 3); ++p) {
-            const int ta = p == 1 ? 1 : 0, tb = p == 2 ? 1 : 0;
-            const uint32_t aA = smem_u32(tileA(s, ta));
-            const uint32_t aB = smem_u32(tileB(s, tb));
+          for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t da = DIR == 0 ? smem_desc(aA + kk * 32, 16, 1024)
                                          : smem_desc(aA + kk * 2048, A_BYTES / 2, 1024);
             const uint64_t db = smem_desc(aB + kk * 32, 16, 1024);
             mma_f16(d, da, db, idesc, (started[acc] || kk > 0 || p > 0) ? 1u : 0u);
           }
         }
+        if (*abort_flag) break;
         started[acc] = true;
         mma_commit(smem_u32(&empty[s]));
         ++n;
@@ -442,10 +453,10 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
               *reinterpret_cast<uint4*>(B + r * 128 + ((c ^ (r & 7)) << 4)) = chunk;
             }
           }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMA
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(t == 0 ? &fullB[s] : &fullL[s]));
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMA
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&fullB[s]));
         ++n;
       }
     }
