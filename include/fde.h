@@ -227,8 +227,9 @@ long long fde_launch_count(const fde_handle* h);
 
 /* Batch of independent problems (Sec. 2's scheme on each, sizes, orders and
  * coefficients may all differ), stepped concurrently: up to 16 host worker
- * threads, each with its own CUDA stream, run disjoint subsets of the
- * problems (largest first).  params[0..count) are copied; problem i gets a
+ * threads (the environment variable FDE_BATCH_WORKERS, 1..256, read at
+ * creation, overrides the cap), each with its own CUDA stream, run disjoint
+ * subsets of the problems (largest first).  params[0..count) are copied; problem i gets a
  * handle of its own (fde_batch_handle) on which the caller sets coefficients
  * or state as for a single problem.  Work of fde_batch_step starts after the
  * work already enqueued on `stream` and `stream` waits for all of it before

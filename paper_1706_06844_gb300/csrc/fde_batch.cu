@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <thread>
 #include <vector>
@@ -63,7 +64,12 @@ int fde_batch_create(const fde_params* p, int count, void* stream, fde_batch** o
     fde::set_global_error("fde_batch_create: no CUDA device");
     return FDE_ERR_CUDA;
   }
-  const int W = std::min(count, kMaxWorkers);
+  int maxw = kMaxWorkers;
+  if (const char* env = std::getenv("FDE_BATCH_WORKERS")) {
+    const int v = std::atoi(env);
+    if (v >= 1 && v <= 256) maxw = v;
+  }
+  const int W = std::min(count, maxw);
   b->streams.resize(W, nullptr);
   b->done.resize(W, nullptr);
   b->work.resize(W);
