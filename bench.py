@@ -473,8 +473,9 @@ def main():
                          "the target (the exit test stays on the FP64-accurate true residual); "
                          "0: every matvec FP64-accurate")
     ap.add_argument("--path", default="tune", choices=["tune", "auto", "gemm", "fft"],
-                    help="level product path: tune = time tensor-core vs FFT products per level "
-                         "at set-up and keep the faster; auto = fixed size rule")
+                    help="level product path: tune = time the tensor-core, FFT and direct "
+                         "products of every level at set-up and keep the fastest; auto = fixed "
+                         "size rule")
     ap.add_argument("--solver", default="fgmres", choices=["fgmres", "mg"],
                     help="mg: multigrid as the solver (x <- x + V(b - M x)) instead of FGMRES")
     ap.add_argument("--warm", type=int, default=0, choices=[0, 1],
@@ -518,7 +519,7 @@ def main():
     solver = fde.FDE_SOLVER_MG if args.solver == "mg" else fde.FDE_SOLVER_FGMRES
     path = {"tune": fde.FDE_PATH_TUNE, "auto": fde.FDE_PATH_AUTO, "gemm": fde.FDE_PATH_GEMM,
             "fft": fde.FDE_PATH_FFT}[args.path]
-    if args.precision == "fp32" and path in (fde.FDE_PATH_TUNE, fde.FDE_PATH_GEMM):
+    if args.precision == "fp32" and path == fde.FDE_PATH_GEMM:
         path = fde.FDE_PATH_AUTO  # no tensor-core path in FP32
     w = Workload(mixed, path=path, outer=outer, precond=precond, cycles=args.cycles,
                  relax=args.relax, solver=solver, warm=args.warm)

@@ -70,9 +70,10 @@ extern "C" {
 #define FDE_PATH_GEMM          1  /* tcgen05 GEMM (BF16/FP16/BF16X3 only) */
 #define FDE_PATH_FFT           2  /* circulant-embedding FFT */
 #define FDE_PATH_DIRECT        3  /* direct summation */
-#define FDE_PATH_TUNE          4  /* BF16/FP16/BF16X3: on the first coefficient set-up every level
-                                     that can take both times its tensor-core and FFT products on
-                                     the device and keeps the faster (AUTO's rule elsewhere) */
+#define FDE_PATH_TUNE          4  /* on the first coefficient set-up every level times its
+                                     candidate paths on the device -- tensor cores (BF16/FP16/
+                                     BF16X3, n >= 127), FFT, direct summation (n <= 1023) -- and
+                                     keeps the fastest */
 
 /* arithmetic of the FP64-accurate outer apply (Krylov matvec, true residual, rhs) */
 #define FDE_OUTER_FP64         0  /* FFT in FP64 */

@@ -241,7 +241,8 @@ struct MG : MGBase {
     double bx0 = 1, bx1 = 0, by0 = 1, by1 = 0;  // Galerkin mass tridiagonals
     double *tx = nullptr, *ty = nullptr;         // Toeplitz generators (FP64)
     int path = FDE_PATH_DIRECT;                  // FFT, DIRECT or GEMM
-    bool tune = false;                           // time GEMM vs FFT at the first setup
+    bool tune = false;                           // time the candidates at the first setup
+    int cands = 0;                               // candidate paths (bit FDE_PATH_*)
     int logLx = 0, logLy = 0;
     cx<T> *S1x = nullptr, *S2x = nullptr, *S1y = nullptr, *S2y = nullptr, *twx = nullptr,
           *twy = nullptr;
@@ -315,14 +316,14 @@ struct MG : MGBase {
       if (last) continue;
       // product path of this level
       int path = p.toeplitz_path;
-      const int nmin = std::min(L.n1, L.n2);
+      const int nmin = std::min(L.n1, L.n2), nmax = std::max(L.n1, L.n2);
       if (path == FDE_PATH_TUNE) {
-        if (lowp && nmin >= tc::kMinGemmN) {
-          path = FDE_PATH_GEMM;
-          L.tune = true;  // FFT data too, below; the first setup times both
-        } else {
-          path = FDE_PATH_AUTO;
-        }
+        // candidates: tensor cores (reduced precision, n >= 127), FFT, and
+        // direct summation while its O(n^2) per line stays small (n <= 1023)
+        L.cands = (1 << FDE_PATH_FFT) | (nmax <= 1023 ? (1 << FDE_PATH_DIRECT) : 0) |
+                  ((lowp && nmin >= tc::kMinGemmN) ? (1 << FDE_PATH_GEMM) : 0);
+        L.tune = true;
+        path = (L.cands & (1 << FDE_PATH_GEMM)) ? FDE_PATH_GEMM : FDE_PATH_FFT;
       }
       if (path == FDE_PATH_AUTO) {
         if (lowp && nmin >= tc::kAutoGemmN) path = FDE_PATH_GEMM;
@@ -357,7 +358,7 @@ struct MG : MGBase {
                          : p.precision == FDE_PREC_FP16 ? tc::kFP16 : tc::kBF16X3;
         int r = tc::level_create(&L.gemm, L.n1, L.n2, prec, sg && l > 0);
         if (r == 13 && (p.toeplitz_path == FDE_PATH_AUTO || L.tune)) {
-          L.tune = false;
+          L.cands &= ~(1 << FDE_PATH_GEMM);
           // the generator copies do not fit beside the pipeline: FFT products
           tc::level_destroy(&L.gemm);
           L.path = FDE_PATH_FFT;
@@ -382,7 +383,7 @@ struct MG : MGBase {
           const int lmax = std::max(L.logLx, L.logLy);
           if (fft_pass_two_buffer_bytes(lmax, sizeof(cx<T>)) > 227 * 1024 &&
               h->fft_ws_elems < ((size_t)152 << lmax)) {
-            L.tune = false;  // FFT impossible here: GEMM it is
+            L.cands &= ~(1 << FDE_PATH_FFT);  // FFT impossible here
           } else {
             RCHK(h->alloc(&L.S1x, (size_t)1 << L.logLx));
             RCHK(h->alloc(&L.S2x, (size_t)1 << L.logLx));
@@ -397,6 +398,14 @@ struct MG : MGBase {
           }
         }
       }
+    }
+    for (size_t l = 0; l + 1 < lv.size(); ++l) {
+      Lv& L = lv[l];
+      if (L.tune && (L.cands & (1 << FDE_PATH_DIRECT)) && !L.txT) {
+        RCHK(h->alloc(&L.txT, L.n1 + 2));
+        RCHK(h->alloc(&L.tyT, L.n2 + 2));
+      }
+      if (L.tune && __builtin_popcount(L.cands) < 2) L.tune = false;
     }
     const Lv& C = lv.back();
     RCHK(h->alloc(&inv, C.N * C.N));
@@ -432,16 +441,19 @@ struct MG : MGBase {
       LCHK(launch_level_fields<T>(h->dpN, h->dmN, h->epN, h->emN, h->n1, L.n1, L.n2, stride,
                                   h->sigma, h->c, L.bx0, L.by0, L.tx, L.ty, p.omega, L.dp, L.dm,
                                   L.ep, L.em, L.W, st));
-      if ((L.path == FDE_PATH_FFT || L.tune) && l + 1 < lv.size()) {
+      if ((L.path == FDE_PATH_FFT || (L.tune && (L.cands & (1 << FDE_PATH_FFT)))) &&
+          l + 1 < lv.size()) {
         LCHK(launch_transpose<T>(L.ep, L.n2, L.n1, L.epT, 0, st));
         LCHK(launch_transpose<T>(L.em, L.n2, L.n1, L.emT, 0, st));
         LCHK(launch_build_spectra<T>(L.tx, L.n1, L.logLx, 1.0, L.S1x, L.S2x, L.twx, st, h->fft_ws));
         LCHK(launch_build_spectra<T>(L.ty, L.n2, L.logLy, 1.0, L.S1y, L.S2y, L.twy, st, h->fft_ws));
       }
-      if (L.path == FDE_PATH_DIRECT && l + 1 < lv.size()) {
+      if ((L.path == FDE_PATH_DIRECT || (L.tune && (L.cands & (1 << FDE_PATH_DIRECT)))) &&
+          l + 1 < lv.size()) {
         LCHK((launch_convert<double, T>(L.n1 + 1, L.tx, 1.0, L.txT, st)));
         LCHK((launch_convert<double, T>(L.n2 + 1, L.ty, 1.0, L.tyT, st)));
-      } else if (L.path == FDE_PATH_GEMM && l + 1 < lv.size()) {
+      }
+      if (L.path == FDE_PATH_GEMM && l + 1 < lv.size()) {
         int r = tc::level_setup(&L.gemm, L.tx, L.ty, st);
         h->launches += 2;
         if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core bank setup failed (%d)", r);
@@ -463,8 +475,8 @@ struct MG : MGBase {
     return FDE_OK;
   }
 
-  // FDE_PATH_TUNE: time each candidate level's GEMM and FFT products (one
-  // warm-up, three timed runs on the level's own buffers) and keep the faster
+  // FDE_PATH_TUNE: time each candidate path's products of a level (one
+  // warm-up, three timed runs on the level's own buffers) and keep the fastest
   int tune(fde_handle* h) {
     cudaStream_t st = h->st;
     for (size_t l = 0; l + 1 < lv.size(); ++l) {
@@ -475,7 +487,9 @@ struct MG : MGBase {
       int best_path = FDE_PATH_GEMM;
       const bool prof = h->prof;
       h->prof = false;
-      for (int cand : {FDE_PATH_GEMM, FDE_PATH_FFT}) {
+      bool first = true;
+      for (int cand : {FDE_PATH_GEMM, FDE_PATH_FFT, FDE_PATH_DIRECT}) {
+        if (!(L.cands & (1 << cand))) continue;
         L.path = cand;
         RCHK(products(h, l, L.x, L.kx));
         cudaEvent_t e0 = h->ev(), e1 = h->ev();
@@ -487,9 +501,10 @@ struct MG : MGBase {
         cudaEventElapsedTime(&ms, e0, e1);
         h->pool.push_back(e0);
         h->pool.push_back(e1);
-        if (cand == FDE_PATH_GEMM || ms < best) {
+        if (first || ms < best) {
           best = ms;
           best_path = cand;
+          first = false;
         }
       }
       h->prof = prof;
