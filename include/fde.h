@@ -14,7 +14,8 @@
  * c = 1/r = 2 hx^alpha / dt and sigma = s/r = hx^alpha / hy^beta.  The system
  * is solved by restarted flexible GMRES (Sec. 5) preconditioned by one
  * multigrid V-cycle (Sec. 4: damped Jacobi, bilinear interpolation, Galerkin
- * or rediscretised coarse operators).
+ * or rediscretised coarse operators) or by the band preconditioner P_2 with a
+ * Galerkin V-cycle (Sec. 4.3); multigrid can also run as the solver itself.
  *
  * Conventions shared by every call:
  *  - Grid functions are row-major n2 x n1 arrays U[j][i] of doubles, x index i
@@ -190,14 +191,16 @@ int fde_level_path(const fde_handle* h, int level);
  * alpha) or 1 (y, beta) to host memory. */
 int fde_weights(const fde_handle* h, int axis, double* w_host, int count);
 
-/* Solve M x = b (Eq. 2) by FGMRES(restart) from x = 0 (Sec. 5), right
- * preconditioned.  Writes x even when not converged (FDE_ERR_NOT_CONVERGED).
- * `st` may be NULL.  Synchronises the stream. */
+/* Solve M x = b (Eq. 2) from x = 0: by FGMRES(restart), right
+ * preconditioned (Sec. 5), or with params.solver = FDE_SOLVER_MG by the
+ * stationary multigrid iteration.  Writes x even when not converged
+ * (FDE_ERR_NOT_CONVERGED).  `st` may be NULL.  Synchronises the stream. */
 int fde_solve(fde_handle* h, const double* b, double* x, fde_stats* st);
 
 /* One CN-WSGD time step (Eq. CNWSGD): b from u_prev, v_half and the OLD
- * coefficients, then fde_solve.  u_next must not alias u_prev.  Increments
- * the step counter. */
+ * coefficients, then the solve of fde_solve (started from u_prev instead of
+ * zero when params.warm = 1).  u_next must not alias u_prev.  Increments the
+ * step counter. */
 int fde_step(fde_handle* h, const double* u_prev, const double* v_half, double* u_next,
              fde_stats* st);
 
