@@ -56,7 +56,7 @@ def _peaks():
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # = 1258.6 GFLOP/s at the 2070 MHz maximum clock
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07  # = 80 548 GFLOP/s (FMA = 2 flops)
 FP32_ISSUE_TOPS = 152 * 128 * 2.07 / 1e3  # = 40.3 T FP32 instructions/s
-TRAFFIC_DF32_PASS = 100.88448e6 + 13.602816e6  # dram__bytes_read.sum + dram__bytes_write.sum
+TRAFFIC_DF32_PASS = 100.882688e6 + 13.245184e6  # dram__bytes_read.sum + dram__bytes_write.sum
 
 
 def problem():
