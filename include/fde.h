@@ -106,11 +106,13 @@ typedef struct fde_params {
                               for P_2) */
   int    relax;            /* 1: relaxed Krylov matvec -- once the FGMRES residual estimate is
                               within FDE_RELAX_FACTOR of rtol ||b||, M z is evaluated in FP32
-                              (inexact Krylov: a matvec error of eta ||M|| ||z|| perturbs the
-                              residual by at most about eta times the current residual); the
-                              right-hand side and every true residual stay FP64-accurate, so
-                              the stopping test is unchanged.  0 (default): every matvec
-                              FP64-accurate, as in the paper's GMRES. */
+                              (inexact Krylov: matvec errors eta_j with
+                              eta_j ||r_{j-1}|| <= rtol ||b|| / m keep the final residual within
+                              rtol; an FP32 FFT apply has eta ~ 1e-6 relative to ||M|| ||z||,
+                              so the switch at 1e4 x the target leaves a margin of ~10 at
+                              m = 13); the right-hand side and every true residual stay
+                              FP64-accurate, so the stopping test is unchanged.  0 (default):
+                              every matvec FP64-accurate, as in the paper's GMRES. */
   int    solver;           /* FDE_SOLVER_FGMRES (default) or FDE_SOLVER_MG: multigrid as the
                               solver itself, x <- x + V(b - M x) until the true residual meets
                               rtol (Sec. 1 and Sec. 4.3: the multigrid method can run without a
@@ -122,7 +124,7 @@ typedef struct fde_params {
 #define FDE_SOLVER_FGMRES 0
 #define FDE_SOLVER_MG     1
 
-#define FDE_RELAX_FACTOR 1000.0
+#define FDE_RELAX_FACTOR 1.0e4
 
 typedef struct fde_stats {
   int    iterations;       /* inner FGMRES steps (= preconditioner applications) */
