@@ -9,7 +9,7 @@ solution).  The timed region holds W warm-up steps' successors: K consecutive
 steps of the time loop with every input already resident in HBM.
 
 The headline solver is mixed precision: FP64 Krylov vectors with
-double-float matvecs until the FGMRES residual estimate is within 1000x of
+double-float matvecs until the FGMRES residual estimate is within 1e4 x of
 the target, FP32 matvecs after that (the exit test is the double-float true
 residual, so the tolerance met is unchanged), and a V-cycle whose level-0
 products run on the tensor cores in BF16x3.  Reported beside it: the same
@@ -504,7 +504,7 @@ def main():
                          "band preconditioner P_2 with a Galerkin V-cycle")
     ap.add_argument("--cycles", type=int, default=1, help="V-cycles per preconditioner application")
     ap.add_argument("--relax", type=int, default=1, choices=[0, 1],
-                    help="1: FP32 Krylov matvecs once the residual estimate is within 1000x of "
+                    help="1: FP32 Krylov matvecs once the residual estimate is within 1e4 x of "
                          "the target (the exit test stays on the FP64-accurate true residual); "
                          "0: every matvec FP64-accurate")
     ap.add_argument("--path", default="tune", choices=["tune", "auto", "gemm", "fft"],
