@@ -383,3 +383,31 @@ def test_time_dependent_coefficients_example2(precision):
         np.testing.assert_allclose(err, ref["error_inf"], rtol=1e-6)
     finally:
         fde.fde_destroy(h)
+
+
+def test_structured_galerkin_levels_equal_exact_galerkin_for_constant_coefficients():
+    # the paper's tilde-P_MGM (exact Galerkin P^T A P at every level): for
+    # constant coefficients the structured-Galerkin hierarchy the GPU builds
+    # is exactly that, so every GPU level operator matches the oracle's dense
+    # triple products
+    import torch
+    from oracle import multigrid as mg
+    from oracle.operator import assemble_M, toeplitz_A
+    n = 31
+    case = Case(inputs.constant_unit(), n)
+    h = case.handle()
+    try:
+        K0 = assemble_M(toeplitz_A(case.wx, n), toeplitz_A(case.wy, n), case.sc["c"],
+                        case.sc["sigma"], *case.coef_new)
+        hier = mg.exact_galerkin(K0, n, n)
+        assert [(L.n1, L.n2) for L in hier.levels] == fde.fde_levels(h)
+        rng = np.random.default_rng(33)
+        for l, lev in enumerate(hier.levels):
+            Xl = rng.standard_normal((lev.n2, lev.n1))
+            yl = torch.empty_like(dev(Xl))
+            fde.fde_level_apply(h, l, dev(Xl), yl)
+            torch.cuda.synchronize()
+            rl = lev.apply(Xl)
+            assert np.max(np.abs(host(yl) - rl)) <= 1e-12 * np.max(np.abs(rl)), l
+    finally:
+        fde.fde_destroy(h)
