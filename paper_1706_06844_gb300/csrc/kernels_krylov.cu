@@ -138,30 +138,32 @@ cudaError_t launch_axpy_dots(const double* V, size_t ldv, int k, const double* h
   return cudaGetLastError();
 }
 
-// mode 0: out = sum; 1: out += sum; 2: out = sqrt(sum)
+// mode 0: out = sum; 1: out += sum; 2: out = sqrt(sum).  One block per sum
+// (block i reduces part[i * nb .. i * nb + nb) in a fixed order), so the k
+// sums run side by side and every result is the same from run to run.
 __global__ void reduce_kernel(const double* __restrict__ part, int k, int nb, double* out,
                               int mode) {
   __shared__ double red[KT];
-  for (int i = 0; i < k; ++i) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += KT) s += part[(size_t)i * nb + b];
-    red[threadIdx.x] = s;
+  const int i = blockIdx.x;
+  if (i >= k) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += KT) s += part[(size_t)i * nb + b];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = KT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
-    for (int o = KT / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      const double t = red[0];
-      out[i] = mode == 0 ? t : (mode == 1 ? out[i] + t : sqrt(t));
-    }
-    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double t = red[0];
+    out[i] = mode == 0 ? t : (mode == 1 ? out[i] + t : sqrt(t));
   }
 }
 
 cudaError_t launch_reduce(const double* part, int k, int nb, double* out, int mode,
                           cudaStream_t st) {
-  reduce_kernel<<<1, KT, 0, st>>>(part, k, nb, out, mode);
+  if (k < 1) return cudaSuccess;
+  reduce_kernel<<<k, KT, 0, st>>>(part, k, nb, out, mode);
   return cudaGetLastError();
 }
 
