@@ -143,6 +143,28 @@ cudaError_t launch_coarse_inverse(const double* tx, const double* ty, int n1, in
 template <typename T>
 cudaError_t launch_coarse_solve(const double* inv, int N, const T* b, T* x, cudaStream_t st);
 
+// ---- the small end of a V-cycle in one launch (kernels_tail.cu): levels with
+// n <= kTailN, from the first such level down to the coarsest, all in one CTA
+constexpr int kTailN = 31;
+constexpr int kTailMaxLevels = 8;
+template <typename T>
+struct TailLevel {
+  int n1, n2;
+  T *x, *b, *kx;
+  const T *W, *dp, *dm, *ep, *em, *tx, *ty;  // tx, ty: generators t_d at [d + 1], d = -1..n-1
+  T *xby, *xbx, *mass;                       // structured-Galerkin mass terms (null: level 0 / none)
+  T bx0, bx1, by0, by1;
+};
+template <typename T>
+struct TailArgs {
+  TailLevel<T> lv[kTailMaxLevels];  // lv[0] = first tail level, lv[nlev - 1] = coarsest
+  int nlev, nu_pre, nu_post;
+  double c, rscale;
+  const double* inv;  // explicit inverse of the coarsest operator (FP64, row-major)
+};
+template <typename T>
+cudaError_t launch_mg_tail(const TailArgs<T>& a, cudaStream_t st);
+
 // ---- nine-point stencil levels (P_2 of Sec. 4.3; layout S[o * N + j * n1 + i],
 // o = 3 (dy + 1) + (dx + 1), coefficients reaching outside the grid are zero)
 // level 0: P_2 = c I + (D+ + D-)(I (x) A2) + sigma (E+ + E-)(A2 (x) I), A2 = tridiag(-1, 2, -1)

@@ -258,6 +258,7 @@ struct MG : MGBase {
   double rscale = 1.0;
   bool sg = true;
   T *acc_x = nullptr, *acc_b = nullptr;  // further V-cycles: iterate and second rhs buffer
+  size_t tail0 = 0;  // first level handled by the one-launch tail of the cycle (== size: none)
 
   int create(fde_handle* h) {
     const fde_params& p = h->p;
@@ -295,6 +296,15 @@ struct MG : MGBase {
     }
     const bool lowp = (p.precision == FDE_PREC_BF16 || p.precision == FDE_PREC_FP16 ||
                        p.precision == FDE_PREC_BF16X3);
+    // the small end of the cycle runs as one launch: from the first level with
+    // n <= kTailN down to the coarsest (direct-sum products there)
+    tail0 = lv.size();
+    for (size_t l = 0; l < lv.size(); ++l)
+      if (std::max(lv[l].n1, lv[l].n2) <= kTailN) {
+        tail0 = l;
+        break;
+      }
+    if (lv.size() - tail0 > (size_t)kTailMaxLevels || tail0 + 1 >= lv.size()) tail0 = lv.size();
     for (size_t l = 0; l < lv.size(); ++l) {
       Lv& L = lv[l];
       const bool last = l + 1 == lv.size();
@@ -317,6 +327,7 @@ struct MG : MGBase {
       // product path of this level
       int path = p.toeplitz_path;
       const int nmin = std::min(L.n1, L.n2), nmax = std::max(L.n1, L.n2);
+      if (l >= tail0) path = FDE_PATH_DIRECT;  // the tail sums directly
       if (path == FDE_PATH_TUNE) {
         // candidates: tensor cores (reduced precision, n >= 127), FFT, and
         // direct summation while its O(n^2) per line stays small (n <= 1023)
@@ -571,6 +582,7 @@ struct MG : MGBase {
     Lv& L = lv[l];
     const fde_params& p = h->p;
     cudaStream_t st = h->st;
+    if (l == tail0) return cycle_tail(h);
     if (l + 1 == lv.size()) {
       const int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
       LCHK(launch_coarse_solve<T>(inv, (int)L.N, L.b, L.x, st));
@@ -593,6 +605,45 @@ struct MG : MGBase {
     LCHK(launch_prolong_add<T>(lv[l + 1].x, L.n1, L.n2, L.x, st));
     h->pend(pi);
     for (int s = 0; s < p.nu_post; ++s) RCHK(smooth(h, l));
+    return FDE_OK;
+  }
+
+  // levels tail0 .. last in one launch (kernels_tail.cu)
+  int cycle_tail(fde_handle* h) {
+    TailArgs<T> a{};
+    a.nlev = (int)(lv.size() - tail0);
+    a.nu_pre = h->p.nu_pre;
+    a.nu_post = h->p.nu_post;
+    a.c = h->c;
+    a.rscale = rscale;
+    a.inv = inv;
+    for (int k = 0; k < a.nlev; ++k) {
+      Lv& L = lv[tail0 + k];
+      TailLevel<T>& t = a.lv[k];
+      t.n1 = L.n1;
+      t.n2 = L.n2;
+      t.x = L.x;
+      t.b = L.b;
+      t.kx = L.kx;
+      t.W = L.W;
+      t.dp = L.dp;
+      t.dm = L.dm;
+      t.ep = L.ep;
+      t.em = L.em;
+      t.tx = L.txT;
+      t.ty = L.tyT;
+      const bool mass = sg && tail0 + k > 0;
+      t.xby = mass ? L.xby : nullptr;
+      t.xbx = mass ? L.xbx : nullptr;
+      t.mass = mass ? L.mass : nullptr;
+      t.bx0 = T(L.bx0);
+      t.bx1 = T(L.bx1);
+      t.by0 = T(L.by0);
+      t.by1 = T(L.by1);
+    }
+    const int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+    LCHK(launch_mg_tail<T>(a, h->st));
+    h->pend(pi);
     return FDE_OK;
   }
 
