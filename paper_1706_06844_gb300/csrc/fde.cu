@@ -674,30 +674,28 @@ struct MG : MGBase {
     if (l < 0 || l >= (int)lv.size()) return h->fail(FDE_ERR_ARG, "level %d out of range", l);
     Lv& L = lv[l];
     if (l + 1 == (int)lv.size()) {
-      // coarsest level: apply through the direct path on the FP64 generators
+      // coarsest level (the cycle uses its inverse): apply through the direct
+      // path, with generators in T allocated on the first request
       LCHK((launch_convert<double, T>(L.N, x, 1.0, L.x, h->st)));
-      T *txT, *tyT;
-      RCHK(h->alloc(&txT, L.n1 + 2));
-      RCHK(h->alloc(&tyT, L.n2 + 2));
-      LCHK((launch_convert<double, T>(L.n1 + 1, L.tx, 1.0, txT, h->st)));
-      LCHK((launch_convert<double, T>(L.n2 + 1, L.ty, 1.0, tyT, h->st)));
+      if (!L.txT) {
+        RCHK(h->alloc(&L.txT, L.n1 + 2));
+        RCHK(h->alloc(&L.tyT, L.n2 + 2));
+      }
+      LCHK((launch_convert<double, T>(L.n1 + 1, L.tx, 1.0, L.txT, h->st)));
+      LCHK((launch_convert<double, T>(L.n2 + 1, L.ty, 1.0, L.tyT, h->st)));
       const T *xin_x = L.x, *xin_y = L.x, *M = L.x;
       double cm = h->c;
-      T *xby, *xbx, *mass;
-      if (sg && l > 0) {
-        RCHK(h->alloc(&xby, L.N));
-        RCHK(h->alloc(&xbx, L.N));
-        RCHK(h->alloc(&mass, L.N));
-        LCHK(launch_mass_prepass<T>(L.x, L.n1, L.n2, L.bx0, L.bx1, L.by0, L.by1, h->c, xby, xbx,
-                                    mass, h->st));
-        xin_x = xby;
-        xin_y = xbx;
-        M = mass;
+      if (sg && l > 0) {  // mass-term buffers of every SG level l > 0 exist
+        LCHK(launch_mass_prepass<T>(L.x, L.n1, L.n2, L.bx0, L.bx1, L.by0, L.by1, h->c, L.xby,
+                                    L.xbx, L.mass, h->st));
+        xin_x = L.xby;
+        xin_y = L.xbx;
+        M = L.mass;
         cm = 1.0;
       }
-      LCHK(launch_direct_pass<T>(xin_x, 1, L.n1, L.n2, L.n1, txT, L.dp, L.dm, M, cm, L.kx, 0,
+      LCHK(launch_direct_pass<T>(xin_x, 1, L.n1, L.n2, L.n1, L.txT, L.dp, L.dm, M, cm, L.kx, 0,
                                  h->st));
-      LCHK(launch_direct_pass<T>(xin_y, L.n1, 1, L.n1, L.n2, tyT, L.ep, L.em, nullptr, 0.0, L.kx,
+      LCHK(launch_direct_pass<T>(xin_y, L.n1, 1, L.n1, L.n2, L.tyT, L.ep, L.em, nullptr, 0.0, L.kx,
                                  1, h->st));
       LCHK((launch_convert<T, double>(L.N, L.kx, 1.0, y, h->st)));
       return FDE_OK;
