@@ -8,10 +8,13 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <memory>
 #include <string>
 #include <type_traits>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
 #include "df32.cuh"
@@ -41,6 +44,12 @@ namespace fde {
 // message returned by fde_last_error(NULL) for calls without a handle
 void set_global_error(const char* msg) { g_create_error = msg; }
 }  // namespace fde
+
+// NVTX range for profilers (no cost without an attached tool)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct MGBase;
 
@@ -115,6 +124,13 @@ struct fde_handle {
     cudaError_t e = cudaMalloc(&q, count * sizeof(P) + 16);
     if (e != cudaSuccess) return fail(FDE_ERR_CUDA, "cudaMalloc(%zu): %s", count * sizeof(P),
                                       cudaGetErrorString(e));
+    // FDE_POISON=1: fill every workspace buffer with NaN bit patterns, so a
+    // read of memory that no kernel wrote first shows up in the results
+    static const bool poison = [] {
+      const char* v = std::getenv("FDE_POISON");
+      return v && v[0] == '1';
+    }();
+    if (poison) cudaMemset(q, 0xFF, count * sizeof(P) + 16);
     allocs.push_back(q);
     *ptr = static_cast<P*>(q);
     return FDE_OK;
@@ -188,6 +204,8 @@ struct MGBase {
   // launches on fixed buffers, so it can be replayed from a CUDA graph
   virtual int cycle_root(fde_handle* h) = 0;
   virtual int level_path(int l) const { (void)l; return -1; }
+  // 1 if a capped device-side wait gave up since the last check
+  virtual int device_error(fde_handle* h) { (void)h; return 0; }
   std::vector<int> n1s, n2s;
   cudaGraphExec_t graph = nullptr;
   long long graph_launches = 0;
@@ -528,6 +546,13 @@ struct MG : MGBase {
   int level_path(int l) const override {
     if (l < 0 || l + 1 >= (int)lv.size()) return -1;
     return lv[l].path;
+  }
+
+  int device_error(fde_handle* h) override {
+    int any = 0;
+    for (auto& L : lv)
+      if (L.gemm.built && tc::level_error(&L.gemm, h->st) != 0) any = 1;
+    return any;
   }
 
   // kx = K_l x (products + mass term)
@@ -884,6 +909,7 @@ struct StencilMG : MGBase {
 // FP64-accurate outer operator
 
 static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
+  NvtxRange range("matvec");
   if (h->p.outer == FDE_OUTER_DF32) {
     df* const* cf = old ? h->cfO : h->cfN;
     int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
@@ -925,6 +951,7 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
 
 // y = M^(m) x with FP32 arithmetic on FP64 data (relaxed Krylov matvec)
 static int outer_apply32(fde_handle* h, const double* x, double* y) {
+  NvtxRange range("matvec_fp32");
   cx<float>* ws = reinterpret_cast<cx<float>*>(h->fft_ws);
   const size_t wse = h->fft_ws_elems * 2;
   int pi = h->pbeg(FDE_KCLASS_OUTER_FP32);
@@ -953,6 +980,7 @@ static int norm2(fde_handle* h, const double* x, double* dev_out, double* host_o
 }
 
 static int precond(fde_handle* h, const double* v, double* z) {
+  NvtxRange range("vcycle");
   if (!h->mg) {
     CCHK(cudaMemcpyAsync(z, v, h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     return FDE_OK;
@@ -1059,6 +1087,7 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
       } else {
         RCHK(outer_apply(h, Zj, w, false));
       }
+      NvtxRange arnoldi("cgs2");
       // classical Gram-Schmidt, twice (CGS2); for 9 <= j + 1 <= 16 the first
       // subtraction and the second projection share one pass over V (measured
       // faster there; outside that range the two separate passes are)
@@ -1468,9 +1497,12 @@ int fde_solve(fde_handle* h, const double* b, double* x, fde_stats* st) {
   if (!h) return FDE_ERR_ARG;
   if (!b || !x || b == x) return h->fail(FDE_ERR_ARG, "null or aliased pointer");
   if (!h->have_new) return h->fail(FDE_ERR_ARG, "FDE_COEF_NEW coefficients not set");
+  NvtxRange range("fde_solve");
   int r = h->p.solver == FDE_SOLVER_MG ? solve_mg(h, b, x, st, nullptr)
                                        : solve_impl(h, b, x, st, nullptr);
   h->prof_collect();
+  if (h->mg && h->mg->device_error(h))
+    return h->fail(FDE_ERR_TIMEOUT, "a capped device-side wait gave up during the solve");
   return r;
 }
 
@@ -1482,9 +1514,12 @@ int fde_step(fde_handle* h, const double* u_prev, const double* v_half, double* 
   RCHK(fde_rhs(h, u_prev, v_half, h->bwork));
   if (!h->have_new) return h->fail(FDE_ERR_ARG, "FDE_COEF_NEW coefficients not set");
   const double* x0 = h->p.warm ? u_prev : nullptr;
+  NvtxRange range("fde_step");
   int r = h->p.solver == FDE_SOLVER_MG ? solve_mg(h, h->bwork, u_next, st, x0)
                                        : solve_impl(h, h->bwork, u_next, st, x0);
   h->prof_collect();
+  if (h->mg && h->mg->device_error(h))
+    return h->fail(FDE_ERR_TIMEOUT, "a capped device-side wait gave up during the step");
   if (r == FDE_OK || r == FDE_ERR_NOT_CONVERGED) {
     CCHK(cudaMemcpyAsync(h->u_last, u_next, h->N * 8, cudaMemcpyDeviceToDevice, h->st));
     h->m++;

@@ -791,11 +791,14 @@ int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y,
   return cudaGetLastError() == cudaSuccess ? 0 : 31;
 }
 
-int level_error(ToeplitzGemmLevel* L) {
+int level_error(ToeplitzGemmLevel* L, cudaStream_t st) {
   if (!L->built) return 0;
   Maps* m = (Maps*)L->maps;
   int e = 0;
-  cudaMemcpy(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (cudaMemcpyAsync(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return -1;
+  if (e) cudaMemsetAsync(m->err, 0, sizeof(int), st);  // reported once
   return e;
 }
 

@@ -38,7 +38,9 @@ int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y,
                    double cm, const float* dp, const float* dm, const float* ep, const float* em,
                    float* kx, cudaStream_t st);
 // device error flag of the level's kernels (1 = a bounded wait gave up); reading it synchronises
-int level_error(ToeplitzGemmLevel* L);
+// 1 if a capped wait of the level's kernels gave up since the last call (the flag
+// is then cleared), 0 if not, -1 if the flag could not be read; syncs `st`
+int level_error(ToeplitzGemmLevel* L, cudaStream_t st);
 void level_destroy(ToeplitzGemmLevel* L);
 
 }  // namespace tc

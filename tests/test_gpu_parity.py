@@ -411,3 +411,54 @@ def test_structured_galerkin_levels_equal_exact_galerkin_for_constant_coefficien
             assert np.max(np.abs(host(yl) - rl)) <= 1e-12 * np.max(np.abs(rl)), l
     finally:
         fde.fde_destroy(h)
+
+
+_POISON_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1]); sys.path.insert(0, sys.argv[1] + '/tests')
+from paper_1706_06844_gb300 import fde, inputs
+from gpu_util import Case, dev, host
+out = []
+for kw in (dict(precision=fde.FDE_PREC_FP32), dict(precision=fde.FDE_PREC_BF16X3,
+           toeplitz_path=fde.FDE_PATH_GEMM, relax=1, outer=fde.FDE_OUTER_DF32),
+           dict(precond=fde.FDE_PRECOND_P2, precision=fde.FDE_PREC_FP32)):
+    case = Case(inputs.perturbed_power_law(), 255, rtol=1e-10, **kw)
+    h = case.handle()
+    B = dev(case.oracle_rhs()); x = torch.empty_like(B)
+    fde.fde_solve(h, B, x); fde.fde_destroy(h)
+    out.append(host(x))
+np.save(sys.argv[2], np.stack(out))
+"""
+
+
+def test_poisoned_workspace_changes_nothing(tmp_path):
+    # FDE_POISON=1 fills every workspace buffer with NaN bit patterns when it
+    # is allocated: a kernel reading memory that nothing wrote first would turn
+    # the solution into NaN or change it; the poisoned solves (in a child
+    # process, where the option is read at the first allocation) give the same
+    # bits as unpoisoned ones
+    import os
+    import subprocess
+    import sys
+    import torch
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    path = str(tmp_path / "poisoned.npy")
+    env = dict(os.environ, FDE_POISON="1")
+    r = subprocess.run([sys.executable, "-c", _POISON_CHILD, root, path], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    poisoned = np.load(path)
+    assert np.all(np.isfinite(poisoned))
+    for k, kw in enumerate((dict(precision=fde.FDE_PREC_FP32),
+                            dict(precision=fde.FDE_PREC_BF16X3, toeplitz_path=fde.FDE_PATH_GEMM,
+                                 relax=1, outer=fde.FDE_OUTER_DF32),
+                            dict(precond=fde.FDE_PRECOND_P2, precision=fde.FDE_PREC_FP32))):
+        case = Case(inputs.perturbed_power_law(), 255, rtol=1e-10, **kw)
+        h = case.handle()
+        try:
+            B = dev(case.oracle_rhs())
+            x = torch.empty_like(B)
+            fde.fde_solve(h, B, x)
+            np.testing.assert_array_equal(host(x), poisoned[k])
+        finally:
+            fde.fde_destroy(h)
