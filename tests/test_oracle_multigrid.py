@@ -324,3 +324,38 @@ def test_fgmres_warm_start():
     xw, itsw, relw, okw = fgmres(A, b, prec, 30, 1e-10, x0=x0)
     assert ok and okw and itsw < its
     assert np.linalg.norm(A(xw) - b) <= 1.0001e-10 * np.linalg.norm(b)
+
+
+def _fgmres_counts(kind, al, be, sizes):
+    from oracle.timeloop import make_preconditioner
+    from oracle.operator import cn_scalars
+    r = np.random.default_rng(3)
+    counts = []
+    for n in sizes:
+        wx, wy = wsgd_weights(al, n, 1, -1), wsgd_weights(be, n, 1, -1)
+        h = 1.0 / (n + 1)
+        sc = cn_scalars(al, be, h, h, h)
+        X, Y = np.meshgrid(np.arange(1, n + 1) * h, np.arange(1, n + 1) * h)
+        cf = (1 + X ** al * Y, 1 + (1 - X) ** al * Y, 1 + Y ** be * X, 1 + (1 - Y) ** be * X)
+        prec, _ = make_preconditioner(kind, al, be, wx, wy, n, n, sc, cf)
+        A = lambda Z: apply_M(Z, wx, wy, sc["c"], sc["sigma"], *cf)
+        x, its, rel, ok = fgmres(A, r.standard_normal((n, n)), prec, 60, 1e-8)
+        assert ok
+        counts.append(its)
+    return counts
+
+
+def test_iteration_counts_flat_in_n_for_multigrid_not_for_p2():
+    # Sec. 4 / Sec. 5: the V-cycle preconditioner's iteration count is (nearly)
+    # independent of n and of alpha, beta; the band preconditioner P_2 is a
+    # second-order operator, so its count grows with n when alpha, beta are far
+    # from 2 and stays low only near 2 (dt = h, variable coefficients)
+    sizes = [15, 31, 63, 127, 255]
+    far, near = (1.2, 1.3), (1.9, 1.8)
+    sg_far, sg_near = _fgmres_counts("sg", *far, sizes), _fgmres_counts("sg", *near, sizes)
+    p2_far, p2_near = _fgmres_counts("p2", *far, sizes), _fgmres_counts("p2", *near, sizes)
+    for c in (sg_far, sg_near):
+        assert max(c) <= 16 and c[-1] - c[0] <= 5, c
+    assert abs(sg_far[-1] - sg_near[-1]) <= 2, (sg_far, sg_near)
+    assert p2_far[-1] - p2_far[0] >= 2 * (sg_far[-1] - sg_far[0]), (p2_far, sg_far)
+    assert p2_far[-1] > p2_near[-1] + 5, (p2_far, p2_near)

@@ -156,3 +156,43 @@ def test_toeplitz_rows_against_dense():
     A = toeplitz_A(w, n)
     np.testing.assert_allclose(toeplitz_rows(X, w), X @ A.T, atol=1e-12)
     np.testing.assert_allclose(toeplitz_rows(X, w, True), X @ A, atol=1e-12)
+
+
+def _q_closed_form(g, xi):
+    # q_gamma(xi) = f_gamma(xi) + f_gamma(-xi) = 2 Re f_gamma(xi), f_gamma of Eq. (fgamma)
+    f = -((2 - g * (1 - np.exp(-1j * xi))) / 2) * (1 + np.exp(1j * (xi + np.pi))) ** g
+    return 2 * f.real
+
+
+@pytest.mark.parametrize("al,be", [(1.5, 1.7), (1.2, 1.9)])
+def test_eigenvalues_cluster_at_symbol_samples(al, be):
+    # Prop. PaPb: with d+- = d, e+- = e constant, {A_x + (s/r) A_y} ~_lambda
+    # F = d q_a(t1) + e (s/r) q_b(t2).  For this real even symbol the sorted
+    # eigenvalues approach the sorted samples F(j pi/(n1+1), k pi/(n2+1)); the
+    # largest gap falls as the grid is refined.  The eigenvalues of a Hermitian
+    # Toeplitz matrix lie strictly inside (min F, max F) = (0, d ||q_a|| + e (s/r) ||q_b||),
+    # ||q_g||_inf = (g - 1) 2^(g+1).
+    d, e, sig = 1.3, 0.6, 0.9
+    fmax = d * (al - 1) * 2 ** (al + 1) + sig * e * (be - 1) * 2 ** (be + 1)
+    gaps = []
+    for n in [15, 31]:
+        n1, n2 = n, n + 2
+        ones = np.ones((n2, n1))
+        M = assemble_M(toeplitz_A(wsgd_weights(al, n1), n1), toeplitz_A(wsgd_weights(be, n2), n2),
+                       0.0, sig, d * ones, d * ones, e * ones, e * ones)
+        lam = np.sort(np.linalg.eigvalsh(M))
+        t1 = np.pi * np.arange(1, n1 + 1) / (n1 + 1)
+        t2 = np.pi * np.arange(1, n2 + 1) / (n2 + 1)
+        F = np.sort((d * _q_closed_form(al, t1)[None, :]
+                     + sig * e * _q_closed_form(be, t2)[:, None]).ravel())
+        assert 0 < lam[0] and lam[-1] < fmax
+        gaps.append(np.max(np.abs(lam - F)) / fmax)
+    assert gaps[1] < 0.011 and gaps[1] < 0.6 * gaps[0], gaps
+    # the one-level factor alone on larger sizes: the same O(1/n) clustering
+    gaps1 = []
+    for n in [63, 127, 255]:
+        A = toeplitz_A(wsgd_weights(al, n), n)
+        lam = np.sort(np.linalg.eigvalsh(A + A.T))
+        F = np.sort(_q_closed_form(al, np.pi * np.arange(1, n + 1) / (n + 1)))
+        gaps1.append(np.max(np.abs(lam - F)))
+    assert gaps1[2] < 0.6 * gaps1[1] < 0.36 * gaps1[0], gaps1
