@@ -217,6 +217,20 @@ int fde_get_state(const fde_handle* h, int* m, double* u_out);
 /* Restore the step counter (the caller keeps u^(m) and passes it to fde_step). */
 int fde_set_state(fde_handle* h, int m);
 
+/* Failure-path self-test of the tensor-core kernels (no paper passage: a
+ * property of this implementation).  Enqueues on the handle's stream one
+ * run of those kernels' bounded mbarrier wait, in a one-warp kernel, on a
+ * barrier that is completed (complete = 1) or that nothing completes
+ * (complete = 0: the wait gives up after 20 ms and raises the device error
+ * flag of the handle's first tensor-core level, as a products kernel whose
+ * wait ran out would).  Nothing faults or hangs.  The flag is read by the
+ * next fde_solve / fde_step, which then returns FDE_ERR_TIMEOUT (once; the
+ * flag is cleared when read) after writing its result as usual.  Returns
+ * FDE_OK when enqueued, FDE_ERR_ARG for a NULL handle or complete not 0/1,
+ * FDE_ERR_UNSUPPORTED if the handle has no tensor-core level, FDE_ERR_CUDA
+ * on a launch error.  Does not synchronise. */
+int fde_wait_selftest(fde_handle* h, int complete);
+
 /* Kernel-level timing with CUDA events on the handle's stream (off by
  * default).  Kernel classes: FDE_KCLASS_*.  fde_profile_query returns the
  * number of launches and their summed event time since the last reset. */

@@ -206,6 +206,12 @@ struct MGBase {
   virtual int level_path(int l) const { (void)l; return -1; }
   // 1 if a capped device-side wait gave up since the last check
   virtual int device_error(fde_handle* h) { (void)h; return 0; }
+  // enqueue the bounded-wait self-test on the first tensor-core level (-1: none)
+  virtual int wait_selftest(fde_handle* h, int complete) {
+    (void)h;
+    (void)complete;
+    return -1;
+  }
   std::vector<int> n1s, n2s;
   cudaGraphExec_t graph = nullptr;
   long long graph_launches = 0;
@@ -553,6 +559,12 @@ struct MG : MGBase {
     for (auto& L : lv)
       if (L.gemm.built && tc::level_error(&L.gemm, h->st) != 0) any = 1;
     return any;
+  }
+
+  int wait_selftest(fde_handle* h, int complete) override {
+    for (auto& L : lv)
+      if (L.gemm.built) return tc::level_wait_selftest(&L.gemm, complete, h->st);
+    return -1;
   }
 
   // kx = K_l x (products + mass term)
@@ -1504,6 +1516,15 @@ int fde_solve(fde_handle* h, const double* b, double* x, fde_stats* st) {
   if (h->mg && h->mg->device_error(h))
     return h->fail(FDE_ERR_TIMEOUT, "a capped device-side wait gave up during the solve");
   return r;
+}
+
+int fde_wait_selftest(fde_handle* h, int complete) {
+  if (!h) return FDE_ERR_ARG;
+  if (complete != 0 && complete != 1) return h->fail(FDE_ERR_ARG, "complete must be 0 or 1");
+  const int r = h->mg ? h->mg->wait_selftest(h, complete) : -1;
+  if (r < 0) return h->fail(FDE_ERR_UNSUPPORTED, "the handle has no tensor-core level");
+  if (r > 0) return h->fail(FDE_ERR_CUDA, "bounded-wait self-test launch failed");
+  return FDE_OK;
 }
 
 int fde_step(fde_handle* h, const double* u_prev, const double* v_half, double* u_next,

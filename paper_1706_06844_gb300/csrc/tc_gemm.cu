@@ -97,8 +97,11 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// bounded wait (about one second): false on timeout or when another role of
-// the CTA already gave up
+// bounded wait (CAP_NS, about one second in the products kernel): false on
+// timeout or when another role of the CTA already gave up.  MAX_ROUNDS > 0 also
+// bounds the number of polling rounds (256 polls each), independently of the
+// timer.
+template <uint64_t CAP_NS = 1000000000ull, uint32_t MAX_ROUNDS = 0>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
   uint64_t t0 = 0;
   for (uint32_t i = 0;; ++i) {
@@ -107,7 +110,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
       if (*abort) return false;
       const uint64_t t = global_ns();
       if (t0 == 0) t0 = t;
-      else if (t - t0 > 1000000000ull) break;
+      else if (t - t0 > CAP_NS) break;
+      if (MAX_ROUNDS != 0 && (i >> 8) >= MAX_ROUNDS) break;
       __nanosleep(64);
     }
   }
@@ -631,6 +635,33 @@ static EncodeTiled get_encoder() {
   return fn;
 }
 
+// Self-test of the failure path: one warp runs the bounded wait above on a
+// barrier of one expected arrival.  With `complete` set, thread 0 arrives first
+// and the wait succeeds; otherwise nothing arrives, the wait gives up after
+// 20 ms (or 2^16 polling rounds) and the kernel raises the level's error flag
+// exactly as the products kernel does.  No copy or MMA is in flight and no
+// tensor memory is held, so giving up needs no draining.
+constexpr uint64_t kSelftestCapNs = 20000000ull;
+constexpr uint32_t kSelftestRounds = 1u << 16;
+
+__global__ void __launch_bounds__(32) wait_selftest_kernel(int complete, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (complete && threadIdx.x == 0) mbar_arrive(smem_u32(&bar));
+  __syncwarp();
+  int ok = 1;
+  if (threadIdx.x == 0)
+    ok = mbar_wait<kSelftestCapNs, kSelftestRounds>(smem_u32(&bar), 0, &abort_flag) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+}
+
 struct Maps {
   // [term hi / lo]: x-CTAs read X K-major (box 64 x 128), y-CTAs read the
   // y-operand MN-major (box 64 x 64)
@@ -800,6 +831,13 @@ int level_error(ToeplitzGemmLevel* L, cudaStream_t st) {
     return -1;
   if (e) cudaMemsetAsync(m->err, 0, sizeof(int), st);  // reported once
   return e;
+}
+
+int level_wait_selftest(ToeplitzGemmLevel* L, int complete, cudaStream_t st) {
+  if (!L->built) return -1;
+  Maps* m = (Maps*)L->maps;
+  wait_selftest_kernel<<<1, 32, 0, st>>>(complete ? 1 : 0, m->err);
+  return cudaGetLastError() == cudaSuccess ? 0 : 31;
 }
 
 void level_destroy(ToeplitzGemmLevel* L) {

@@ -37,10 +37,14 @@ int level_setup(ToeplitzGemmLevel* L, const double* tx, const double* ty, cudaSt
 int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y, const float* M,
                    double cm, const float* dp, const float* dm, const float* ep, const float* em,
                    float* kx, cudaStream_t st);
-// device error flag of the level's kernels (1 = a bounded wait gave up); reading it synchronises
 // 1 if a capped wait of the level's kernels gave up since the last call (the flag
 // is then cleared), 0 if not, -1 if the flag could not be read; syncs `st`
 int level_error(ToeplitzGemmLevel* L, cudaStream_t st);
+// enqueue on `st` one run of the kernels' bounded wait on a barrier that is
+// completed (complete = 1) or never completed (complete = 0: the wait gives up
+// after 20 ms and raises the level's error flag); 0 on success, -1 if the level
+// is not built, 31 on a launch error
+int level_wait_selftest(ToeplitzGemmLevel* L, int complete, cudaStream_t st);
 void level_destroy(ToeplitzGemmLevel* L);
 
 }  // namespace tc

@@ -67,6 +67,7 @@ SIGNATURES = {
     "fde_step_host": (ctypes.c_int, [_VP, _DP, _DP, _DP, ctypes.POINTER(fde_stats)]),
     "fde_get_state": (ctypes.c_int, [_VP, _IP, _DP]),
     "fde_set_state": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "fde_wait_selftest": (ctypes.c_int, [_VP, ctypes.c_int]),
     "fde_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "fde_profile_query": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_double)]),
@@ -214,6 +215,10 @@ def fde_get_state(h, u_out=None):
 
 def fde_set_state(h, m):
     return _check(h, lib().fde_set_state(h, m))
+
+
+def fde_wait_selftest(h, complete):
+    return _check(h, lib().fde_wait_selftest(h, int(complete)))
 
 
 def fde_profile_enable(h, on):

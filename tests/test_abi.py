@@ -63,3 +63,4 @@ def test_batch_argument_errors_without_gpu():
     assert fde.fde_batch_size(None) == 0
     assert fde.fde_batch_status(None, 0) == fde.FDE_ERR_ARG
     assert fde.lib().fde_batch_step(None, None, None, None, None) == fde.FDE_ERR_ARG
+    assert fde.lib().fde_wait_selftest(None, 0) == fde.FDE_ERR_ARG

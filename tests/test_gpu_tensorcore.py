@@ -118,3 +118,54 @@ def test_tuned_paths_and_vcycle():
         assert np.linalg.norm(host(z) - ref) <= 1e-3 * np.linalg.norm(ref)
     finally:
         fde.fde_destroy(h)
+
+
+def test_capped_wait_gives_up_and_reports_timeout():
+    # failure detection without a fault: the tensor-core kernels' bounded
+    # mbarrier wait runs once on a barrier that nothing completes; it gives up
+    # after 20 ms and raises the level's device flag, the next solve writes its
+    # result as usual and returns FDE_ERR_TIMEOUT, and the flag is cleared: the
+    # context stays usable and the following solve is clean
+    import time
+    import torch
+    case = Case(inputs.perturbed_power_law(), 127, precision=fde.FDE_PREC_BF16X3, rtol=1e-10,
+                toeplitz_path=fde.FDE_PATH_GEMM)
+    h = case.handle()
+    try:
+        B = case.oracle_rhs()
+        b = dev(B)
+        x = torch.empty_like(b)
+        fde.fde_wait_selftest(h, 1)  # a completed barrier raises nothing
+        st = fde.fde_solve(h, b, x)
+        assert st.converged
+        x_ref = host(x).copy()
+        t0 = time.perf_counter()
+        fde.fde_wait_selftest(h, 0)
+        torch.cuda.synchronize()
+        assert time.perf_counter() - t0 < 5.0
+        x.zero_()
+        with pytest.raises(fde.FDEError) as e:
+            fde.fde_solve(h, b, x)
+        assert e.value.code == fde.FDE_ERR_TIMEOUT
+        assert np.linalg.norm(host(x) - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+        st = fde.fde_solve(h, b, x)
+        assert st.converged
+        assert np.linalg.norm(host(x) - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+        res = np.linalg.norm(B - case.oracle_apply(host(x))) / np.linalg.norm(B)
+        assert res <= 1.05e-10
+    finally:
+        fde.fde_destroy(h)
+
+
+def test_wait_selftest_needs_a_tensor_core_level():
+    case = Case(inputs.perturbed_power_law(), 63, precision=fde.FDE_PREC_FP32)
+    h = case.handle()
+    try:
+        with pytest.raises(fde.FDEError) as e:
+            fde.fde_wait_selftest(h, 0)
+        assert e.value.code == fde.FDE_ERR_UNSUPPORTED
+        with pytest.raises(fde.FDEError) as e:
+            fde.fde_wait_selftest(h, 2)
+        assert e.value.code == fde.FDE_ERR_ARG
+    finally:
+        fde.fde_destroy(h)
