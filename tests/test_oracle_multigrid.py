@@ -345,6 +345,40 @@ def _fgmres_counts(kind, al, be, sizes):
     return counts
 
 
+def _cn_counts(kind, sizes):
+    # FGMRES(30) counts of one CN step of the perturbed power-law workload
+    # (alpha = 1.5, beta = 1.7, dt = h), rtol 1e-8
+    from paper_1706_06844_gb300 import inputs
+    from oracle.timeloop import make_preconditioner
+    from oracle.operator import cn_scalars, apply_M_fft, rhs_fft
+    pb = inputs.perturbed_power_law()
+    counts = []
+    for n in sizes:
+        X, Y, hx, hy = pb.grid(n, n)
+        wx, wy = wsgd_weights(pb.alpha, n + 1, 1, pb.qx), wsgd_weights(pb.beta, n + 1, 1, pb.qy)
+        sc = cn_scalars(pb.alpha, pb.beta, hx, hy, hx)
+        c, s = sc["c"], sc["sigma"]
+        c1, c0 = pb.coefficients(X, Y, hx), pb.coefficients(X, Y, 0.0)
+        B = rhs_fft(pb.exact(X, Y, 0.0), wx, wy, c, s, *c0, pb.source(X, Y, 0.5 * hx), hx,
+                    pb.alpha)
+        prec, _ = make_preconditioner(kind, pb.alpha, pb.beta, wx, wy, n, n, sc, c1)
+        x, its, rel, ok = fgmres(lambda Z: apply_M_fft(Z, wx, wy, c, s, *c1), B, prec, 30, 1e-8)
+        assert ok
+        counts.append(its)
+    return counts
+
+
+def test_cn_step_counts_flat_in_n():
+    # Sec. 4-5: for a CN step of a smooth problem the multigrid preconditioners'
+    # counts do not grow with n (structured Galerkin and rediscretised alike);
+    # P_2 needs more iterations at every size when alpha, beta are away from 2
+    sizes = [31, 63, 127, 255]
+    sg, rd, p2 = (_cn_counts(k, sizes) for k in ("sg", "redisc", "p2"))
+    for c in (sg, rd):
+        assert 12 <= min(c) and max(c) <= 16 and max(c) - min(c) <= 2, (sg, rd)
+    assert all(a > b for a, b in zip(p2, sg)), (p2, sg)
+
+
 def test_iteration_counts_flat_in_n_for_multigrid_not_for_p2():
     # Sec. 4 / Sec. 5: the V-cycle preconditioner's iteration count is (nearly)
     # independent of n and of alpha, beta; the band preconditioner P_2 is a
@@ -353,8 +387,9 @@ def test_iteration_counts_flat_in_n_for_multigrid_not_for_p2():
     sizes = [15, 31, 63, 127, 255]
     far, near = (1.2, 1.3), (1.9, 1.8)
     sg_far, sg_near = _fgmres_counts("sg", *far, sizes), _fgmres_counts("sg", *near, sizes)
+    rd_far, rd_near = _fgmres_counts("redisc", *far, sizes), _fgmres_counts("redisc", *near, sizes)
     p2_far, p2_near = _fgmres_counts("p2", *far, sizes), _fgmres_counts("p2", *near, sizes)
-    for c in (sg_far, sg_near):
+    for c in (sg_far, sg_near, rd_far, rd_near):
         assert max(c) <= 16 and c[-1] - c[0] <= 5, c
     assert abs(sg_far[-1] - sg_near[-1]) <= 2, (sg_far, sg_near)
     assert p2_far[-1] - p2_far[0] >= 2 * (sg_far[-1] - sg_far[0]), (p2_far, sg_far)
