@@ -196,7 +196,10 @@ int fde_weights(const fde_handle* h, int axis, double* w_host, int count);
 /* Solve M x = b (Eq. 2) from x = 0: by FGMRES(restart), right
  * preconditioned (Sec. 5), or with params.solver = FDE_SOLVER_MG by the
  * stationary multigrid iteration.  Writes x even when not converged
- * (FDE_ERR_NOT_CONVERGED).  `st` may be NULL.  Synchronises the stream. */
+ * (FDE_ERR_NOT_CONVERGED).  FDE_ERR_NONFINITE: NaN/Inf in a residual norm.
+ * FDE_ERR_TIMEOUT: a capped wait of a tensor-core kernel gave up during the
+ * solve (x is written; the flag is cleared, so the handle stays usable).
+ * `st` may be NULL.  Synchronises the stream. */
 int fde_solve(fde_handle* h, const double* b, double* x, fde_stats* st);
 
 /* One CN-WSGD time step (Eq. CNWSGD): b from u_prev, v_half and the OLD
