@@ -103,7 +103,9 @@ typedef struct fde_params {
   int    outer;            /* FDE_OUTER_* */
   int    cycles;           /* V-cycles per preconditioner application (0 or 1: one; at most 4);
                               cycle k + 1 corrects the residual of cycle k (Sec. 5.1 tries two
-                              for P_2) */
+                              for P_2).  When n1 or n2 <= coarsest_n the hierarchy has one
+                              level, the cycle is the exact coarsest-grid solve, and the
+                              Toeplitz preconditioners run it once */
   int    relax;            /* 1: relaxed Krylov matvec -- once the FGMRES residual estimate is
                               within FDE_RELAX_FACTOR of rtol ||b||, M z is evaluated in FP32
                               (inexact Krylov: matvec errors eta_j with

@@ -690,7 +690,9 @@ struct MG : MGBase {
     Lv& L = lv[0];
     LCHK((launch_convert<double, T>(L.N, r, 1.0, L.b, h->st)));
     RCHK(run_cycle(h));
-    const int cycles = h->p.cycles > 1 ? h->p.cycles : 1;
+    // a one-level hierarchy is the coarsest-grid solve itself, exact up to
+    // rounding: further cycles are skipped (level 0 then has no product path)
+    const int cycles = (h->p.cycles > 1 && lv.size() > 1) ? h->p.cycles : 1;
     if (cycles > 1) {
       // stationary iteration z_{k+1} = z_k + V(r - K_0 z_k): r is kept in acc_b,
       // each cycle reads its right-hand side from L.b and leaves z in L.x
