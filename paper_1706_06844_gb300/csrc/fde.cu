@@ -944,8 +944,6 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
   }
   const double* dp = old ? h->dpO : h->dpN;
   const double* dm = old ? h->dmO : h->dmN;
-  const double* ep = old ? h->epOs : h->epNs;
-  const double* em = old ? h->emOs : h->emNs;
   int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
   LCHK((launch_fft_pass<double, double, double>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x, h->S2x,
                                         h->twx, dp, dm, x, h->c, y, 0, h->st, h->fft_ws,

@@ -123,9 +123,10 @@ __global__ void stencil_convert_kernel(const double* __restrict__ S, size_t N, d
                                        T* __restrict__ ST, T* __restrict__ W) {
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
        idx += (size_t)gridDim.x * blockDim.x) {
+    if (ST) {
 #pragma unroll
-    if (ST)
       for (int o = 0; o < 9; ++o) ST[(size_t)o * N + idx] = (T)S[(size_t)o * N + idx];
+    }
     W[idx] = (T)(omega / S[4 * N + idx]);
   }
 }
