@@ -394,3 +394,62 @@ def test_iteration_counts_flat_in_n_for_multigrid_not_for_p2():
     assert abs(sg_far[-1] - sg_near[-1]) <= 2, (sg_far, sg_near)
     assert p2_far[-1] - p2_far[0] >= 2 * (sg_far[-1] - sg_far[0]), (p2_far, sg_far)
     assert p2_far[-1] > p2_near[-1] + 5, (p2_far, p2_near)
+
+
+def test_grid_transfer_helpers():
+    # Sec. 4.1 / 4.2: for odd n = 2k + 1 the coarse nodes are fine nodes (the
+    # coarse grid of width 2h sits on every other fine node); the level sizes
+    # halve down to the fixed coarsest grid (n = 2047: 9 levels down to 7)
+    for n in [7, 15, 63, 2047]:
+        k = mg.coarse_size(n)
+        assert n == 2 * k + 1
+        xf = (mg.coarse_to_fine(n) + 1) / (n + 1)
+        xc = np.arange(1, k + 1) / (k + 1)
+        np.testing.assert_allclose(xf, xc, rtol=0, atol=1e-15)
+    assert mg.level_sizes(2047) == [2047, 1023, 511, 255, 127, 63, 31, 15, 7]
+    assert mg.level_sizes(16) == [16, 8]
+    # even n: k = n/2 coarse nodes on the odd fine nodes (1-based 1, 3, ...)
+    assert list(mg.coarse_to_fine(8)) == [0, 2, 4, 6]
+
+
+def test_jacobi_sweep_and_fixed_point():
+    # Eq. (Sn): from x = 0 one sweep gives omega b / diag(K); the solution of
+    # K x = b is a fixed point of the damped iteration
+    n = 15
+    wx, wy = wsgd_weights(1.6, n), wsgd_weights(1.4, n)
+    X, Y = np.meshgrid(np.arange(1, n + 1) / (n + 1), np.arange(1, n + 1) / (n + 1))
+    cf = (1 + X * Y, 2 - X, 1 + Y, 1.5 + 0 * X)
+    hier = mg.structured_galerkin(wx, wy, n, n, 0.4, 1.3, cf)
+    lev = hier.levels[0]
+    K = assemble_M(toeplitz_A(wx, n), toeplitz_A(wy, n), 0.4, 1.3, *cf)
+    np.testing.assert_allclose(lev.diag().ravel(), np.diag(K), rtol=1e-14)
+    b = rng.standard_normal((n, n))
+    x1 = mg.jacobi(lev, np.zeros((n, n)), b, 0.7, 1)
+    np.testing.assert_allclose(x1.ravel(), 0.7 * b.ravel() / np.diag(K), rtol=1e-14)
+    xs = np.linalg.solve(K, b.ravel()).reshape(n, n)
+    np.testing.assert_allclose(mg.jacobi(lev, xs, b, 0.7, 3), xs, rtol=0, atol=1e-12)
+
+
+def test_laplacian_weights_and_shift_choice():
+    # gamma = 2 member of Eq. (w): the second difference (1, -2, 1); the shift
+    # used by the drawn workloads switches to (1,-1) below gamma_0 (Sec. 2)
+    from oracle.wsgd import choose_shift, GAMMA0
+    np.testing.assert_array_equal(mg.laplacian_weights(), [1.0, -2.0, 1.0])
+    A2 = toeplitz_A(np.r_[mg.laplacian_weights(), np.zeros(4)], 5)
+    np.testing.assert_array_equal(A2, 2 * np.eye(5) - np.eye(5, k=1) - np.eye(5, k=-1))
+    assert choose_shift(GAMMA0, 1.9) == 0 and choose_shift(1.9, GAMMA0) == 0
+    assert choose_shift(GAMMA0 - 1e-9, 1.9) == -1 and choose_shift(1.9, 1.2) == -1
+
+
+def test_apply_kron_with_mass_factors_equals_dense_kronecker():
+    # the coarse-level form c (By (x) Bx) + D+ (By (x) Ax) + ... evaluated by
+    # matmuls equals the explicit Kronecker products
+    from oracle.operator import apply_kron
+    n1, n2 = 6, 5
+    Ax, Ay = rng.standard_normal((n1, n1)), rng.standard_normal((n2, n2))
+    Bx, By = rng.standard_normal((n1, n1)), rng.standard_normal((n2, n2))
+    cf = [rng.uniform(0.5, 2, (n2, n1)) for _ in range(4)]
+    X = rng.standard_normal((n2, n1))
+    K = assemble_M(Ax, Ay, 0.3, 1.7, *cf, Bx=Bx, By=By)
+    np.testing.assert_allclose(apply_kron(X, Ax, Ay, 0.3, 1.7, *cf, Bx, By).ravel(),
+                               K @ X.ravel(), rtol=1e-12, atol=1e-12)
