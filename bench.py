@@ -314,25 +314,37 @@ class OracleStep:
         self.rhs = lambda: rhs_fft(U, wx, wy, c, s, *coef, V, hx, prob.alpha)
         self.A = lambda Z: apply_M_fft(Z, wx, wy, c, s, *coef)
         self.prec = lambda R: mg.vcycle(hier, R)
+        self.wall_s = 0.0  # timed wall and process CPU seconds (all threads)
+        self.cpu_s = 0.0
+
+    def threads_used(self):
+        """Effective number of host threads of the timed work: process CPU
+        time over wall time, at least 1."""
+        return max(1, int(round(self.cpu_s / self.wall_s))) if self.wall_s > 0 else 1
 
     def full(self):
         """Time one whole step; returns (seconds, iterations, solution, rhs)."""
         from oracle.krylov import fgmres
-        t0 = time.perf_counter()
+        c0, t0 = time.process_time(), time.perf_counter()
         B = self.rhs()
         x, its, rel, ok = fgmres(self.A, B, self.prec, RESTART, RTOL)
-        return time.perf_counter() - t0, its, x, B
+        t = time.perf_counter() - t0
+        self.wall_s += t
+        self.cpu_s += time.process_time() - c0
+        return t, its, x, B
 
     def sample(self, iters):
         """Time the right-hand side and the first `iters` FGMRES iterations
         (with the closing true residual); returns (rhs seconds, iteration
         seconds per iteration)."""
         from oracle.krylov import fgmres
-        t0 = time.perf_counter()
+        c0, t0 = time.process_time(), time.perf_counter()
         B = self.rhs()
         t1 = time.perf_counter()
         fgmres(self.A, B, self.prec, RESTART, RTOL, maxit=iters)
         t2 = time.perf_counter()
+        self.wall_s += t2 - t0
+        self.cpu_s += time.process_time() - c0
         return t1 - t0, (t2 - t1) / iters
 
 
@@ -344,10 +356,11 @@ def cpu_baseline_sample(refine=False):
     from oracle.krylov import fgmres
     o = OracleStep()
     t, its, x, B = o.full()
+    threads = o.threads_used()
     if refine:
         xr, _, _, _ = fgmres(o.A, B, o.prec, RESTART, 1e-12, x0=x)
-        return t, its, xr
-    return t, its
+        return t, its, xr, threads
+    return t, its, threads
 
 
 def run_reference(args, rank):
@@ -367,7 +380,7 @@ def run_reference(args, rank):
             times.append(t_rhs + t_it * its_full)
     total = sum(times)
     v = args.steps / total
-    cores = os.cpu_count()
+    cores = o.threads_used()
     sample = (f"one whole CN step at n=2047 ({its_full} FGMRES iterations, {t_full:.1f} s); "
               f"then each step: the right-hand side + the first {sample_its} FGMRES(30)/SG "
               f"V-cycle iterations of the FP64 numpy oracle, scaled to {its_full} iterations")
@@ -377,7 +390,8 @@ def run_reference(args, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N_GRID, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": round(v, 5), "unit": "steps/s", "cores": cores,
-                             "kind": "oracle", "sample": sample},
+                             "cores_available": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": round(v, 5), "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "whole_step_s": round(t_full, 2), "iterations_per_step": [its_full]}
@@ -612,8 +626,9 @@ def main():
     cpu = None
     accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, k, xref = cpu_baseline_sample(refine=True)
-        cpu = {"value": round(1.0 / t, 5), "unit": "steps/s", "cores": os.cpu_count(),
+        t, k, xref, threads = cpu_baseline_sample(refine=True)
+        cpu = {"value": round(1.0 / t, 5), "unit": "steps/s", "cores": threads,
+               "cores_available": os.cpu_count(),
                "kind": "oracle", "sample": f"one CN step at n=2047 of the FP64 numpy oracle "
                                            f"({k} FGMRES iterations, {t:.1f} s)"}
         err = float(np.linalg.norm(first - xref) / np.linalg.norm(xref))
