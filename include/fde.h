@@ -239,12 +239,15 @@ int fde_wait_selftest(fde_handle* h, int complete);
 /* Kernel-level timing with CUDA events on the handle's stream (off by
  * default).  Kernel classes: FDE_KCLASS_*.  fde_profile_query returns the
  * number of launches and their summed event time since the last reset. */
-#define FDE_KCLASS_OUTER_APPLY  0  /* FP64-accurate Toeplitz apply (both directions) */
-#define FDE_KCLASS_LEVEL_APPLY  1  /* preconditioner Toeplitz products */
+#define FDE_KCLASS_OUTER_APPLY  0  /* FP64-accurate Toeplitz apply, whole apply (both FFT passes
+                                      and the transposes of the column pass) */
+#define FDE_KCLASS_LEVEL_APPLY  1  /* preconditioner Toeplitz products (incl. operand packing) */
 #define FDE_KCLASS_KRYLOV       2  /* Arnoldi / update / norm kernels */
 #define FDE_KCLASS_MG_OTHER     3  /* smoother, transfers, coarse solve */
 #define FDE_KCLASS_OUTER_FP32   4  /* relaxed (FP32) Krylov matvecs, whole apply */
-#define FDE_KCLASS_COUNT        5
+#define FDE_KCLASS_TC_GEMM      5  /* each tcgen05 products launch (one direction) on its own;
+                                      these launches are also counted in LEVEL_APPLY */
+#define FDE_KCLASS_COUNT        6
 int fde_profile_enable(fde_handle* h, int on);
 int fde_profile_query(fde_handle* h, int kclass, long long* launches, double* ms);
 /* Total kernels this handle has launched. */
@@ -289,7 +292,10 @@ int fde_batch_status(const fde_batch* b, int i);
  * the working data (weights, spectra, twiddles, about 450 KB) lives in one
  * fixed device array that every GPU loading the library holds until exit.
  * The first call on a device looks that array up (cudaGetSymbolAddress) with
- * the device current; make that first call before any stream capture.  Each
+ * the device current and keeps the address; make that first call before any
+ * stream capture, and do not reset the device (cudaDeviceReset) between calls:
+ * a kept address would then be stale.  y must not overlap x or a coefficient
+ * array (FDE_ERR_ARG).  Each
  * call rewrites the array before using it; calls that overlap on the GPU
  * (other streams or host threads) race on it and must be serialised by the
  * caller.  Work is enqueued on `stream`; errors via fde_last_error(NULL). */

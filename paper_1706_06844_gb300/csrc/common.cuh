@@ -33,6 +33,11 @@ __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
 // ---------------------------------------------------------------- launches
 // Every launcher returns the cudaError_t of its launch (cudaGetLastError()).
 
+// Raise a kernel's dynamic shared-memory limit to 227 KB on the CURRENT
+// device, once per (kernel, device): the attribute belongs to one device, so a
+// process that launches on several GPUs sets it on each.  Thread-safe.
+cudaError_t ensure_max_smem(const void* kernel);
+
 // Circulant-embedding Toeplitz pass over a set of vectors (rows or columns of a
 // grid).  For every vector v (elements x_v[i] = X[v*vs + i*es], i < n):
 //   y_v[i] = cmass * M[v*vs + i*es] + cp[.] * (A x_v)_i + cm[.] * (A^T x_v)_i

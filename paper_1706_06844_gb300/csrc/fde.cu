@@ -596,10 +596,21 @@ struct MG : MGBase {
       LCHK(launch_direct_pass<T>(xin_y, L.n1, 1, L.n1, L.n2, L.tyT, L.ep, L.em, nullptr, 0.0, kx,
                                  1, st));
     } else {
-      int r = tc::level_products(&L.gemm, (const float*)xin_x, (const float*)xin_y,
-                                 (const float*)M, cm, (const float*)L.dp, (const float*)L.dm,
-                                 (const float*)L.ep, (const float*)L.em, (float*)kx, st);
-      h->launches += (sg && l > 0) ? 4 : 3;
+      int r = tc::level_pack(&L.gemm, (const float*)xin_x, (const float*)xin_y, st);
+      h->launches += (sg && l > 0) ? 2 : 1;
+      if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core operand packing failed (%d)", r);
+      // each direction is one launch, timed on its own (FDE_KCLASS_TC_GEMM)
+      int gi = h->pbeg(FDE_KCLASS_TC_GEMM);
+      r = tc::level_gemm(&L.gemm, 0, (const float*)M, cm, (const float*)L.dp, (const float*)L.dm,
+                         (float*)kx, st);
+      h->pend(gi);
+      h->launches++;
+      if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core products failed (%d)", r);
+      gi = h->pbeg(FDE_KCLASS_TC_GEMM);
+      r = tc::level_gemm(&L.gemm, 1, nullptr, 0.0, (const float*)L.ep, (const float*)L.em,
+                         (float*)kx, st);
+      h->pend(gi);
+      h->launches++;
       if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core products failed (%d)", r);
     }
     h->pend(pi);
@@ -926,38 +937,34 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
   NvtxRange range("matvec");
   if (h->p.outer == FDE_OUTER_DF32) {
     df* const* cf = old ? h->cfO : h->cfN;
-    int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
+    const int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
     cx<df>* ws = reinterpret_cast<cx<df>*>(h->fft_ws);
     LCHK((launch_fft_pass<double, df, df>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1xd, h->S2xd,
                                           h->twxd, cf[0], cf[1], x, h->c, y, 0, h->st, ws,
                                           h->fft_ws_elems)));
-    h->pend(pi);
     df* const* cfT = old ? h->cfOT : h->cfNT;
     LCHK(launch_transpose<double>(x, h->n2, h->n1, h->xT, 0, h->st));
-    pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
     LCHK((launch_fft_pass<double, df, df>(h->xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1yd,
                                           h->S2yd, h->twyd, cfT[0], cfT[1], nullptr, 0.0, h->yT, 0,
                                           h->st, ws, h->fft_ws_elems)));
-    h->pend(pi);
     LCHK(launch_transpose<double>(h->yT, h->n1, h->n2, y, 1, h->st));
+    h->pend(pi);
     return FDE_OK;
   }
   const double* dp = old ? h->dpO : h->dpN;
   const double* dm = old ? h->dmO : h->dmN;
-  int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
+  const int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
   LCHK((launch_fft_pass<double, double, double>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x, h->S2x,
                                         h->twx, dp, dm, x, h->c, y, 0, h->st, h->fft_ws,
                                         h->fft_ws_elems)));
-  h->pend(pi);
   const double* epT = old ? h->epOsT : h->epNsT;
   const double* emT = old ? h->emOsT : h->emNsT;
   LCHK(launch_transpose<double>(x, h->n2, h->n1, h->xT, 0, h->st));
-  pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
   LCHK((launch_fft_pass<double, double, double>(h->xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1y,
                                                 h->S2y, h->twy, epT, emT, nullptr, 0.0, h->yT, 0,
                                                 h->st, h->fft_ws, h->fft_ws_elems)));
-  h->pend(pi);
   LCHK(launch_transpose<double>(h->yT, h->n1, h->n2, y, 1, h->st));
+  h->pend(pi);
   return FDE_OK;
 }
 

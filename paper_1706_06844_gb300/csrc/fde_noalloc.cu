@@ -12,12 +12,15 @@
 // file-scope device array (NOALLOC_BYTES, about 450 KB), which every GPU that
 // loads the library holds until the process exits.  Every call shares that
 // array and rewrites all of it before use; two calls that overlap on the GPU
-// (different streams, or different host threads) race on it.
+// (different streams, or different host threads) race on it.  The array's
+// device address is looked up once per device and kept, so the device must
+// not be reset (cudaDeviceReset) between calls.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdint>
 #include <mutex>
 
 #include "common.cuh"
@@ -78,6 +81,12 @@ int fail(int code, const char* msg) {
   return code;
 }
 
+// true if the byte ranges [a, a + na) and [b, b + nb) share a byte
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+  return a0 < b0 + nb && b0 < a0 + na;
+}
+
 }  // namespace
 
 extern "C" int fde_apply_noalloc(const fde_params* p, const double* dp, const double* dm,
@@ -101,6 +110,12 @@ extern "C" int fde_apply_noalloc(const fde_params* p, const double* dp, const do
              p->n1, p->n2, kMaxN);
     return fail(FDE_ERR_ARG, buf);
   }
+  // y is written while other CTAs still read x and the coefficients: no
+  // byte of y may belong to any input
+  const size_t nbytes = (size_t)p->n1 * p->n2 * sizeof(double);
+  for (const double* in : {x, dp, dm, ep, em})
+    if (overlaps(y, nbytes, in, nbytes))
+      return fail(FDE_ERR_ARG, "fde_apply_noalloc: y overlaps an input array");
   void* base = nullptr;
   int rc = scratch_address(&base);
   if (rc != FDE_OK) return rc;

@@ -13,10 +13,27 @@
 //    (bit-reversed in, natural out) give A x and A^T x of both vectors at once
 //    -- no bit-reversal permutation is ever performed.
 //  * direct_pass: plain O(n^2) summation for small levels.
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "common.cuh"
 #include "df32.cuh"
 
 namespace fde {
+
+cudaError_t ensure_max_smem(const void* kernel) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({kernel, dev})) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) done.insert({kernel, dev});
+  return e;
+}
 
 __device__ __forceinline__ int bitrev(int x, int bits) {
   return (int)(__brev((unsigned)x) >> (32 - bits));
@@ -322,14 +339,8 @@ cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int log
   if (fft_pass_two_buffer_bytes(logL, sizeof(cx<R>)) > 227 * 1024) {
     const size_t smem1 = (size_t)padded_len(L) * sizeof(cx<R>);
     if (smem1 > 227 * 1024) return cudaErrorInvalidValue;
-    static bool attr1 = false;
-    if (!attr1) {
-      cudaError_t e = cudaFuncSetAttribute(fft_pass_seq_kernel<T, R, C>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           227 * 1024);
-      if (e != cudaSuccess) return e;
-      attr1 = true;
-    }
+    cudaError_t e = ensure_max_smem((const void*)fft_pass_seq_kernel<T, R, C>);
+    if (e != cudaSuccess) return e;
     const int per_sm = (int)((227 * 1024) / (smem1 + 1024));
     int grid = 152 * (per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm));
     if (grid > npairs) grid = npairs;
@@ -340,12 +351,9 @@ cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int log
     return cudaGetLastError();
   }
   const size_t smem = 2 * (size_t)padded_len(L) * sizeof(cx<R>);
-  static bool attr_set = false;  // per instantiation
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, R, C>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (smem > 48 * 1024) {
+    cudaError_t e = ensure_max_smem((const void*)fft_pass_kernel<T, R, C>);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   const int per_sm = (int)((227 * 1024) / (smem + 1024));
   int grid = 152 * (per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm));

@@ -763,43 +763,40 @@ int level_setup(ToeplitzGemmLevel* L, const double* tx, const double* ty, cudaSt
 }
 
 template <int NT>
-static void launch_pair(ToeplitzGemmLevel* L, Maps* m, const float* M, double cm,
-                        const float* dp, const float* dm, const float* ep, const float* em,
-                        float* kx, bool f16, cudaStream_t st) {
+static void launch_dir(ToeplitzGemmLevel* L, Maps* m, int dir, const float* M, double cm,
+                       const float* c0, const float* c1, float* kx, bool f16, cudaStream_t st) {
   KParams kp;
-  kp.M = M;
   kp.cm = (float)cm;
   kp.n1 = L->n1;
   kp.n2 = L->n2;
   kp.inv_scale = f16 ? 1.f / 1024.f : 1.f;
   kp.err = m->err;
   kp.out = kx;
-  // x products: kx = cm M + dp (X A_x^T) + dm (X A_x)
-  kp.gen_hi = (const uint16_t*)m->genx_hi;
-  kp.gen_lo = (const uint16_t*)(NT == 2 ? m->genx_lo : m->genx_hi);
-  kp.glen = m->glen_x;
-  kp.c0 = dp;
-  kp.c1 = dm;
-  dim3 gx((L->n1 + BN - 1) / BN, (L->n2 + BM - 1) / BM);
-  toeplitz_gemm_kernel<0, NT><<<gx, NUM_THREADS, Cfg<NT>::FIXED + NT * gen_bytes(L->n1), st>>>(
-      m->ax[0], m->ax[1], kp, make_idesc(false, f16));
-  // y products (transposed tiles): kx += ep (A_y Y) + em (A_y^T Y)
-  kp.M = nullptr;
-  kp.gen_hi = (const uint16_t*)m->geny_hi;
-  kp.gen_lo = (const uint16_t*)(NT == 2 ? m->geny_lo : m->geny_hi);
-  kp.glen = m->glen_y;
-  kp.c0 = ep;
-  kp.c1 = em;
-  dim3 gy((L->n2 + BN - 1) / BN, (L->n1 + BM - 1) / BM);
-  toeplitz_gemm_kernel<1, NT><<<gy, NUM_THREADS, Cfg<NT>::FIXED + NT * gen_bytes(L->n2), st>>>(
-      m->ay[0], m->ay[1], kp, make_idesc(true, f16));
+  kp.c0 = c0;
+  kp.c1 = c1;
+  if (dir == 0) {
+    // x products: kx = cm M + dp (X A_x^T) + dm (X A_x)
+    kp.M = M;
+    kp.gen_hi = (const uint16_t*)m->genx_hi;
+    kp.gen_lo = (const uint16_t*)(NT == 2 ? m->genx_lo : m->genx_hi);
+    kp.glen = m->glen_x;
+    dim3 gx((L->n1 + BN - 1) / BN, (L->n2 + BM - 1) / BM);
+    toeplitz_gemm_kernel<0, NT><<<gx, NUM_THREADS, Cfg<NT>::FIXED + NT * gen_bytes(L->n1), st>>>(
+        m->ax[0], m->ax[1], kp, make_idesc(false, f16));
+  } else {
+    // y products (transposed tiles): kx += ep (A_y Y) + em (A_y^T Y)
+    kp.M = nullptr;
+    kp.gen_hi = (const uint16_t*)m->geny_hi;
+    kp.gen_lo = (const uint16_t*)(NT == 2 ? m->geny_lo : m->geny_hi);
+    kp.glen = m->glen_y;
+    dim3 gy((L->n2 + BN - 1) / BN, (L->n1 + BM - 1) / BM);
+    toeplitz_gemm_kernel<1, NT><<<gy, NUM_THREADS, Cfg<NT>::FIXED + NT * gen_bytes(L->n2), st>>>(
+        m->ay[0], m->ay[1], kp, make_idesc(true, f16));
+  }
 }
 
-int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y, const float* M,
-                   double cm, const float* dp, const float* dm, const float* ep, const float* em,
-                   float* kx, cudaStream_t st) {
+int level_pack(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y, cudaStream_t st) {
   if (!L->built) return 30;
-  Maps* m = (Maps*)L->maps;
   const int n1 = L->n1, n2 = L->n2;
   const size_t N = (size_t)n1 * n2;
   int g = (int)((N + 255) / 256);
@@ -816,10 +813,28 @@ int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y,
       pack_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(xin_y, n1, n2, L->ld, (__nv_bfloat16*)L->xb,
                                                     (__nv_bfloat16*)(split ? L->xb_lo : nullptr));
   }
-  const bool f16 = L->prec == kFP16;
-  if (split) launch_pair<2>(L, m, M, cm, dp, dm, ep, em, kx, f16, st);
-  else launch_pair<1>(L, m, M, cm, dp, dm, ep, em, kx, f16, st);
   return cudaGetLastError() == cudaSuccess ? 0 : 31;
+}
+
+int level_gemm(ToeplitzGemmLevel* L, int dir, const float* M, double cm, const float* c0,
+               const float* c1, float* kx, cudaStream_t st) {
+  if (!L->built) return 30;
+  if (dir != 0 && dir != 1) return 32;
+  Maps* m = (Maps*)L->maps;
+  const bool f16 = L->prec == kFP16;
+  if (L->prec == kBF16X3) launch_dir<2>(L, m, dir, M, cm, c0, c1, kx, f16, st);
+  else launch_dir<1>(L, m, dir, M, cm, c0, c1, kx, f16, st);
+  return cudaGetLastError() == cudaSuccess ? 0 : 31;
+}
+
+int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y, const float* M,
+                   double cm, const float* dp, const float* dm, const float* ep, const float* em,
+                   float* kx, cudaStream_t st) {
+  int r = level_pack(L, xin_x, xin_y, st);
+  if (r) return r;
+  r = level_gemm(L, 0, M, cm, dp, dm, kx, st);
+  if (r) return r;
+  return level_gemm(L, 1, nullptr, 0.0, ep, em, kx, st);
 }
 
 int level_error(ToeplitzGemmLevel* L, cudaStream_t st) {

@@ -37,6 +37,14 @@ int level_setup(ToeplitzGemmLevel* L, const double* tx, const double* ty, cudaSt
 int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y, const float* M,
                    double cm, const float* dp, const float* dm, const float* ep, const float* em,
                    float* kx, cudaStream_t st);
+// the same in its three steps, for callers that time the launches one by one:
+// level_pack writes the 16-bit operand copies of xin_x (and xin_y on
+// structured-Galerkin levels); level_gemm launches one direction, dir 0:
+// kx = cm * M + c0 (.) (X A_x^T) + c1 (.) (X A_x), dir 1: kx += c0 (.) (A_y Y)
+// + c1 (.) (A_y^T Y) (M ignored)
+int level_pack(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y, cudaStream_t st);
+int level_gemm(ToeplitzGemmLevel* L, int dir, const float* M, double cm, const float* c0,
+               const float* c1, float* kx, cudaStream_t st);
 // 1 if a capped wait of the level's kernels gave up since the last call (the flag
 // is then cleared), 0 if not, -1 if the flag could not be read; syncs `st`
 int level_error(ToeplitzGemmLevel* L, cudaStream_t st);

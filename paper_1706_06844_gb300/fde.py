@@ -21,7 +21,7 @@ FDE_OUTER_FP64, FDE_OUTER_DF32 = 0, 1
 FDE_SOLVER_FGMRES, FDE_SOLVER_MG = 0, 1
 FDE_COEF_NEW, FDE_COEF_OLD = 0, 1
 FDE_KCLASS_OUTER_APPLY, FDE_KCLASS_LEVEL_APPLY, FDE_KCLASS_KRYLOV, FDE_KCLASS_MG_OTHER = 0, 1, 2, 3
-FDE_KCLASS_OUTER_FP32, FDE_KCLASS_COUNT = 4, 5
+FDE_KCLASS_OUTER_FP32, FDE_KCLASS_TC_GEMM, FDE_KCLASS_COUNT = 4, 5, 6
 
 
 class fde_params(ctypes.Structure):

@@ -80,3 +80,42 @@ class Case:
                                           self.coef_new, p.coarsest_n)
         return mg.rediscretised(self.problem.alpha, self.problem.beta, self.wx, self.wy,
                                 self.n1, self.n2, c, s, self.coef_new, p.coarsest_n)
+
+
+def sampled_apply(Ax, Ay, c, sigma, dp, dm, ep, em, X, rows, cols):
+    """Rows `rows` and columns `cols` of K x and of |K||x| for
+    K = c I + D+ (I (x) Ax) + D- (I (x) Ax^T) + sigma [E+ (Ay (x) I) + E- (Ay^T (x) I)]
+    (Eq. M written with dense 1-D factors), each entry summed on its own:
+    O(n^2) per sampled line instead of the whole O(n^3) product.
+    Returns (K x rows, |K||x| rows, K x cols, |K||x| cols)."""
+    X = np.asarray(X)
+    aX, aAx, aAy = np.abs(X), np.abs(Ax), np.abs(Ay)
+
+    def row(j, Z, A1, A2, absolute):
+        f = (lambda a: np.abs(a)) if absolute else (lambda a: a)
+        return (abs(c) * Z[j] if absolute else c * Z[j]) \
+            + f(dp[j]) * (Z[j] @ A1.T) + f(dm[j]) * (Z[j] @ A1) \
+            + (abs(sigma) if absolute else sigma) * (
+                f(ep[j]) * (A2[j] @ Z) + f(em[j]) * (A2.T[j] @ Z))
+
+    def col(i, Z, A1, A2, absolute):
+        f = (lambda a: np.abs(a)) if absolute else (lambda a: a)
+        return (abs(c) * Z[:, i] if absolute else c * Z[:, i]) \
+            + f(dp[:, i]) * (Z @ A1.T[:, i]) + f(dm[:, i]) * (Z @ A1[:, i]) \
+            + (abs(sigma) if absolute else sigma) * (
+                f(ep[:, i]) * (A2 @ Z[:, i]) + f(em[:, i]) * (A2.T @ Z[:, i]))
+
+    R = np.array([row(j, X, Ax, Ay, False) for j in rows])
+    Ra = np.array([row(j, aX, aAx, aAy, True) for j in rows])
+    C = np.array([col(i, X, Ax, Ay, False) for i in cols]).T
+    Ca = np.array([col(i, aX, aAx, aAy, True) for i in cols]).T
+    return R, Ra, C, Ca
+
+
+def sample_lines(n, count, rng):
+    """`count` line indices of an n-point axis: both ends, the tile edges of
+    128 and 256 near the middle, and random interior lines."""
+    fixed = [0, 1, n - 2, n - 1, min(n - 1, 127), min(n - 1, 128), min(n - 1, 255),
+             min(n - 1, 256)]
+    extra = list(rng.choice(n, size=max(0, count - len(fixed)), replace=False))
+    return sorted(set(int(v) for v in fixed + extra))

@@ -81,7 +81,8 @@ def test_bench_configuration_n2047():
             assert st.converged == 1 and res <= 1.05e-8, (name, res)
             its[name] = st.iterations
             if name == "mixed":
-                assert fde.fde_level_path(h, 0) in (fde.FDE_PATH_GEMM, fde.FDE_PATH_FFT)
+                # the tuner keeps the tensor cores for the bench grid's level 0
+                assert fde.fde_level_path(h, 0) == fde.FDE_PATH_GEMM
                 assert st.relaxed > 0
         finally:
             fde.fde_destroy(h)

@@ -11,7 +11,7 @@ import pytest
 
 from paper_1706_06844_gb300 import inputs
 from paper_1706_06844_gb300 import fde
-from gpu_util import Case, dev, host
+from gpu_util import Case, dev, host, sampled_apply, sample_lines
 
 pytestmark = pytest.mark.gpu
 
@@ -38,11 +38,12 @@ def test_gemm_level_apply(precision, precond, n1, n2):
         pytest.skip("level sizes must stay odd")
     case = Case(inputs.perturbed_power_law(), n1, n2, precond=precond, precision=precision,
                 toeplitz_path=fde.FDE_PATH_GEMM)
+    # a tensor-core level that cannot be created is a failure, not a skip
+    h = case.handle()
     try:
-        h = case.handle()
-    except fde.FDEError as e:
-        pytest.skip(str(e))
-    try:
+        for l, (m1, m2) in enumerate(fde.fde_levels(h)[:-1]):
+            if min(m1, m2) >= 127:
+                assert fde.fde_level_path(h, l) == fde.FDE_PATH_GEMM, l
         hier = case.oracle_hierarchy()
         rng = np.random.default_rng(9)
         for l, lev in enumerate(hier.levels):
@@ -61,6 +62,40 @@ def test_gemm_level_apply(precision, precond, n1, n2):
             assert rel <= 0.05
             # 16-bit operands really were used (an FP32 path would sit near 1e-7)
             assert rel > 1e-6 * (U16[precision] / 2.0 ** -11), rel
+    finally:
+        fde.fde_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [fde.FDE_PREC_BF16X3, fde.FDE_PREC_BF16, fde.FDE_PREC_FP16])
+def test_gemm_level0_products_n2047(precision):
+    # the bench grid's level-0 products forced onto the tensor cores (no tuner,
+    # no fallback), element by element on sampled rows and columns (both ends,
+    # the 128/256 tile edges, random lines) against the oracle's level-0
+    # operator under the same error model as the smaller sizes
+    import torch
+    from oracle.operator import toeplitz_A
+    n = 2047
+    case = Case(inputs.perturbed_power_law(), n, precond=fde.FDE_PRECOND_MG_SG,
+                precision=precision, toeplitz_path=fde.FDE_PATH_GEMM)
+    h = case.handle()
+    try:
+        assert fde.fde_level_path(h, 0) == fde.FDE_PATH_GEMM
+        rng = np.random.default_rng(2047)
+        X = rng.standard_normal((n, n))
+        y = torch.empty_like(dev(X))
+        fde.fde_level_apply(h, 0, dev(X), y)
+        torch.cuda.synchronize()
+        yh = host(y)
+        Ax, Ay = toeplitz_A(case.wx, n), toeplitz_A(case.wy, n)
+        rows, cols = sample_lines(n, 24, rng), sample_lines(n, 24, rng)
+        R, Ra, C, Ca = sampled_apply(Ax, Ay, case.sc["c"], case.sc["sigma"], *case.coef_new, X,
+                                     rows, cols)
+        u = 2 * U16[precision] + n * 2.0 ** -24 + 2.0 ** -22
+        for got, ref, ab in [(yh[rows], R, Ra), (yh[:, cols], C, Ca)]:
+            err = np.abs(got - ref)
+            assert np.all(err <= u * ab + 1e-30), float(np.max(err / (u * ab + 1e-300)))
+            rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert rel > 1e-6 * (U16[precision] / 2.0 ** -11), rel  # 16-bit operands used
     finally:
         fde.fde_destroy(h)
 
