@@ -215,4 +215,39 @@ cudaError_t launch_sumsq(const double* x, size_t N, double* part, int nb, cudaSt
 
 int krylov_blocks();
 
+// ---- Arnoldi state on the device (FGMRES, Sec. 5): the rotated Hessenberg
+// matrix R ((m + 1) x m, column j at R[j (m + 1) ..]), the Givens rotations,
+// the rotated right-hand side g, and the status the host reads after a step
+struct ArnoldiStatus {
+  double gabs;      // |g_{j+1}|: the FGMRES residual estimate after the step
+  double hnext;     // ||w|| before normalisation (0: exact breakdown)
+  double inv_norm;  // 1 / hnext (scales w into the next basis vector)
+  int nonfinite;    // a Hessenberg entry was NaN or Inf
+  int pad;
+};
+struct ArnoldiState {
+  static constexpr int kMaxM = 64;
+  int m;
+  double *R, *cs, *sn, *g;
+  ArnoldiStatus* status;
+};
+// one Arnoldi step j (k = j + 1 basis vectors V_0 .. V_j, w = the new vector):
+// CGS2 in three fused passes over V, the Givens update of column j in the
+// last block of the third pass, then w /= ||w||.  ldv and N even (the basis is
+// zero-padded), k <= 32; part: cgs_blocks() * 32 doubles; tickets: 3 counters
+// that start at zero (each pass resets its own).
+cudaError_t launch_cgs2(const double* V, size_t ldv, int k, double* w, size_t N, double* part,
+                        unsigned* tickets, double* h, double* h2, const ArnoldiState& st, int j,
+                        cudaStream_t s);
+// k > 32: the same step from separate passes (dots, reduce, axpy); the Givens
+// update and the scaling as above
+cudaError_t launch_arnoldi_column(const ArnoldiState& st, int j, const double* h,
+                                  const double* h2, const double* nrm2, cudaStream_t s);
+cudaError_t launch_scale_by(double* w, size_t N, const ArnoldiStatus* status, cudaStream_t s);
+// g = (beta, 0, ...), beta read from device memory; status.gabs = beta
+cudaError_t launch_arnoldi_start(const ArnoldiState& st, const double* beta_dev, cudaStream_t s);
+// y = R^{-1} g for the first k columns
+cudaError_t launch_arnoldi_lsq(const ArnoldiState& st, int k, double* y, cudaStream_t s);
+int cgs_blocks();
+
 }  // namespace fde

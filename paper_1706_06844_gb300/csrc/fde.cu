@@ -94,12 +94,20 @@ struct fde_handle {
 
   std::unique_ptr<MGBase> mg;
 
-  // Krylov workspace
+  // Krylov workspace: basis V (restart + 1 columns) and Z (restart columns)
+  // at a column pitch ldv, a multiple of 64 doubles with zero padding, so the
+  // fused Gram-Schmidt passes read whole double2 pairs
   double *V = nullptr, *Z = nullptr, *part = nullptr, *hdev = nullptr, *h2dev = nullptr;
   double *ydev = nullptr, *tmp = nullptr, *bwork = nullptr, *hu = nullptr, *hv = nullptr,
          *hx_out = nullptr, *u_last = nullptr;
+  size_t ldv = 0;
   int nb = 0;
   int m = 0;
+  // Arnoldi state on the device (rotated Hessenberg matrix, rotations, g)
+  ArnoldiState ast{};
+  double* cgs_part = nullptr;
+  unsigned* tickets = nullptr;
+  ArnoldiStatus* status_host = nullptr;  // pinned: the status read after each step
 
   // profiling
   bool prof = false;
@@ -1086,80 +1094,65 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
     // V_0 = b / ||b||
     LCHK(launch_scale_inv(N, b, h->hdev, h->V, h->st));
   }
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), col(m + 2), y(m);
   const double tol = p.rtol * bnorm;
+  const size_t ldv = h->ldv;
+  const size_t Ne = (N + 1) / 2 * 2;  // even length covered by the zero padding
+  const double* beta_dev = x0 ? h->h2dev : h->hdev;
   int status = FDE_ERR_NOT_CONVERGED;
   while (st.iterations < p.maxit) {
     st.restarts++;
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
+    // g = (beta, 0, ...) on the device
+    LCHK(launch_arnoldi_start(h->ast, beta_dev, h->st));
+    double gprev = beta;  // residual estimate before the step (|g_j|)
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      double* Vj = h->V + (size_t)j * N;
-      double* Zj = h->Z + (size_t)j * N;
-      double* w = h->V + (size_t)(j + 1) * N;
+      double* Vj = h->V + (size_t)j * ldv;
+      double* Zj = h->Z + (size_t)j * ldv;
+      double* w = h->V + (size_t)(j + 1) * ldv;
       RCHK(precond(h, Vj, Zj));
-      // relaxed matvec once the residual estimate |g_j| is near the target
-      if (p.relax && std::fabs(g[j]) <= FDE_RELAX_FACTOR * tol) {
+      // relaxed matvec once the residual estimate is near the target
+      if (p.relax && gprev <= FDE_RELAX_FACTOR * tol) {
         RCHK(outer_apply32(h, Zj, w));
         st.relaxed++;
       } else {
         RCHK(outer_apply(h, Zj, w, false));
       }
       NvtxRange arnoldi("cgs2");
-      // classical Gram-Schmidt, twice (CGS2); for 9 <= j + 1 <= 16 the first
-      // subtraction and the second projection share one pass over V (measured
-      // faster there; outside that range the two separate passes are)
       int pi = h->pbeg(FDE_KCLASS_KRYLOV);
-      LCHK(launch_dots(h->V, N, j + 1, w, N, h->part, h->nb, h->st));
-      LCHK(launch_reduce(h->part, j + 1, h->nb, h->hdev, 0, h->st));
-      if (j + 1 >= 9 && j + 1 <= 16) {
-        LCHK(launch_axpy_dots(h->V, N, j + 1, h->hdev, w, N, h->part, h->nb, 2, h->st));
+      if (j + 1 <= 32) {
+        // three fused passes over V, Givens update in the last block, w /= ||w||
+        LCHK(launch_cgs2(h->V, ldv, j + 1, w, Ne, h->cgs_part, h->tickets, h->hdev, h->h2dev,
+                         h->ast, j, h->st));
+        h->launches += 3;
       } else {
-        LCHK(launch_axpy_dots(h->V, N, j + 1, h->hdev, w, N, h->part, h->nb, 0, h->st));
-        LCHK(launch_dots(h->V, N, j + 1, w, N, h->part, h->nb, h->st));
+        // longer bases: separate dot and update passes, then the same column update
+        LCHK(launch_dots(h->V, ldv, j + 1, w, N, h->part, h->nb, h->st));
+        LCHK(launch_reduce(h->part, j + 1, h->nb, h->hdev, 0, h->st));
+        LCHK(launch_axpy_dots(h->V, ldv, j + 1, h->hdev, w, N, h->part, h->nb, 0, h->st));
+        LCHK(launch_dots(h->V, ldv, j + 1, w, N, h->part, h->nb, h->st));
+        LCHK(launch_reduce(h->part, j + 1, h->nb, h->h2dev, 0, h->st));
+        LCHK(launch_axpy_dots(h->V, ldv, j + 1, h->h2dev, w, N, h->part, h->nb, 1, h->st));
+        LCHK(launch_reduce(h->part, 1, h->nb, h->ydev, 0, h->st));
+        LCHK(launch_arnoldi_column(h->ast, j, h->hdev, h->h2dev, h->ydev, h->st));
+        LCHK(launch_scale_by(w, Ne, h->ast.status, h->st));
       }
-      LCHK(launch_reduce(h->part, j + 1, h->nb, h->h2dev, 0, h->st));
-      LCHK(launch_reduce(h->part, j + 1, h->nb, h->hdev, 1, h->st));
-      LCHK(launch_axpy_dots(h->V, N, j + 1, h->h2dev, w, N, h->part, h->nb, 1, h->st));
-      LCHK(launch_reduce(h->part, 1, h->nb, h->hdev + j + 1, 2, h->st));
-      LCHK(launch_scale_inv(N, w, h->hdev + j + 1, w, h->st));
       h->pend(pi);
-      CCHK(cudaMemcpyAsync(col.data(), h->hdev, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost,
-                           h->st));
+      CCHK(cudaMemcpyAsync(h->status_host, h->ast.status, sizeof(ArnoldiStatus),
+                           cudaMemcpyDeviceToHost, h->st));
       CCHK(cudaStreamSynchronize(h->st));
-      for (int i = 0; i <= j + 1; ++i)
-        if (!std::isfinite(col[i]))
-          return h->fail(FDE_ERR_NONFINITE, "non-finite Hessenberg entry at iteration %d",
-                         st.iterations + 1);
-      // previous rotations, new rotation (Givens)
-      for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-        col[i] = t;
-      }
-      const double rho = std::hypot(col[j], col[j + 1]);
-      const double hnext = col[j + 1];
-      cs[j] = col[j] / rho;
-      sn[j] = col[j + 1] / rho;
-      col[j] = rho;
-      col[j + 1] = 0.0;
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = col[i];
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
+      const ArnoldiStatus as = *h->status_host;
+      if (as.nonfinite)
+        return h->fail(FDE_ERR_NONFINITE, "non-finite Hessenberg entry at iteration %d",
+                       st.iterations + 1);
       st.iterations++;
       k = j + 1;
-      if (std::fabs(g[j + 1]) <= tol || st.iterations >= p.maxit || hnext == 0.0) break;
+      gprev = as.gabs;
+      if (as.gabs <= tol || st.iterations >= p.maxit || as.hnext == 0.0) break;
     }
-    // y = R^{-1} g, x += Z y
-    for (int i = k - 1; i >= 0; --i) {
-      double s = g[i];
-      for (int l = i + 1; l < k; ++l) s -= H[(size_t)i * m + l] * y[l];
-      y[i] = s / H[(size_t)i * m + i];
-    }
-    CCHK(cudaMemcpyAsync(h->ydev, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    // y = R^{-1} g, x += Z y (on the device)
     int pi = h->pbeg(FDE_KCLASS_KRYLOV);
-    LCHK(launch_update(h->Z, N, k, h->ydev, x, N, h->st));
+    LCHK(launch_arnoldi_lsq(h->ast, k, h->ydev, h->st));
+    LCHK(launch_update(h->Z, ldv, k, h->ydev, x, N, h->st));
     h->pend(pi);
     // true residual in FP64
     RCHK(outer_apply(h, x, h->tmp, false));
@@ -1174,6 +1167,7 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
     }
     if (st.iterations >= p.maxit) break;
     LCHK(launch_scale_inv(N, h->tmp, h->h2dev, h->V, h->st));
+    beta_dev = h->h2dev;
   }
   if (st_out) *st_out = st;
   if (status == FDE_ERR_NOT_CONVERGED)
@@ -1341,13 +1335,32 @@ int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
                          &h->hu, &h->hv, &h->hx_out, &h->u_last, &h->epNsT, &h->emNsT,
                          &h->epOsT, &h->emOsT, &h->xT, &h->yT};
     for (double** f : fields) RCHK(h->alloc(f, N));
-    RCHK(h->alloc(&h->V, N * (size_t)(p.restart + 1)));
-    RCHK(h->alloc(&h->Z, N * (size_t)p.restart));
+    h->ldv = (N + 63) / 64 * 64;
+    RCHK(h->alloc(&h->V, h->ldv * (size_t)(p.restart + 1)));
+    RCHK(h->alloc(&h->Z, h->ldv * (size_t)p.restart));
+    // the padding between columns must read as zero in the Gram-Schmidt passes
+    CCHK(cudaMemsetAsync(h->V, 0, h->ldv * (size_t)(p.restart + 1) * sizeof(double), h->st));
+    CCHK(cudaMemsetAsync(h->Z, 0, h->ldv * (size_t)p.restart * sizeof(double), h->st));
     h->nb = krylov_blocks();
     RCHK(h->alloc(&h->part, (size_t)h->nb * (p.restart + 2)));
     RCHK(h->alloc(&h->hdev, p.restart + 4));
     RCHK(h->alloc(&h->h2dev, p.restart + 4));
     RCHK(h->alloc(&h->ydev, p.restart + 4));
+    RCHK(h->alloc(&h->cgs_part, (size_t)cgs_blocks() * 32 + 8));
+    RCHK(h->alloc(&h->tickets, 4));
+    CCHK(cudaMemsetAsync(h->tickets, 0, 4 * sizeof(unsigned), h->st));
+    {
+      const int mm = p.restart;
+      double* a = nullptr;
+      RCHK(h->alloc(&a, (size_t)(mm + 1) * mm + 3 * (size_t)mm + 2));
+      h->ast.m = mm;
+      h->ast.R = a;
+      h->ast.cs = a + (size_t)(mm + 1) * mm;
+      h->ast.sn = h->ast.cs + mm;
+      h->ast.g = h->ast.sn + mm;
+      RCHK(h->alloc(&h->ast.status, 1));
+      CCHK(cudaMallocHost(&h->status_host, sizeof(ArnoldiStatus)));
+    }
     if (p.precond == FDE_PRECOND_P2) {
       if (p.precision == FDE_PREC_FP64) {
         auto* mg = new StencilMG<double>();
@@ -1394,6 +1407,7 @@ void fde_destroy(fde_handle* h) {
     cudaEventDestroy(pe.b);
   }
   for (auto e : h->pool) cudaEventDestroy(e);
+  if (h->status_host) cudaFreeHost(h->status_host);
   delete h;
 }
 

@@ -217,4 +217,319 @@ cudaError_t launch_sumsq(const double* x, size_t N, double* part, int nb, cudaSt
   return cudaGetLastError();
 }
 
+// ============================================================================
+// Fused classical Gram-Schmidt with re-orthogonalisation (CGS2) for one
+// Arnoldi step of FGMRES (Sec. 5), three passes over the basis:
+//   project            h  = V^T w
+//   subtract_project   w -= V h,  h2 = V^T w          (one read of V: the
+//                      values of V a thread subtracts stay in its registers
+//                      for the second projection)
+//   subtract_norm      w -= V h2, ||w||, and in the last block the Hessenberg
+//                      column h + h2 | ||w||, the Givens rotations and the
+//                      residual estimate |g_{j+1}|
+// then w is scaled by 1/||w||.  Each pass reduces its per-block partial sums
+// in the block that finishes last (a ticket counter), in a fixed block order,
+// so results are the same from run to run and no separate reduction launch is
+// needed.  Vectors are the columns of the padded basis (ldv a multiple of 64
+// doubles, zero padding) and are read as double2.
+
+namespace {
+
+constexpr int CT = 256;  // threads per block of the fused passes
+
+// block-wide sum of acc[0..cnt) into red[g] (thread 0 reads it back after the barrier)
+template <int KMAX>
+__device__ __forceinline__ void block_reduce_vec(const double* acc, int cnt, double* sred) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < KMAX; ++g) {
+    if (g < cnt) {
+      const double v = warp_sum(acc[g]);
+      if (lane == 0) sred[g * (CT / 32) + wid] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// write this block's partial sums, take a ticket; true in the block that
+// finishes last, which then sums part[i * nb + b] over b = 0 .. nb - 1 in order
+__device__ __forceinline__ bool publish_partials(const double* sred, int cnt, double* part, int nb,
+                                                 unsigned* ticket) {
+  __shared__ unsigned last;
+  if ((int)threadIdx.x < cnt) {
+    double t = 0.0;
+    for (int w = 0; w < CT / 32; ++w) t += sred[threadIdx.x * (CT / 32) + w];
+    part[(size_t)threadIdx.x * nb + blockIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == (unsigned)(nb - 1)) ? 1u : 0u;
+  __syncthreads();
+  if (last) __threadfence();
+  return last != 0;
+}
+
+// the last block: out[i] = sum_b part[i * nb + b] (one warp per sum, lanes
+// strided over b, then a fixed-order warp reduction)
+__device__ __forceinline__ void final_sums(const double* part, int cnt, int nb, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = wid; i < cnt; i += CT / 32) {
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += ((volatile const double*)part)[(size_t)i * nb + b];
+    s = warp_sum(s);
+    if (lane == 0) out[i] = s;
+  }
+}
+
+__device__ __forceinline__ double2 ld2(const double* p, size_t q) {
+  return reinterpret_cast<const double2*>(p)[q];
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(CT) cgs_project_kernel(const double* __restrict__ V, size_t ldv,
+                                                         int k, const double* __restrict__ w,
+                                                         size_t n2, double* part, int nb,
+                                                         unsigned* ticket, double* h) {
+  __shared__ double sred[KMAX * (CT / 32)];
+  double acc[KMAX];
+#pragma unroll
+  for (int g = 0; g < KMAX; ++g) acc[g] = 0.0;
+  for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n2; q += (size_t)nb * CT) {
+    const double2 wv = ld2(w, q);
+#pragma unroll
+    for (int g = 0; g < KMAX; ++g)
+      if (g < k) {
+        const double2 v = ld2(V + (size_t)g * ldv, q);
+        acc[g] = fma(v.x, wv.x, fma(v.y, wv.y, acc[g]));
+      }
+  }
+  block_reduce_vec<KMAX>(acc, k, sred);
+  if (publish_partials(sred, k, part, nb, ticket)) {
+    final_sums(part, k, nb, h);
+    if (threadIdx.x == 0) *ticket = 0u;
+  }
+}
+
+// k in 17 .. 32: the same pass over scalar elements, so the KMAX values a
+// thread keeps for the second projection fit its registers
+template <int KMAX>
+__global__ void __launch_bounds__(CT) cgs_subtract_project1_kernel(
+    const double* __restrict__ V, size_t ldv, int k, const double* __restrict__ h, double* w,
+    size_t n, double* part, int nb, unsigned* ticket, double* h2) {
+  __shared__ double sred[KMAX * (CT / 32)];
+  __shared__ double hs[KMAX];
+  if ((int)threadIdx.x < KMAX) hs[threadIdx.x] = (int)threadIdx.x < k ? h[threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[KMAX];
+#pragma unroll
+  for (int g = 0; g < KMAX; ++g) acc[g] = 0.0;
+  for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n; q += (size_t)nb * CT) {
+    double v[KMAX];
+#pragma unroll
+    for (int g = 0; g < KMAX; ++g) v[g] = g < k ? V[(size_t)g * ldv + q] : 0.0;
+    double wv = w[q];
+#pragma unroll
+    for (int g = 0; g < KMAX; ++g) wv = fma(-hs[g], v[g], wv);
+    w[q] = wv;
+#pragma unroll
+    for (int g = 0; g < KMAX; ++g) acc[g] = fma(v[g], wv, acc[g]);
+  }
+  block_reduce_vec<KMAX>(acc, k, sred);
+  if (publish_partials(sred, k, part, nb, ticket)) {
+    final_sums(part, k, nb, h2);
+    if (threadIdx.x == 0) *ticket = 0u;
+  }
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(CT) cgs_subtract_project_kernel(
+    const double* __restrict__ V, size_t ldv, int k, const double* __restrict__ h, double* w,
+    size_t n2, double* part, int nb, unsigned* ticket, double* h2) {
+  __shared__ double sred[KMAX * (CT / 32)];
+  __shared__ double hs[KMAX];
+  if ((int)threadIdx.x < KMAX) hs[threadIdx.x] = (int)threadIdx.x < k ? h[threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[KMAX];
+#pragma unroll
+  for (int g = 0; g < KMAX; ++g) acc[g] = 0.0;
+  double2* w2 = reinterpret_cast<double2*>(w);
+  for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n2; q += (size_t)nb * CT) {
+    double2 v[KMAX];
+#pragma unroll
+    for (int g = 0; g < KMAX; ++g)
+      v[g] = g < k ? ld2(V + (size_t)g * ldv, q) : make_double2(0.0, 0.0);
+    double2 wv = w2[q];
+#pragma unroll
+    for (int g = 0; g < KMAX; ++g) {
+      wv.x = fma(-hs[g], v[g].x, wv.x);
+      wv.y = fma(-hs[g], v[g].y, wv.y);
+    }
+    w2[q] = wv;
+#pragma unroll
+    for (int g = 0; g < KMAX; ++g) acc[g] = fma(v[g].x, wv.x, fma(v[g].y, wv.y, acc[g]));
+  }
+  block_reduce_vec<KMAX>(acc, k, sred);
+  if (publish_partials(sred, k, part, nb, ticket)) {
+    final_sums(part, k, nb, h2);
+    if (threadIdx.x == 0) *ticket = 0u;
+  }
+}
+
+// Hessenberg column of Arnoldi step j (h + h2 above the diagonal, ||w||
+// below), the previous rotations applied to it, the new rotation, the rotated
+// right-hand side g and the status (one thread)
+__device__ void arnoldi_column(const ArnoldiState& st, int j, const double* h, const double* h2,
+                               double nrm2) {
+  const int m = st.m;
+  double col[ArnoldiState::kMaxM + 1];
+  int bad = 0;
+  for (int i = 0; i <= j; ++i) {
+    col[i] = h[i] + h2[i];
+    if (!isfinite(col[i])) bad = 1;
+  }
+  const double hnext = sqrt(nrm2);
+  col[j + 1] = hnext;
+  if (!isfinite(hnext)) bad = 1;
+  for (int i = 0; i < j; ++i) {
+    const double t = st.cs[i] * col[i] + st.sn[i] * col[i + 1];
+    col[i + 1] = -st.sn[i] * col[i] + st.cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double rho = hypot(col[j], col[j + 1]);
+  st.cs[j] = col[j] / rho;
+  st.sn[j] = col[j + 1] / rho;
+  col[j] = rho;
+  for (int i = 0; i <= j; ++i) st.R[(size_t)j * (m + 1) + i] = col[i];
+  const double gj = st.g[j];
+  st.g[j + 1] = -st.sn[j] * gj;
+  st.g[j] = st.cs[j] * gj;
+  st.status->gabs = fabs(st.g[j + 1]);
+  st.status->hnext = hnext;
+  st.status->inv_norm = 1.0 / hnext;
+  st.status->nonfinite = bad;
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(CT) cgs_subtract_norm_kernel(
+    const double* __restrict__ V, size_t ldv, int k, const double* __restrict__ h,
+    const double* __restrict__ h2, double* w, size_t n2, double* part, int nb, unsigned* ticket,
+    ArnoldiState st, int j) {
+  __shared__ double sred[CT / 32];
+  __shared__ double hs[KMAX];
+  __shared__ double nrm2;
+  if ((int)threadIdx.x < KMAX) hs[threadIdx.x] = (int)threadIdx.x < k ? h2[threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[1] = {0.0};
+  double2* w2 = reinterpret_cast<double2*>(w);
+  for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n2; q += (size_t)nb * CT) {
+    double2 wv = w2[q];
+#pragma unroll
+    for (int g = 0; g < KMAX; ++g)
+      if (g < k) {
+        const double2 v = ld2(V + (size_t)g * ldv, q);
+        wv.x = fma(-hs[g], v.x, wv.x);
+        wv.y = fma(-hs[g], v.y, wv.y);
+      }
+    w2[q] = wv;
+    acc[0] = fma(wv.x, wv.x, fma(wv.y, wv.y, acc[0]));
+  }
+  block_reduce_vec<1>(acc, 1, sred);
+  if (publish_partials(sred, 1, part, nb, ticket)) {
+    final_sums(part, 1, nb, &nrm2);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *ticket = 0u;
+      arnoldi_column(st, j, h, h2, nrm2);
+    }
+  }
+}
+
+__global__ void arnoldi_column_kernel(ArnoldiState st, int j, const double* h, const double* h2,
+                                      const double* nrm2) {
+  if (threadIdx.x == 0) arnoldi_column(st, j, h, h2, *nrm2);
+}
+
+__global__ void scale_by_kernel(double* w, size_t n2, const ArnoldiStatus* s) {
+  const double inv = s->inv_norm;
+  double2* w2 = reinterpret_cast<double2*>(w);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n2;
+       q += (size_t)gridDim.x * blockDim.x) {
+    double2 v = w2[q];
+    v.x *= inv;
+    v.y *= inv;
+    w2[q] = v;
+  }
+}
+
+// g = (beta, 0, ..., 0) with beta = *beta_dev
+__global__ void arnoldi_start_kernel(ArnoldiState st, const double* beta_dev) {
+  for (int i = threadIdx.x; i <= st.m; i += blockDim.x) st.g[i] = i == 0 ? *beta_dev : 0.0;
+  if (threadIdx.x == 0) st.status->gabs = *beta_dev;
+}
+
+// y = R^{-1} g over the first k columns (back substitution, one thread)
+__global__ void arnoldi_lsq_kernel(ArnoldiState st, int k, double* y) {
+  if (threadIdx.x != 0) return;
+  const int m = st.m;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = st.g[i];
+    for (int l = i + 1; l < k; ++l) s -= st.R[(size_t)l * (m + 1) + i] * y[l];
+    y[i] = s / st.R[(size_t)i * (m + 1) + i];
+  }
+}
+
+}  // namespace
+
+int cgs_blocks() { return 152; }
+
+cudaError_t launch_cgs2(const double* V, size_t ldv, int k, double* w, size_t N, double* part,
+                        unsigned* tickets, double* h, double* h2, const ArnoldiState& st, int j,
+                        cudaStream_t s) {
+  if (k < 1 || k > ArnoldiState::kMaxM || (ldv & 1) || (N & 1)) return cudaErrorInvalidValue;
+  const size_t n2 = N / 2;
+  const int nb = cgs_blocks();
+#define CGS_LAUNCH(KM, SUBPROJ)                                                           \
+  cgs_project_kernel<KM><<<nb, CT, 0, s>>>(V, ldv, k, w, n2, part, nb, tickets, h);      \
+  SUBPROJ;                                                                               \
+  cgs_subtract_norm_kernel<KM><<<nb, CT, 0, s>>>(V, ldv, k, h, h2, w, n2, part, nb,      \
+                                                 tickets + 2, st, j);
+  if (k <= 8) {
+    CGS_LAUNCH(8, (cgs_subtract_project_kernel<8><<<nb, CT, 0, s>>>(V, ldv, k, h, w, n2, part, nb,
+                                                                   tickets + 1, h2)))
+  } else if (k <= 16) {
+    CGS_LAUNCH(16, (cgs_subtract_project_kernel<16><<<nb, CT, 0, s>>>(V, ldv, k, h, w, n2, part,
+                                                                     nb, tickets + 1, h2)))
+  } else if (k <= 32) {
+    CGS_LAUNCH(32, (cgs_subtract_project1_kernel<32><<<nb, CT, 0, s>>>(V, ldv, k, h, w, N, part,
+                                                                      nb, tickets + 1, h2)))
+  } else {
+    return cudaErrorInvalidValue;
+  }
+#undef CGS_LAUNCH
+  scale_by_kernel<<<152 * 4, 256, 0, s>>>(w, n2, st.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arnoldi_column(const ArnoldiState& st, int j, const double* h,
+                                  const double* h2, const double* nrm2, cudaStream_t s) {
+  arnoldi_column_kernel<<<1, 32, 0, s>>>(st, j, h, h2, nrm2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by(double* w, size_t N, const ArnoldiStatus* status, cudaStream_t s) {
+  if (N & 1) return cudaErrorInvalidValue;
+  scale_by_kernel<<<152 * 4, 256, 0, s>>>(w, N / 2, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arnoldi_start(const ArnoldiState& st, const double* beta_dev, cudaStream_t s) {
+  arnoldi_start_kernel<<<1, 64, 0, s>>>(st, beta_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arnoldi_lsq(const ArnoldiState& st, int k, double* y, cudaStream_t s) {
+  arnoldi_lsq_kernel<<<1, 32, 0, s>>>(st, k, y);
+  return cudaGetLastError();
+}
+
 }  // namespace fde

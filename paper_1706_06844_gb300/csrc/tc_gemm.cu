@@ -51,13 +51,20 @@ constexpr int NSYN = 8;            // synthesis / epilogue warps
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int GEN_OFF = 320;           // zero padding in front of the generator copy
 constexpr int GEN_PAD = 1024;          // total padding elements
+// A job's Toeplitz tile reads generator entries base0 - 255 .. base0 + 68 of
+// one copy (forward or reversed); the producer streams the 16-byte aligned
+// window [ws, ws + WIN), ws = (base0 - 256) rounded down to 8 entries, into
+// the stage's window buffer with one bulk copy per term.
+constexpr int WIN = 336;               // entries (16-bit) per window
+constexpr int WIN_BYTES = WIN * 2;     // 672: a multiple of 16
 
 template <int NT>
 struct Cfg {
   static constexpr int STAGES = NT == 1 ? 3 : 2;
   static constexpr int STAGE_BYTES = NT * (A_BYTES + B_BYTES);  // 1 KB multiple
-  // + 256 B barriers + the generator copies (gen_bytes(n) per term, after the barriers)
-  static constexpr size_t FIXED = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+  // + 1 KB alignment slack + 256 B barriers + one generator window per stage and term
+  static constexpr size_t FIXED =
+      (size_t)STAGES * STAGE_BYTES + 1024 + 256 + (size_t)STAGES * NT * WIN_BYTES;
 };
 // epilogue staging (DIR 0: transposed accumulators + operand batches; DIR 1:
 // operand blocks) must fit in the pipeline stages it reuses
@@ -130,6 +137,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
       "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16), completing `bytes` of the transaction count of mbarrier `bar`
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -216,6 +233,13 @@ struct JobIter {
   }
 };
 
+// first entry of the generator copy (forward | reversed, 2 glen entries) that
+// row 0, column 0 of job (acc, delta) reads, and its 16-byte aligned window
+__device__ __forceinline__ int job_base(int acc, int delta, int nn, int glen) {
+  return acc == 0 ? glen + (nn + GEN_OFF) - delta : GEN_OFF - delta;
+}
+__device__ __forceinline__ int job_window(int base0) { return (base0 - 256) & ~7; }
+
 struct KParams {
   // generator t as 16-bit copies, each [forward | reversed] of gen_len(n) entries:
   // forward f[e] = t[e - GEN_OFF], reversed r[e] = t[(n + GEN_OFF) - e], zero outside [-1, n-1]
@@ -250,22 +274,17 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
   // barrier, so the two products that need only the high term can start
   // while the low term is still being synthesised
   uint64_t* fullL = bars + 3 * C::STAGES + 1;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 4 * C::STAGES + 1);
+  // generator windows of a stage landed (bulk copies issued by the producer)
+  uint64_t* fullW = bars + 4 * C::STAGES + 1;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 5 * C::STAGES + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  // generator copies: term t at gsm + t * 2 * glen (16-bit units), forward then reversed
-  uint16_t* gsm = reinterpret_cast<uint16_t*>(base + C::STAGES * C::STAGE_BYTES + 256);
+  // generator window of stage s, term t (WIN 16-bit entries)
+  unsigned char* wins = base + C::STAGES * C::STAGE_BYTES + 256;
+  auto win = [&](int s, int t) { return wins + (s * NT + t) * WIN_BYTES; };
   auto tileA = [&](int s, int t) { return base + s * C::STAGE_BYTES + t * A_BYTES; };
   auto tileB = [&](int s, int t) {
     return base + s * C::STAGE_BYTES + NT * A_BYTES + t * B_BYTES;
   };
-  {
-    const int words = kp.glen;  // 2 * glen 16-bit values = glen 32-bit words per term
-    for (int t = 0; t < NT; ++t) {
-      const uint4* src = reinterpret_cast<const uint4*>(t == 0 ? kp.gen_hi : kp.gen_lo);
-      uint4* dst = reinterpret_cast<uint4*>(gsm + (size_t)t * 2 * kp.glen);
-      for (int e = threadIdx.x; e < words / 4; e += NUM_THREADS) dst[e] = src[e];
-    }
-  }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // output tile: rows m0 .. m0+127 of the M dimension, columns out0 .. out0+255 of N
@@ -277,6 +296,7 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
       mbar_init(smem_u32(&fullA[s]), 1);
       mbar_init(smem_u32(&fullB[s]), NSYN);
       mbar_init(smem_u32(&fullL[s]), NSYN);
+      mbar_init(smem_u32(&fullW[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
     mbar_init(smem_u32(accbar), 1);
@@ -305,6 +325,15 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
         const int s = n % C::STAGES;
         const uint32_t ph = (uint32_t)(n / C::STAGES) & 1u;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag)) break;
+        {
+          // the generator windows this job's Toeplitz tiles are built from
+          const int nn = DIR == 0 ? kp.n1 : kp.n2;
+          const int ws = job_window(job_base(acc, delta, nn, kp.glen));
+          const uint32_t wb = smem_u32(&fullW[s]);
+          mbar_expect_tx(wb, NT * WIN_BYTES);
+          for (int t = 0; t < NT; ++t)
+            bulk_load(smem_u32(win(s, t)), (t == 0 ? kp.gen_hi : kp.gen_lo) + ws, WIN_BYTES, wb);
+        }
         const uint32_t fb = smem_u32(&fullA[s]);
         mbar_expect_tx(fb, NT * A_BYTES);
         for (int t = 0; t < NT; ++t) {
@@ -323,9 +352,12 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
       }
       const uint64_t t0 = global_ns();  // every issued copy lands before the CTA exits
       for (int s = 0; s < C::STAGES; ++s)
-        if (issued_mask & (1u << s))
+        if (issued_mask & (1u << s)) {
           while (!mbar_try(smem_u32(&fullA[s]), (parity_mask >> s) & 1u))
             if (global_ns() - t0 > 1000000000ull) break;
+          while (!mbar_try(smem_u32(&fullW[s]), (parity_mask >> s) & 1u))
+            if (global_ns() - t0 > 1000000000ull) break;
+        }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -412,20 +444,23 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
       while (!*abort_flag && it.next(acc, k0, delta)) {
         const int s = n % C::STAGES;
         const uint32_t ph = (uint32_t)(n / C::STAGES) & 1u;
-        if (!warp_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag)) break;
+        // the window arrives after the MMAs released the stage (the producer
+        // waits for that before issuing it)
+        if (!warp_wait(smem_u32(&fullW[s]), ph, abort_flag)) break;
         // row r, 16-byte chunk c (k = 8c .. 8c+7) of the tile: acc 0 needs
         // t[delta + r - k] = reversed[(n + GEN_OFF) - delta - r + k], acc 1 needs
         // t[-delta + k - r] = forward[GEN_OFF - delta - r + k]: eight consecutive
-        // 16-bit entries starting at e0 = base0 - r + 8c
+        // 16-bit entries starting at e0 = base0 - r + 8c, at e0 - ws in the window
         const int nn = DIR == 0 ? kp.n1 : kp.n2;
-        const int base0 = acc == 0 ? kp.glen + (nn + GEN_OFF) - delta : GEN_OFF - delta;
+        const int gb = job_base(acc, delta, nn, kp.glen);
+        const int base0 = gb - job_window(gb);
         // A thread owns 16-byte chunk column c of an 8-row block r0 .. r0+7: row
         // r0 + u starts at entry e0 - u, e0 = base0 - r0 + 8c, so the eight chunks
         // are shifted views of entries e0 - 7 .. e0 + 7: nine words are loaded once
         // and re-aligned so that word k holds entries (e0 - 7 + 2k, e0 - 6 + 2k);
         // row u then starts 7 - u entries in -- a compile-time word and shift.
         for (int t = 0; t < NT; ++t) {
-          const uint32_t* g32 = reinterpret_cast<const uint32_t*>(gsm + (size_t)t * 2 * kp.glen);
+          const uint32_t* g32 = reinterpret_cast<const uint32_t*>(win(s, t));
           unsigned char* B = tileB(s, t);
 #pragma unroll
           for (int it = 0; it < (BN / 8) * 8 / (NSYN * 32); ++it) {
@@ -718,10 +753,8 @@ int level_create(ToeplitzGemmLevel* L, int n1, int n2, int prec, bool mass) {
   }
   hm.glen_x = gen_len(n1);
   hm.glen_y = gen_len(n2);
-  if (Cfg<1>::FIXED + gen_bytes(n1 > n2 ? n1 : n2) * (split ? 2 : 1) +
-          (split ? (size_t)Cfg<2>::STAGES * Cfg<2>::STAGE_BYTES - Cfg<1>::STAGES * Cfg<1>::STAGE_BYTES
-                 : 0) > 227 * 1024)
-    return 13;  // generator copies do not fit next to the pipeline
+  static_assert(Cfg<1>::FIXED <= 227 * 1024 && Cfg<2>::FIXED <= 227 * 1024,
+                "pipeline and generator windows exceed shared memory");
   if (cudaMalloc(&hm.genx_hi, gen_bytes(n1)) != cudaSuccess) return 1;
   if (cudaMalloc(&hm.geny_hi, gen_bytes(n2)) != cudaSuccess) return 1;
   if (split) {
@@ -781,7 +814,7 @@ static void launch_dir(ToeplitzGemmLevel* L, Maps* m, int dir, const float* M, d
     kp.gen_lo = (const uint16_t*)(NT == 2 ? m->genx_lo : m->genx_hi);
     kp.glen = m->glen_x;
     dim3 gx((L->n1 + BN - 1) / BN, (L->n2 + BM - 1) / BM);
-    toeplitz_gemm_kernel<0, NT><<<gx, NUM_THREADS, Cfg<NT>::FIXED + NT * gen_bytes(L->n1), st>>>(
+    toeplitz_gemm_kernel<0, NT><<<gx, NUM_THREADS, Cfg<NT>::FIXED, st>>>(
         m->ax[0], m->ax[1], kp, make_idesc(false, f16));
   } else {
     // y products (transposed tiles): kx += ep (A_y Y) + em (A_y^T Y)
@@ -790,7 +823,7 @@ static void launch_dir(ToeplitzGemmLevel* L, Maps* m, int dir, const float* M, d
     kp.gen_lo = (const uint16_t*)(NT == 2 ? m->geny_lo : m->geny_hi);
     kp.glen = m->glen_y;
     dim3 gy((L->n2 + BN - 1) / BN, (L->n1 + BM - 1) / BM);
-    toeplitz_gemm_kernel<1, NT><<<gy, NUM_THREADS, Cfg<NT>::FIXED + NT * gen_bytes(L->n2), st>>>(
+    toeplitz_gemm_kernel<1, NT><<<gy, NUM_THREADS, Cfg<NT>::FIXED, st>>>(
         m->ay[0], m->ay[1], kp, make_idesc(true, f16));
   }
 }

@@ -1,15 +1,16 @@
 """n = 4095: FFT length 8192, where two complex buffers of 16-byte values no
 longer fit in shared memory (one-buffer passes with the forward spectrum parked
-in global memory; twiddles of the spectra builds in global memory), and where
-the split-precision tensor-core level falls back to FFT products. The
-operator apply is checked element by element against the oracle, and full
-solves against the oracle's FP64 true residual."""
+in global memory; twiddles of the spectra builds in global memory), and the
+tensor-core products of the two finest levels (n = 4095 and 2047), whose
+generator windows are streamed per job.  The operator apply and the level-0
+tensor-core products are checked element by element against the oracle, and
+full solves against the oracle's FP64 true residual."""
 import numpy as np
 import pytest
 
 from paper_1706_06844_gb300 import inputs
 from paper_1706_06844_gb300 import fde
-from gpu_util import Case, dev, host
+from gpu_util import Case, dev, host, sampled_apply, sample_lines
 
 pytestmark = pytest.mark.gpu
 
@@ -50,6 +51,36 @@ def test_outer_apply_n4095(outer):
         bound = 8 * 13 * OUTER_EPS[outer] * (absr + np.sqrt(np.mean(absr ** 2)))
         err = np.abs(host(y) - ref)
         assert np.all(err <= bound), float(np.max(err / bound))
+    finally:
+        fde.fde_destroy(h)
+
+
+def test_gemm_level0_products_n4095():
+    # BF16x3 tensor-core products of the 4095 x 4095 level (32 x 16 tiles of
+    # 128 x 256, 64 K blocks each) on sampled rows and columns, under the
+    # elementwise error model of the smaller sizes
+    import torch
+    from oracle.operator import toeplitz_A
+    case = Case(_problem(), N, precond=fde.FDE_PRECOND_MG_SG, precision=fde.FDE_PREC_BF16X3,
+                toeplitz_path=fde.FDE_PATH_GEMM)
+    h = case.handle()
+    try:
+        assert fde.fde_level_path(h, 0) == fde.FDE_PATH_GEMM
+        assert fde.fde_level_path(h, 1) == fde.FDE_PATH_GEMM
+        rng = np.random.default_rng(4095)
+        X = rng.standard_normal((N, N))
+        y = torch.empty_like(dev(X))
+        fde.fde_level_apply(h, 0, dev(X), y)
+        torch.cuda.synchronize()
+        yh = host(y)
+        Ax, Ay = toeplitz_A(case.wx, N), toeplitz_A(case.wy, N)
+        rows, cols = sample_lines(N, 16, rng), sample_lines(N, 16, rng)
+        R, Ra, C, Ca = sampled_apply(Ax, Ay, case.sc["c"], case.sc["sigma"], *case.coef_new, X,
+                                     rows, cols)
+        u = 2 * 2.0 ** -16 + N * 2.0 ** -24 + 2.0 ** -22
+        for got, ref, ab in [(yh[rows], R, Ra), (yh[:, cols], C, Ca)]:
+            err = np.abs(got - ref)
+            assert np.all(err <= u * ab + 1e-30), float(np.max(err / (u * ab + 1e-300)))
     finally:
         fde.fde_destroy(h)
 

@@ -170,6 +170,34 @@ def test_solve_matches_oracle(name, mk, precision, outer):
         fde.fde_destroy(h)
 
 
+@pytest.mark.parametrize("restart", [5, 40])
+def test_restarts_and_long_bases(restart):
+    # unpreconditioned FGMRES needs ~100 iterations here: restart 5 runs many
+    # restart cycles (true residual recomputed, V_0 rebuilt, the device-side
+    # Arnoldi state restarted), restart 40 builds bases longer than the 32
+    # vectors of the fused Gram-Schmidt passes (separate passes beyond that);
+    # both meet the oracle's FP64 true residual, and the iteration count stays
+    # within 2 of the oracle's MGS FGMRES with the same restart length
+    import torch
+    from oracle.krylov import fgmres
+    case = Case(inputs.perturbed_power_law(), 31, precond=fde.FDE_PRECOND_NONE, rtol=1e-8,
+                restart=restart, maxit=5000)
+    h = case.handle()
+    try:
+        B = case.oracle_rhs()
+        x = torch.empty_like(dev(B))
+        st = fde.fde_solve(h, dev(B), x)
+        res = np.linalg.norm(B - case.oracle_apply(host(x))) / np.linalg.norm(B)
+        assert st.converged and res <= 1.05e-8, res
+        xo, its, rel, ok = fgmres(case.oracle_apply, B, None, restart, 1e-8, maxit=5000)
+        assert ok and abs(st.iterations - its) <= 2, (st.iterations, its)
+        if restart == 40:
+            assert st.iterations > 33  # the separate-pass branch ran
+        assert st.restarts >= (st.iterations + restart - 1) // restart
+    finally:
+        fde.fde_destroy(h)
+
+
 def test_time_loop_matches_oracle():
     # eight CN steps (Eq. CNWSGD) of the constant-coefficient bubble at n = 63:
     # each step's solution within 1e-8 (relative L2) of the oracle's solve
