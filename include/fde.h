@@ -56,6 +56,10 @@ extern "C" {
 #define FDE_PRECOND_P2         3  /* band preconditioner P_2 (Sec. 4.3): Laplacian (alpha = beta = 2)
                                      five-point operator with the problem's coefficients, one
                                      Galerkin V-cycle (nine-point coarse stencils, R = P^T) */
+#define FDE_PRECOND_MG_EXACT   4  /* V-cycle with the exact Galerkin coarse operators
+                                     A_{l+1} = P^T A_l P as dense matrices formed on the device
+                                     (Sec. 4, TGM step 3; the paper's tilde-P_MGM, Sec. 5.1):
+                                     a validation mode for small grids, n1 n2 <= 4096, FP64 only */
 
 /* arithmetic of the preconditioner (the outer Krylov method is always FP64) */
 #define FDE_PREC_FP64          0  /* V-cycle in FP64 ("plain FP64" solver) */
@@ -147,7 +151,10 @@ void fde_default_params(fde_params* p);
  * the workspace and generates the WSGD weights w_0..w_n (Eq. gk, Eq. w) on
  * the device in FP64.  `stream` is a cudaStream_t (NULL = legacy default).
  * Coefficients must be set (fde_set_coefficients) before any apply or solve.
- * Multigrid needs every level size odd (n, (n-1)/2, ...) down to <= coarsest_n.
+ * Levels coarsen n -> (n - n mod 2)/2 (Sec. 4.1's K matrix: coarse j on fine
+ * 2j for odd n, 2j - 1 for even n) down to <= coarsest_n; the structured-
+ * Galerkin hierarchy (MG_SG) needs every level size odd, the others take
+ * either parity.
  * On error *out is NULL and the status says why. */
 int fde_create(const fde_params* p, void* stream, fde_handle** out);
 

@@ -30,6 +30,30 @@ __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
   return {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
 }
 
+// ---------------------------------------------------------------- grid transfer
+// One axis of the bilinear transfer of Sec. 4.1 (P = T(1 + cos) K): a fine
+// axis of n points coarsens to m = (n - n mod 2) / 2 points, coarse point c
+// sitting on fine point 2c + (n mod 2) (0-based; the down-sampling matrix K
+// puts coarse j on fine 2j for odd n and on fine 2j - 1 for even n, 1-based);
+// P's column c holds 1/2, 1, 1/2 at fine 2c + o - 1, 2c + o, 2c + o + 1,
+// truncated at the ends of the axis (only even n reaches past fine 0).
+__host__ __device__ __forceinline__ int coarse_n(int n) { return (n - (n & 1)) / 2; }
+__host__ __device__ __forceinline__ int coarse_at(int n, int c) { return 2 * c + (n & 1); }
+// coarse parents of fine point i and P's weights: returns their count (1 or 2)
+template <typename T>
+__host__ __device__ __forceinline__ int coarse_parents(int n, int i, int* q, T* w) {
+  const int m = coarse_n(n), r = i - (n & 1);
+  int k = 0;
+  if ((r & 1) == 0 && r >= 0) {  // on a coarse point
+    if (r / 2 < m) { q[k] = r / 2; w[k] = T(1); ++k; }
+    return k;
+  }
+  const int lo = (r - 1) >> 1;  // between coarse lo and lo + 1
+  if (lo >= 0 && lo < m) { q[k] = lo; w[k] = T(0.5); ++k; }
+  if (lo + 1 >= 0 && lo + 1 < m) { q[k] = lo + 1; w[k] = T(0.5); ++k; }
+  return k;
+}
+
 // ---------------------------------------------------------------- launches
 // Every launcher returns the cudaError_t of its launch (cudaGetLastError()).
 
@@ -98,7 +122,7 @@ cudaError_t launch_transpose(const T* in, int rows, int cols, T* out, int add, c
 template <typename T>
 cudaError_t launch_mul(size_t N, const T* W, const T* B, T* Y, cudaStream_t st);
 
-// coarse b_c = rscale * P^T r (bilinear P, odd fine sizes n = 2 nc + 1)
+// coarse b_c = rscale * P^T r (bilinear P of the transfer above, any fine sizes)
 template <typename T>
 cudaError_t launch_restrict(const T* R, int n1, int n2, double rscale, T* BC, cudaStream_t st);
 
@@ -124,17 +148,19 @@ cudaError_t launch_generator_from_weights(const double* w, int n, double scale, 
 // q-coarsening t^c_d = sum_m q_m t_{2d+m}, q = (1/4, 1, 3/2, 1, 1/4)
 cudaError_t launch_coarsen_generator(const double* t, int n, double* tc, int nc,
                                      cudaStream_t st);
-// coarse coefficient injection F_c[jc][ic] = F[2jc+1][2ic+1] (odd sizes)
+// coarse coefficient injection F_c[jc][ic] = F[coarse_at(n2, jc)][coarse_at(n1, ic)]
 template <typename T>
 cudaError_t launch_inject(const T* F, int n1, int n2, T* FC, cudaStream_t st);
 // per-level fields: dp, dm, ep, em (ep, em scaled by sigma), W = omega/diag(K_l)
-// from FP64 fine coefficients at the level's nodes (injection stride `stride`).
+// from FP64 fine coefficients at the level's nodes: level point (j, i) is
+// finest point (stride j + offy, stride i + offx), stride = 2^l, the offsets
+// summing the per-level shifts n_t mod 2 of the transfer: off = sum_t 2^t (n_t & 1).
 template <typename T>
 cudaError_t launch_level_fields(const double* dp, const double* dm, const double* ep,
-                                const double* em, int n1f, int n1, int n2, int stride,
-                                double sigma, double c, double bx0, double by0, const double* tx,
-                                const double* ty, double omega, T* odp, T* odm, T* oep, T* oem,
-                                T* W, cudaStream_t st);
+                                const double* em, int n1f, int n1, int n2, int stride, int offx,
+                                int offy, double sigma, double c, double bx0, double by0,
+                                const double* tx, const double* ty, double omega, T* odp, T* odm,
+                                T* oep, T* oem, T* W, cudaStream_t st);
 // out = a X + b Y + c Z (Z may be null when c == 0), FP64
 cudaError_t launch_lincomb(size_t N, double a, const double* X, double b, const double* Y,
                            double c, const double* Z, double* out, cudaStream_t st);
@@ -193,6 +219,24 @@ cudaError_t launch_add(size_t N, const T* A, const T* B, T* Y, cudaStream_t st);
 cudaError_t launch_stencil_inverse(const double* S, int n1, int n2, double* work, double* inv,
                                    int* info, cudaStream_t st);
 
+// ---- dense levels (exact Galerkin validation mode, N_l x N_l row-major FP64)
+// level 0: M of Eq. (M) from the generators t_d = -w_{d+1} (t[d + 1]) and the
+// unscaled coefficients
+cudaError_t launch_dense_assemble(const double* tx, const double* ty, int n1, int n2, double c,
+                                  double sigma, const double* dp, const double* dm,
+                                  const double* ep, const double* em, double* A, cudaStream_t st);
+// Ac = P^T A P for the fine n1 x n2 grid (AP: N_f x N_c scratch)
+cudaError_t launch_dense_galerkin(const double* A, int n1, int n2, double* AP, double* Ac,
+                                  cudaStream_t st);
+cudaError_t launch_dense_jacobi_weights(const double* A, size_t N, double omega, double* W,
+                                        cudaStream_t st);
+// mode 0: Y = A X; 1: Y = B - A X; 2: Y = X + W (B - A X).  Y must not alias X.
+cudaError_t launch_dense_apply(int mode, const double* A, size_t N, const double* X,
+                               const double* B, const double* W, double* Y, cudaStream_t st);
+// explicit inverse of a dense N x N matrix (N <= 1024; work 2 N^2)
+cudaError_t launch_dense_inverse(const double* K, int N, double* work, double* inv, int* info,
+                                 cudaStream_t st);
+
 // ---- Krylov (FP64)
 // partial dots: part[i * nb + blk] = sum over block chunk of V_i . w  (i < k)
 cudaError_t launch_dots(const double* V, size_t ldv, int k, const double* w, size_t N,
@@ -234,7 +278,8 @@ struct ArnoldiState {
 // one Arnoldi step j (k = j + 1 basis vectors V_0 .. V_j, w = the new vector):
 // CGS2 in three fused passes over V, the Givens update of column j in the
 // last block of the third pass, then w /= ||w||.  ldv and N even (the basis is
-// zero-padded), k <= 32; part: cgs_blocks() * 32 doubles; tickets: 3 counters
+// zero-padded), k <= 32; part: cgs_blocks() * 32 doubles (cgs_blocks() is the
+// largest grid a pass uses: the blocks the GPU holds at once); tickets: 3 counters
 // that start at zero (each pass resets its own).
 cudaError_t launch_cgs2(const double* V, size_t ldv, int k, double* w, size_t N, double* part,
                         unsigned* tickets, double* h, double* h2, const ArnoldiState& st, int j,

@@ -271,6 +271,7 @@ struct MG : MGBase {
     int n1, n2;
     size_t N;
     double bx0 = 1, bx1 = 0, by0 = 1, by1 = 0;  // Galerkin mass tridiagonals
+    int offx = 0, offy = 0;                      // finest index of level point 0 per axis
     double *tx = nullptr, *ty = nullptr;         // Toeplitz generators (FP64)
     int path = FDE_PATH_DIRECT;                  // FFT, DIRECT or GEMM
     bool tune = false;                           // time the candidates at the first setup
@@ -306,16 +307,25 @@ struct MG : MGBase {
       n1s.push_back(m1);
       n2s.push_back(m2);
       if (m1 <= p.coarsest_n || m2 <= p.coarsest_n) break;
-      if (!(m1 & 1) || !(m2 & 1))
+      // the structured Galerkin projection keeps a 1-D factor Toeplitz only
+      // when the fine size is odd (n = 2 n_c + 1); the rediscretised cycle
+      // coarsens either parity (Sec. 4.1's K matrix)
+      if (sg && (!(m1 & 1) || !(m2 & 1)))
         return h->fail(FDE_ERR_UNSUPPORTED,
-                       "multigrid needs odd level sizes down to the coarsest grid (got %d x %d)",
+                       "the structured-Galerkin hierarchy needs odd level sizes down to the "
+                       "coarsest grid (got %d x %d); use MG_REDISC, MG_EXACT or P2",
                        m1, m2);
-      m1 = (m1 - 1) / 2;
-      m2 = (m2 - 1) / 2;
+      m1 = coarse_n(m1);
+      m2 = coarse_n(m2);
     }
     if (lv.back().N > 1024)
       return h->fail(FDE_ERR_UNSUPPORTED, "coarsest grid %d x %d exceeds 1024 unknowns",
                      lv.back().n1, lv.back().n2);
+    // injection offsets of every level (finest point of level point (j, i))
+    for (size_t l = 1; l < lv.size(); ++l) {
+      lv[l].offx = lv[l - 1].offx + ((lv[l - 1].n1 & 1) << (l - 1));
+      lv[l].offy = lv[l - 1].offy + ((lv[l - 1].n2 & 1) << (l - 1));
+    }
     // mass tridiagonals (structured Galerkin: b^{c}_0 = 3/2 b_0 + 2 b_1, b^{c}_1 = b_0/4 + b_1)
     for (size_t l = 1; l < lv.size(); ++l) {
       if (sg) {
@@ -482,8 +492,8 @@ struct MG : MGBase {
       }
       const int stride = 1 << l;
       LCHK(launch_level_fields<T>(h->dpN, h->dmN, h->epN, h->emN, h->n1, L.n1, L.n2, stride,
-                                  h->sigma, h->c, L.bx0, L.by0, L.tx, L.ty, p.omega, L.dp, L.dm,
-                                  L.ep, L.em, L.W, st));
+                                  L.offx, L.offy, h->sigma, h->c, L.bx0, L.by0, L.tx, L.ty,
+                                  p.omega, L.dp, L.dm, L.ep, L.em, L.W, st));
       if ((L.path == FDE_PATH_FFT || (L.tune && (L.cands & (1 << FDE_PATH_FFT)))) &&
           l + 1 < lv.size()) {
         LCHK(launch_transpose<T>(L.ep, L.n2, L.n1, L.epT, 0, st));
@@ -506,8 +516,8 @@ struct MG : MGBase {
     Lv& C = lv.back();
     const int stride = 1 << (lv.size() - 1);
     LCHK(launch_level_fields<double>(h->dpN, h->dmN, h->epN, h->emN, h->n1, C.n1, C.n2, stride,
-                                     h->sigma, h->c, C.bx0, C.by0, C.tx, C.ty, p.omega, cf[0],
-                                     cf[1], cf[2], cf[3], nullptr, st));
+                                     C.offx, C.offy, h->sigma, h->c, C.bx0, C.by0, C.tx, C.ty,
+                                     p.omega, cf[0], cf[1], cf[2], cf[3], nullptr, st));
     LCHK(launch_coarse_inverse(C.tx, C.ty, C.n1, C.n2, C.bx0, C.bx1, C.by0, C.by1, h->c, cf[0],
                                cf[1], cf[2], cf[3], cwork, inv, info, st));
     int hinfo = 0;
@@ -795,12 +805,8 @@ struct StencilMG : MGBase {
       n1s.push_back(m1);
       n2s.push_back(m2);
       if (m1 <= p.coarsest_n || m2 <= p.coarsest_n) break;
-      if (!(m1 & 1) || !(m2 & 1))
-        return h->fail(FDE_ERR_UNSUPPORTED,
-                       "multigrid needs odd level sizes down to the coarsest grid (got %d x %d)",
-                       m1, m2);
-      m1 = (m1 - 1) / 2;
-      m2 = (m2 - 1) / 2;
+      m1 = coarse_n(m1);  // either parity: Sec. 4.1's transfer
+      m2 = coarse_n(m2);
     }
     if (lv.back().N > 1024)
       return h->fail(FDE_ERR_UNSUPPORTED, "coarsest grid %d x %d exceeds 1024 unknowns",
@@ -934,6 +940,166 @@ struct StencilMG : MGBase {
     LCHK(launch_stencil_apply<T>(0, l == 0, L.S, L.n1, L.n2, L.x, nullptr, nullptr, L.kx,
                                  h->st));
     LCHK((launch_convert<T, double>(L.N, L.kx, 1.0, y, h->st)));
+    return FDE_OK;
+  }
+};
+
+// ============================================================================
+// Exact Galerkin hierarchy with explicit matrices (Sec. 4, TGM step 3 at every
+// level; the paper's tilde-P_MGM of Sec. 5.1): level 0 is M of Eq. (M)
+// assembled densely, level l + 1 is P^T A_l P, formed on the device in FP64;
+// damped Jacobi with the true diagonal, R = P^T, dense coarsest inverse.  A
+// validation mode for small variable-coefficient grids (N <= kDenseMaxN),
+// where the structured-Galerkin reading and the exact one differ.
+
+constexpr size_t kDenseMaxN = 4096;
+
+struct DenseMG : MGBase {
+  struct Lv {
+    int n1, n2;
+    size_t N;
+    double *A = nullptr, *W = nullptr, *x = nullptr, *b = nullptr, *kx = nullptr;
+  };
+  std::vector<Lv> lv;
+  double *AP = nullptr, *inv = nullptr, *cwork = nullptr;
+  double *acc_x = nullptr, *acc_b = nullptr;
+  int* info = nullptr;
+
+  int create(fde_handle* h) {
+    const fde_params& p = h->p;
+    if (h->N > kDenseMaxN)
+      return h->fail(FDE_ERR_UNSUPPORTED,
+                     "the exact-Galerkin hierarchy stores dense levels: N = %zu exceeds %zu",
+                     h->N, kDenseMaxN);
+    int m1 = h->n1, m2 = h->n2;
+    for (;;) {
+      Lv L;
+      L.n1 = m1;
+      L.n2 = m2;
+      L.N = (size_t)m1 * m2;
+      lv.push_back(L);
+      n1s.push_back(m1);
+      n2s.push_back(m2);
+      if (m1 <= p.coarsest_n || m2 <= p.coarsest_n) break;
+      m1 = coarse_n(m1);
+      m2 = coarse_n(m2);
+    }
+    if (lv.back().N > 1024)
+      return h->fail(FDE_ERR_UNSUPPORTED, "coarsest grid %d x %d exceeds 1024 unknowns",
+                     lv.back().n1, lv.back().n2);
+    size_t ap = 0;
+    for (size_t l = 0; l < lv.size(); ++l) {
+      Lv& L = lv[l];
+      RCHK(h->alloc(&L.A, L.N * L.N));
+      RCHK(h->alloc(&L.W, L.N));
+      RCHK(h->alloc(&L.x, L.N));
+      RCHK(h->alloc(&L.b, L.N));
+      RCHK(h->alloc(&L.kx, L.N));
+      if (l + 1 < lv.size()) ap = std::max(ap, L.N * lv[l + 1].N);
+    }
+    if (ap) RCHK(h->alloc(&AP, ap));
+    const Lv& C = lv.back();
+    RCHK(h->alloc(&inv, C.N * C.N));
+    RCHK(h->alloc(&cwork, C.N * C.N * 2));
+    RCHK(h->alloc(&info, 4));
+    if (p.cycles > 1) {
+      RCHK(h->alloc(&acc_x, lv[0].N));
+      RCHK(h->alloc(&acc_b, lv[0].N));
+    }
+    return FDE_OK;
+  }
+
+  int setup(fde_handle* h) override {
+    cudaStream_t st = h->st;
+    LCHK(launch_dense_assemble(h->tx0, h->ty0, h->n1, h->n2, h->c, h->sigma, h->dpN, h->dmN,
+                               h->epN, h->emN, lv[0].A, st));
+    for (size_t l = 0; l + 1 < lv.size(); ++l)
+      LCHK(launch_dense_galerkin(lv[l].A, lv[l].n1, lv[l].n2, AP, lv[l + 1].A, st));
+    for (auto& L : lv) LCHK(launch_dense_jacobi_weights(L.A, L.N, h->p.omega, L.W, st));
+    const Lv& C = lv.back();
+    LCHK(launch_dense_inverse(C.A, (int)C.N, cwork, inv, info, st));
+    int hinfo = 0;
+    CCHK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CCHK(cudaStreamSynchronize(st));
+    if (hinfo != 0) return h->fail(FDE_ERR_NONFINITE, "coarsest-grid matrix is singular");
+    return FDE_OK;
+  }
+
+  int apply(fde_handle* h, size_t l, int mode, const double* x, const double* b, double* y) {
+    Lv& L = lv[l];
+    const int pi = h->pbeg(FDE_KCLASS_LEVEL_APPLY);
+    LCHK(launch_dense_apply(mode, L.A, L.N, x, b, L.W, y, h->st));
+    h->pend(pi);
+    return FDE_OK;
+  }
+
+  // V-cycle on level l from x = 0 (ping-pong between x and kx as the P_2
+  // hierarchy does); *out receives the buffer holding the result
+  int cycle(fde_handle* h, size_t l, double** out) {
+    Lv& L = lv[l];
+    const fde_params& p = h->p;
+    cudaStream_t st = h->st;
+    double *x = L.x, *t = L.kx;
+    if (l + 1 == lv.size()) {
+      const int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+      LCHK(launch_coarse_solve<double>(inv, (int)L.N, L.b, x, st));
+      h->pend(pi);
+      *out = x;
+      return FDE_OK;
+    }
+    int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+    if (p.nu_pre >= 1) LCHK(launch_mul<double>(L.N, L.W, L.b, x, st));
+    else CCHK(cudaMemsetAsync(x, 0, L.N * sizeof(double), st));
+    h->pend(pi);
+    for (int s = 1; s < p.nu_pre; ++s) {
+      RCHK(apply(h, l, 2, x, L.b, t));
+      std::swap(x, t);
+    }
+    RCHK(apply(h, l, 1, x, L.b, t));  // r = b - A x
+    pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+    LCHK(launch_restrict<double>(t, L.n1, L.n2, 1.0, lv[l + 1].b, st));  // R = P^T
+    h->pend(pi);
+    double* xc = nullptr;
+    RCHK(cycle(h, l + 1, &xc));
+    pi = h->pbeg(FDE_KCLASS_MG_OTHER);
+    LCHK(launch_prolong_add<double>(xc, L.n1, L.n2, x, st));
+    h->pend(pi);
+    for (int s = 0; s < p.nu_post; ++s) {
+      RCHK(apply(h, l, 2, x, L.b, t));
+      std::swap(x, t);
+    }
+    *out = x;
+    return FDE_OK;
+  }
+
+  double* root_out = nullptr;
+  int cycle_root(fde_handle* h) override { return cycle(h, 0, &root_out); }
+
+  int vcycle(fde_handle* h, const double* r, double* z) override {
+    Lv& L = lv[0];
+    CCHK(cudaMemcpyAsync(L.b, r, L.N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    RCHK(run_cycle(h));
+    const int cycles = (h->p.cycles > 1 && lv.size() > 1) ? h->p.cycles : 1;
+    if (cycles > 1) {
+      // stationary iteration z_{k+1} = z_k + V(r - A_0 z_k): r is kept in acc_b
+      CCHK(cudaMemcpyAsync(acc_b, L.b, L.N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+      for (int k = 1; k < cycles; ++k) {
+        CCHK(cudaMemcpyAsync(acc_x, root_out, L.N * sizeof(double), cudaMemcpyDeviceToDevice,
+                             h->st));
+        RCHK(apply(h, 0, 1, acc_x, acc_b, L.b));
+        RCHK(run_cycle(h));
+        LCHK(launch_add<double>(L.N, acc_x, root_out, root_out, h->st));
+      }
+    }
+    CCHK(cudaMemcpyAsync(z, root_out, L.N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    return FDE_OK;
+  }
+
+  int level_apply(fde_handle* h, int l, const double* x, double* y) override {
+    if (l < 0 || l >= (int)lv.size()) return h->fail(FDE_ERR_ARG, "level %d out of range", l);
+    Lv& L = lv[l];
+    CCHK(cudaMemcpyAsync(L.x, x, L.N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    LCHK(launch_dense_apply(0, L.A, L.N, L.x, nullptr, nullptr, y, h->st));
     return FDE_OK;
   }
 };
@@ -1217,7 +1383,10 @@ static int validate(const fde_params* p, std::string& why) {
   if (!(p->rtol > 0.0) || !(p->rtol < 1.0)) return bad("rtol must be in (0, 1)");
   if (p->restart < 1 || p->restart > 64) return bad("restart must be in [1, 64]");
   if (p->maxit < 1) return bad("maxit must be >= 1");
-  if (p->precond < FDE_PRECOND_NONE || p->precond > FDE_PRECOND_P2) return bad("unknown precond");
+  if (p->precond < FDE_PRECOND_NONE || p->precond > FDE_PRECOND_MG_EXACT)
+    return bad("unknown precond");
+  if (p->precond == FDE_PRECOND_MG_EXACT && p->precision != FDE_PREC_FP64)
+    return bad("the exact-Galerkin validation mode runs in FP64 only");
   if (p->cycles < 0 || p->cycles > 4) return bad("cycles must be in [0, 4]");
   if (p->relax != 0 && p->relax != 1) return bad("relax must be 0 or 1");
   if (p->solver != FDE_SOLVER_FGMRES && p->solver != FDE_SOLVER_MG) return bad("unknown solver");
@@ -1361,7 +1530,11 @@ int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
       RCHK(h->alloc(&h->ast.status, 1));
       CCHK(cudaMallocHost(&h->status_host, sizeof(ArnoldiStatus)));
     }
-    if (p.precond == FDE_PRECOND_P2) {
+    if (p.precond == FDE_PRECOND_MG_EXACT) {
+      auto* mg = new DenseMG();
+      h->mg.reset(mg);
+      RCHK(mg->create(h));
+    } else if (p.precond == FDE_PRECOND_P2) {
       if (p.precision == FDE_PREC_FP64) {
         auto* mg = new StencilMG<double>();
         h->mg.reset(mg);

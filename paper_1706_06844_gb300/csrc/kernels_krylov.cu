@@ -3,6 +3,10 @@
 // basis update w -= V h, norms, and the solution update x += Z y.
 // Reductions are two-pass (per-block partials, then one block sums them in a
 // fixed order), so results are deterministic run to run.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "common.cuh"
 
 namespace fde {
@@ -269,15 +273,26 @@ __device__ __forceinline__ bool publish_partials(const double* sred, int cnt, do
   return last != 0;
 }
 
-// the last block: out[i] = sum_b part[i * nb + b] (one warp per sum, lanes
-// strided over b, then a fixed-order warp reduction)
+// the last block: out[i] = sum_b part[i * nb + b], the whole block on each
+// sum (thread t adds b = t, t + CT, ... with L2 loads that bypass L1, then a
+// fixed-order warp and block reduction), so the result is the same every run
 __device__ __forceinline__ void final_sums(const double* part, int cnt, int nb, double* out) {
+  __shared__ double wsum[CT / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int i = wid; i < cnt; i += CT / 32) {
+  for (int i = 0; i < cnt; ++i) {
+    const double* p = part + (size_t)i * nb;
     double s = 0.0;
-    for (int b = lane; b < nb; b += 32) s += ((volatile const double*)part)[(size_t)i * nb + b];
+#pragma unroll 4
+    for (int b = threadIdx.x; b < nb; b += CT) s += __ldcg(p + b);
     s = warp_sum(s);
-    if (lane == 0) out[i] = s;
+    if (lane == 0) wsum[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < CT / 32; ++w) t += wsum[w];
+      out[i] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -480,28 +495,51 @@ __global__ void arnoldi_lsq_kernel(ArnoldiState st, int k, double* y) {
 
 }  // namespace
 
-int cgs_blocks() { return 152; }
+// blocks of a fused pass: every block the GPU holds at once (occupancy x SMs),
+// at most kMaxCgsBlocks, so the loads in flight saturate HBM whatever k is
+constexpr int kMaxCgsBlocks = 2048;
+int cgs_blocks() { return kMaxCgsBlocks; }
+
+static int resident_blocks(const void* kernel) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({kernel, dev});
+  if (it != cache.end()) return it->second;
+  int per_sm = 1, sms = 152;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, CT, 0);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int nb = (per_sm < 1 ? 1 : per_sm) * sms;
+  if (nb > kMaxCgsBlocks) nb = kMaxCgsBlocks;
+  cache[{kernel, dev}] = nb;
+  return nb;
+}
 
 cudaError_t launch_cgs2(const double* V, size_t ldv, int k, double* w, size_t N, double* part,
                         unsigned* tickets, double* h, double* h2, const ArnoldiState& st, int j,
                         cudaStream_t s) {
   if (k < 1 || k > ArnoldiState::kMaxM || (ldv & 1) || (N & 1)) return cudaErrorInvalidValue;
   const size_t n2 = N / 2;
-  const int nb = cgs_blocks();
-#define CGS_LAUNCH(KM, SUBPROJ)                                                           \
-  cgs_project_kernel<KM><<<nb, CT, 0, s>>>(V, ldv, k, w, n2, part, nb, tickets, h);      \
-  SUBPROJ;                                                                               \
-  cgs_subtract_norm_kernel<KM><<<nb, CT, 0, s>>>(V, ldv, k, h, h2, w, n2, part, nb,      \
-                                                 tickets + 2, st, j);
-  if (k <= 8) {
-    CGS_LAUNCH(8, (cgs_subtract_project_kernel<8><<<nb, CT, 0, s>>>(V, ldv, k, h, w, n2, part, nb,
-                                                                   tickets + 1, h2)))
+#define CGS_LAUNCH(KM, SP, SPN)                                                                \
+  {                                                                                           \
+    const int b1 = resident_blocks((const void*)cgs_project_kernel<KM>);                      \
+    const int b2 = resident_blocks((const void*)SP<KM>);                                      \
+    const int b3 = resident_blocks((const void*)cgs_subtract_norm_kernel<KM>);                \
+    cgs_project_kernel<KM><<<b1, CT, 0, s>>>(V, ldv, k, w, n2, part, b1, tickets, h);         \
+    SP<KM><<<b2, CT, 0, s>>>(V, ldv, k, h, w, SPN, part, b2, tickets + 1, h2);                \
+    cgs_subtract_norm_kernel<KM><<<b3, CT, 0, s>>>(V, ldv, k, h, h2, w, n2, part, b3,         \
+                                                   tickets + 2, st, j);                       \
+  }
+  if (k <= 4) {
+    CGS_LAUNCH(4, cgs_subtract_project_kernel, n2)
+  } else if (k <= 8) {
+    CGS_LAUNCH(8, cgs_subtract_project_kernel, n2)
   } else if (k <= 16) {
-    CGS_LAUNCH(16, (cgs_subtract_project_kernel<16><<<nb, CT, 0, s>>>(V, ldv, k, h, w, n2, part,
-                                                                     nb, tickets + 1, h2)))
+    CGS_LAUNCH(16, cgs_subtract_project_kernel, n2)
   } else if (k <= 32) {
-    CGS_LAUNCH(32, (cgs_subtract_project1_kernel<32><<<nb, CT, 0, s>>>(V, ldv, k, h, w, N, part,
-                                                                      nb, tickets + 1, h2)))
+    CGS_LAUNCH(32, cgs_subtract_project1_kernel, N)
   } else {
     return cudaErrorInvalidValue;
   }

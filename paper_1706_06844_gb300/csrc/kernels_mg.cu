@@ -105,30 +105,35 @@ cudaError_t launch_mul(size_t N, const T* W, const T* B, T* Y, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-// b_c = rscale * (P_y (x) P_x)^T r, P column stencil (1/2, 1, 1/2) centred on fine 2k+1
+// b_c = rscale * (P_y (x) P_x)^T r, P column stencil (1/2, 1, 1/2) centred on
+// fine coarse_at(n, c), truncated at the ends of each axis
 template <typename T>
 __global__ void restrict_kernel(const T* __restrict__ R, int n1, int n2, T rscale,
                                 T* __restrict__ BC) {
-  const int m1 = (n1 - 1) / 2, m2 = (n2 - 1) / 2;
+  const int m1 = coarse_n(n1), m2 = coarse_n(n2);
   const size_t NC = (size_t)m1 * m2;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < NC;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int ic = (int)(idx % m1), jc = (int)(idx / m1);
-    const int i = 2 * ic + 1, j = 2 * jc + 1;
-    const T* r0 = R + (size_t)(j - 1) * n1;
-    const T* r1 = r0 + n1;
-    const T* r2 = r1 + n1;
+    const int i = coarse_at(n1, ic), j = coarse_at(n2, jc);
     const T h = T(0.5);
-    const T s0 = h * r0[i - 1] + r0[i] + h * r0[i + 1];
-    const T s1 = h * r1[i - 1] + r1[i] + h * r1[i + 1];
-    const T s2 = h * r2[i - 1] + r2[i] + h * r2[i + 1];
-    BC[idx] = rscale * (h * s0 + s1 + h * s2);
+    T acc = T(0);
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int jj = j + dj;
+      if (jj < 0 || jj >= n2) continue;
+      const T* r = R + (size_t)jj * n1;
+      T sr = r[i];
+      if (i > 0) sr += h * r[i - 1];
+      if (i + 1 < n1) sr += h * r[i + 1];
+      acc += (dj ? h : T(1)) * sr;
+    }
+    BC[idx] = rscale * acc;
   }
 }
 
 template <typename T>
 cudaError_t launch_restrict(const T* R, int n1, int n2, double rscale, T* BC, cudaStream_t st) {
-  const size_t NC = (size_t)((n1 - 1) / 2) * ((n2 - 1) / 2);
+  const size_t NC = (size_t)coarse_n(n1) * coarse_n(n2);
   restrict_kernel<T><<<grid_for(NC, 256), 256, 0, st>>>(R, n1, n2, T(rscale), BC);
   return cudaGetLastError();
 }
@@ -136,26 +141,18 @@ cudaError_t launch_restrict(const T* R, int n1, int n2, double rscale, T* BC, cu
 // x += (P_y (x) P_x) x_c
 template <typename T>
 __global__ void prolong_add_kernel(const T* __restrict__ XC, int n1, int n2, T* X) {
-  const int m1 = (n1 - 1) / 2, m2 = (n2 - 1) / 2;
+  const int m1 = coarse_n(n1);
   const size_t N = (size_t)n1 * n2;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx % n1), j = (int)(idx / n1);
     int ci[2], cj[2];
     T wi[2], wj[2];
-    int ni, nj;
-    if (i & 1) { ci[0] = (i - 1) / 2; wi[0] = T(1); ni = 1; }
-    else { ci[0] = i / 2 - 1; ci[1] = i / 2; wi[0] = wi[1] = T(0.5); ni = 2; }
-    if (j & 1) { cj[0] = (j - 1) / 2; wj[0] = T(1); nj = 1; }
-    else { cj[0] = j / 2 - 1; cj[1] = j / 2; wj[0] = wj[1] = T(0.5); nj = 2; }
+    const int ni = coarse_parents<T>(n1, i, ci, wi);
+    const int nj = coarse_parents<T>(n2, j, cj, wj);
     T s = T(0);
-    for (int b = 0; b < nj; ++b) {
-      if (cj[b] < 0 || cj[b] >= m2) continue;
-      for (int a = 0; a < ni; ++a) {
-        if (ci[a] < 0 || ci[a] >= m1) continue;
-        s += wj[b] * wi[a] * XC[(size_t)cj[b] * m1 + ci[a]];
-      }
-    }
+    for (int b = 0; b < nj; ++b)
+      for (int a = 0; a < ni; ++a) s += wj[b] * wi[a] * XC[(size_t)cj[b] * m1 + ci[a]];
     X[idx] += s;
   }
 }
@@ -283,30 +280,32 @@ cudaError_t launch_coarsen_generator(const double* t, int n, double* tc, int nc,
 
 template <typename T>
 __global__ void inject_kernel(const T* __restrict__ F, int n1, int n2, T* FC) {
-  const int m1 = (n1 - 1) / 2, m2 = (n2 - 1) / 2;
+  const int m1 = coarse_n(n1), m2 = coarse_n(n2);
   const size_t NC = (size_t)m1 * m2;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < NC;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int ic = (int)(idx % m1), jc = (int)(idx / m1);
-    FC[idx] = F[(size_t)(2 * jc + 1) * n1 + 2 * ic + 1];
+    FC[idx] = F[(size_t)coarse_at(n2, jc) * n1 + coarse_at(n1, ic)];
   }
 }
 
 template <typename T>
 cudaError_t launch_inject(const T* F, int n1, int n2, T* FC, cudaStream_t st) {
-  const size_t NC = (size_t)((n1 - 1) / 2) * ((n2 - 1) / 2);
+  const size_t NC = (size_t)coarse_n(n1) * coarse_n(n2);
   inject_kernel<T><<<grid_for(NC, 256), 256, 0, st>>>(F, n1, n2, FC);
   return cudaGetLastError();
 }
 
 // Level fields by injection from the finest grid: level node (j, i) is fine
-// node ((j+1) s - 1, (i+1) s - 1), s = 2^l.  diag(K_l) = c by0 bx0
+// node (s j + offy, s i + offx), s = 2^l (for odd sizes all the way down,
+// off = s - 1: node ((j+1) s - 1, (i+1) s - 1)).  diag(K_l) = c by0 bx0
 // + (d+ + d-) by0 ax0 + sigma (e+ + e-) ay0 bx0 (ax0, ay0: Toeplitz diagonals,
 // bx0, by0: Galerkin mass diagonals); W = omega / diag.
 template <typename T>
 __global__ void level_fields_kernel(const double* __restrict__ dp, const double* __restrict__ dm,
                                     const double* __restrict__ ep, const double* __restrict__ em,
-                                    int n1f, int n1, int n2, int s, double sigma, double c,
+                                    int n1f, int n1, int n2, int s, int offx, int offy,
+                                    double sigma, double c,
                                     double bx0, double by0, const double* __restrict__ tx,
                                     const double* __restrict__ ty, double omega, T* odp, T* odm,
                                     T* oep, T* oem, T* W) {
@@ -315,7 +314,7 @@ __global__ void level_fields_kernel(const double* __restrict__ dp, const double*
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx % n1), j = (int)(idx / n1);
-    const size_t f = (size_t)((j + 1) * s - 1) * n1f + (size_t)((i + 1) * s - 1);
+    const size_t f = (size_t)(s * j + offy) * n1f + (size_t)(s * i + offx);
     const double a = dp[f], b = dm[f], e = sigma * ep[f], g = sigma * em[f];
     odp[idx] = T(a);
     odm[idx] = T(b);
@@ -328,14 +327,14 @@ __global__ void level_fields_kernel(const double* __restrict__ dp, const double*
 
 template <typename T>
 cudaError_t launch_level_fields(const double* dp, const double* dm, const double* ep,
-                                const double* em, int n1f, int n1, int n2, int stride,
-                                double sigma, double c, double bx0, double by0, const double* tx,
-                                const double* ty, double omega, T* odp, T* odm, T* oep, T* oem,
-                                T* W, cudaStream_t st) {
+                                const double* em, int n1f, int n1, int n2, int stride, int offx,
+                                int offy, double sigma, double c, double bx0, double by0,
+                                const double* tx, const double* ty, double omega, T* odp, T* odm,
+                                T* oep, T* oem, T* W, cudaStream_t st) {
   const size_t N = (size_t)n1 * n2;
   level_fields_kernel<T><<<grid_for(N, 256), 256, 0, st>>>(dp, dm, ep, em, n1f, n1, n2, stride,
-                                                           sigma, c, bx0, by0, tx, ty, omega,
-                                                           odp, odm, oep, oem, W);
+                                                           offx, offy, sigma, c, bx0, by0, tx, ty,
+                                                           omega, odp, odm, oep, oem, W);
   return cudaGetLastError();
 }
 
@@ -470,6 +469,25 @@ cudaError_t launch_stencil_inverse(const double* S, int n1, int n2, double* work
   return cudaGetLastError();
 }
 
+// explicit inverse of a dense N x N matrix (row-major, N <= 1024)
+__global__ void dense_inverse_kernel(const double* __restrict__ K, int N, double* A, double* inv,
+                                     int* info) {
+  const int W2 = 2 * N;
+  for (int e = threadIdx.x; e < N * W2; e += blockDim.x) {
+    const int r = e / W2, col = e % W2;
+    A[e] = col < N ? K[(size_t)r * N + col] : (col - N == r ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  gauss_jordan_block(A, N, inv, info);
+}
+
+cudaError_t launch_dense_inverse(const double* K, int N, double* work, double* inv, int* info,
+                                 cudaStream_t st) {
+  if (N > 1024) return cudaErrorInvalidValue;
+  dense_inverse_kernel<<<1, 256, 0, st>>>(K, N, work, inv, info);
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void coarse_solve_kernel(const double* __restrict__ inv, int N, const T* __restrict__ b,
                                     T* x) {
@@ -501,7 +519,8 @@ cudaError_t launch_coarse_solve(const double* inv, int N, const T* b, T* x, cuda
   template cudaError_t launch_prolong_add<T>(const T*, int, int, T*, cudaStream_t);               \
   template cudaError_t launch_inject<T>(const T*, int, int, T*, cudaStream_t);                    \
   template cudaError_t launch_level_fields<T>(const double*, const double*, const double*,        \
-                                              const double*, int, int, int, int, double, double,  \
+                                              const double*, int, int, int, int, int, int,        \
+                                              double, double,                                     \
                                               double, double, const double*, const double*,       \
                                               double, T*, T*, T*, T*, T*, cudaStream_t);          \
   template cudaError_t launch_coarse_solve<T>(const double*, int, const T*, T*, cudaStream_t); \

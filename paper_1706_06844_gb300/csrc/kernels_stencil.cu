@@ -72,7 +72,10 @@ __global__ void galerkin9_kernel(const double* __restrict__ Sf, int n1, int n2,
     for (int ay = -1; ay <= 1; ++ay) {
 #pragma unroll
       for (int ax = -1; ax <= 1; ++ax) {
-        const int fy = 2 * J + 1 + ay, fx = 2 * I + 1 + ax;  // always inside the fine grid
+        // the fine points of P's column (J, I); for even sizes the first
+        // column is truncated at the low end
+        const int fy = coarse_at(n2, J) + ay, fx = coarse_at(n1, I) + ax;
+        if (fy < 0 || fy >= n2 || fx < 0 || fx >= n1) continue;
         const double pa = (ay ? 0.5 : 1.0) * (ax ? 0.5 : 1.0);
         const size_t frow = (size_t)fy * n1 + fx;
 #pragma unroll
@@ -85,19 +88,8 @@ __global__ void galerkin9_kernel(const double* __restrict__ Sf, int n1, int n2,
             // coarse parents of fine node b along each axis
             int qy[2], qx[2];
             double wy[2], wx[2];
-            int ny = 0, nx = 0;
-            if (by & 1) {
-              qy[0] = (by - 1) >> 1; wy[0] = 1.0; ny = 1;
-            } else {
-              if (by / 2 - 1 >= 0) { qy[ny] = by / 2 - 1; wy[ny] = 0.5; ++ny; }
-              if (by / 2 < m2) { qy[ny] = by / 2; wy[ny] = 0.5; ++ny; }
-            }
-            if (bx & 1) {
-              qx[0] = (bx - 1) >> 1; wx[0] = 1.0; nx = 1;
-            } else {
-              if (bx / 2 - 1 >= 0) { qx[nx] = bx / 2 - 1; wx[nx] = 0.5; ++nx; }
-              if (bx / 2 < m1) { qx[nx] = bx / 2; wx[nx] = 0.5; ++nx; }
-            }
+            const int ny = coarse_parents<double>(n2, by, qy, wy);
+            const int nx = coarse_parents<double>(n1, bx, qx, wx);
             for (int u = 0; u < ny; ++u)
               for (int t = 0; t < nx; ++t)
                 acc[(qy[u] - J + 1) * 3 + (qx[t] - I + 1)] += v * wy[u] * wx[t];
@@ -235,5 +227,142 @@ cudaError_t launch_add(size_t N, const T* A, const T* B, T* Y, cudaStream_t st) 
 FDE_STENCIL_INST(float)
 FDE_STENCIL_INST(double)
 #undef FDE_STENCIL_INST
+
+// ============================================================================
+// Dense levels: the exact Galerkin hierarchy A_{l+1} = P^T A_l P of Sec. 4
+// (TGM step 3 at every level; the paper's tilde-P_MGM of Sec. 5.1) with
+// explicit N_l x N_l matrices, for small grids.  Row-major, FP64.
+
+// level 0: M of Eq. (M) assembled entry by entry; generators t_d at t[d + 1]
+// (d = -1 .. n - 1), A_gamma[i][k] = t_{i - k}
+__global__ void dense_assemble_kernel(const double* __restrict__ tx, const double* __restrict__ ty,
+                                      int n1, int n2, double c, double sigma,
+                                      const double* __restrict__ dp, const double* __restrict__ dm,
+                                      const double* __restrict__ ep, const double* __restrict__ em,
+                                      double* __restrict__ A) {
+  const size_t N = (size_t)n1 * n2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N * N;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = e / N, col = e % N;
+    const int i = (int)(r % n1), j = (int)(r / n1);
+    const int k = (int)(col % n1), l = (int)(col / n1);
+    double v = 0.0;
+    if (l == j) {  // x direction within grid row j
+      const int d = i - k;
+      if (d >= -1 && d <= n1 - 1) v += dp[r] * tx[d + 1];   // D+ (I (x) A_alpha)
+      if (-d >= -1 && -d <= n1 - 1) v += dm[r] * tx[-d + 1];  // D- (I (x) A_alpha^T)
+      if (k == i) v += c;
+    }
+    if (k == i) {  // y direction within grid column i
+      const int d = j - l;
+      if (d >= -1 && d <= n2 - 1) v += sigma * ep[r] * ty[d + 1];
+      if (-d >= -1 && -d <= n2 - 1) v += sigma * em[r] * ty[-d + 1];
+    }
+    A[e] = v;
+  }
+}
+
+cudaError_t launch_dense_assemble(const double* tx, const double* ty, int n1, int n2, double c,
+                                  double sigma, const double* dp, const double* dm,
+                                  const double* ep, const double* em, double* A, cudaStream_t st) {
+  const size_t N = (size_t)n1 * n2;
+  dense_assemble_kernel<<<blocks_for(N * N, 256), 256, 0, st>>>(tx, ty, n1, n2, c, sigma, dp, dm,
+                                                               ep, em, A);
+  return cudaGetLastError();
+}
+
+// AP = A P (N_f x N_c) and A_c = P^T AP (N_c x N_c), P the bilinear transfer
+// of the fine n1 x n2 grid; each column of P has at most nine entries
+__global__ void dense_times_p_kernel(const double* __restrict__ A, int n1, int n2,
+                                     double* __restrict__ AP) {
+  const int m1 = coarse_n(n1), m2 = coarse_n(n2);
+  const size_t Nf = (size_t)n1 * n2, Nc = (size_t)m1 * m2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nf * Nc;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = e / Nc, cc = e % Nc;
+    const int cx = (int)(cc % m1), cy = (int)(cc / m1);
+    double s = 0.0;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int fy = coarse_at(n2, cy) + dy;
+      if (fy < 0 || fy >= n2) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int fx = coarse_at(n1, cx) + dx;
+        if (fx < 0 || fx >= n1) continue;
+        s += (dy ? 0.5 : 1.0) * (dx ? 0.5 : 1.0) * A[r * Nf + (size_t)fy * n1 + fx];
+      }
+    }
+    AP[e] = s;
+  }
+}
+
+__global__ void dense_pt_times_kernel(const double* __restrict__ AP, int n1, int n2,
+                                      double* __restrict__ Ac) {
+  const int m1 = coarse_n(n1), m2 = coarse_n(n2);
+  const size_t Nc = (size_t)m1 * m2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nc * Nc;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t rc = e / Nc, cc = e % Nc;
+    const int cx = (int)(rc % m1), cy = (int)(rc / m1);
+    double s = 0.0;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int fy = coarse_at(n2, cy) + dy;
+      if (fy < 0 || fy >= n2) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int fx = coarse_at(n1, cx) + dx;
+        if (fx < 0 || fx >= n1) continue;
+        s += (dy ? 0.5 : 1.0) * (dx ? 0.5 : 1.0) * AP[((size_t)fy * n1 + fx) * Nc + cc];
+      }
+    }
+    Ac[e] = s;
+  }
+}
+
+cudaError_t launch_dense_galerkin(const double* A, int n1, int n2, double* AP, double* Ac,
+                                  cudaStream_t st) {
+  const size_t Nf = (size_t)n1 * n2, Nc = (size_t)coarse_n(n1) * coarse_n(n2);
+  dense_times_p_kernel<<<blocks_for(Nf * Nc, 256), 256, 0, st>>>(A, n1, n2, AP);
+  dense_pt_times_kernel<<<blocks_for(Nc * Nc, 256), 256, 0, st>>>(AP, n1, n2, Ac);
+  return cudaGetLastError();
+}
+
+// W = omega / diag(A)
+__global__ void dense_jacobi_weights_kernel(const double* __restrict__ A, size_t N, double omega,
+                                            double* W) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x)
+    W[i] = omega / A[i * N + i];
+}
+
+cudaError_t launch_dense_jacobi_weights(const double* A, size_t N, double omega, double* W,
+                                        cudaStream_t st) {
+  dense_jacobi_weights_kernel<<<blocks_for(N, 256), 256, 0, st>>>(A, N, omega, W);
+  return cudaGetLastError();
+}
+
+// mode 0: y = A x; 1: y = b - A x; 2: y = x + W (b - A x).  One warp per row
+// (coalesced along the row), fixed-order warp reduction.  y must not alias x.
+__global__ void dense_apply_kernel(int mode, const double* __restrict__ A, size_t N,
+                                   const double* __restrict__ X, const double* __restrict__ B,
+                                   const double* __restrict__ W, double* __restrict__ Y) {
+  const int lane = threadIdx.x & 31;
+  const size_t warps = (size_t)gridDim.x * (blockDim.x / 32);
+  for (size_t r = blockIdx.x * (size_t)(blockDim.x / 32) + (threadIdx.x >> 5); r < N;
+       r += warps) {
+    double s = 0.0;
+    for (size_t k = lane; k < N; k += 32) s += A[r * N + k] * X[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      if (mode == 0) Y[r] = s;
+      else if (mode == 1) Y[r] = B[r] - s;
+      else Y[r] = X[r] + W[r] * (B[r] - s);
+    }
+  }
+}
+
+cudaError_t launch_dense_apply(int mode, const double* A, size_t N, const double* X,
+                               const double* B, const double* W, double* Y, cudaStream_t st) {
+  dense_apply_kernel<<<blocks_for(N * 32, 256), 256, 0, st>>>(mode, A, N, X, B, W, Y);
+  return cudaGetLastError();
+}
 
 }  // namespace fde

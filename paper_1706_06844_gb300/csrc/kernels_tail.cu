@@ -100,43 +100,39 @@ __device__ void blk_smooth(const TailLevel<T>& L, T c, T* xs, T* ts) {
 
 template <typename T>
 __device__ void blk_restrict(const T* R, int n1, int n2, T rscale, T* BC) {
-  const int m1 = (n1 - 1) / 2, m2 = (n2 - 1) / 2;
+  const int m1 = coarse_n(n1), m2 = coarse_n(n2);
   const size_t NC = (size_t)m1 * m2;
   for (size_t idx = threadIdx.x; idx < NC; idx += blockDim.x) {
     const int ic = (int)(idx % m1), jc = (int)(idx / m1);
-    const int i = 2 * ic + 1, j = 2 * jc + 1;
-    const T* r0 = R + (size_t)(j - 1) * n1;
-    const T* r1 = r0 + n1;
-    const T* r2 = r1 + n1;
+    const int i = coarse_at(n1, ic), j = coarse_at(n2, jc);
     const T h = T(0.5);
-    const T s0 = h * r0[i - 1] + r0[i] + h * r0[i + 1];
-    const T s1 = h * r1[i - 1] + r1[i] + h * r1[i + 1];
-    const T s2 = h * r2[i - 1] + r2[i] + h * r2[i + 1];
-    BC[idx] = rscale * (h * s0 + s1 + h * s2);
+    T acc = T(0);
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int jj = j + dj;
+      if (jj < 0 || jj >= n2) continue;
+      const T* r = R + (size_t)jj * n1;
+      T sr = r[i];
+      if (i > 0) sr += h * r[i - 1];
+      if (i + 1 < n1) sr += h * r[i + 1];
+      acc += (dj ? h : T(1)) * sr;
+    }
+    BC[idx] = rscale * acc;
   }
 }
 
 template <typename T>
 __device__ void blk_prolong_add(const T* XC, int n1, int n2, T* X) {
-  const int m1 = (n1 - 1) / 2, m2 = (n2 - 1) / 2;
+  const int m1 = coarse_n(n1);
   const size_t N = (size_t)n1 * n2;
   for (size_t idx = threadIdx.x; idx < N; idx += blockDim.x) {
     const int i = (int)(idx % n1), j = (int)(idx / n1);
     int ci[2], cj[2];
     T wi[2], wj[2];
-    int ni, nj;
-    if (i & 1) { ci[0] = (i - 1) / 2; wi[0] = T(1); ni = 1; }
-    else { ci[0] = i / 2 - 1; ci[1] = i / 2; wi[0] = wi[1] = T(0.5); ni = 2; }
-    if (j & 1) { cj[0] = (j - 1) / 2; wj[0] = T(1); nj = 1; }
-    else { cj[0] = j / 2 - 1; cj[1] = j / 2; wj[0] = wj[1] = T(0.5); nj = 2; }
+    const int ni = coarse_parents<T>(n1, i, ci, wi);
+    const int nj = coarse_parents<T>(n2, j, cj, wj);
     T s = T(0);
-    for (int b = 0; b < nj; ++b) {
-      if (cj[b] < 0 || cj[b] >= m2) continue;
-      for (int a = 0; a < ni; ++a) {
-        if (ci[a] < 0 || ci[a] >= m1) continue;
-        s += wj[b] * wi[a] * XC[(size_t)cj[b] * m1 + ci[a]];
-      }
-    }
+    for (int b = 0; b < nj; ++b)
+      for (int a = 0; a < ni; ++a) s += wj[b] * wi[a] * XC[(size_t)cj[b] * m1 + ci[a]];
     X[idx] += s;
   }
 }

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libfde.so")
 FDE_OK, FDE_ERR_ARG, FDE_ERR_NOT_CONVERGED, FDE_ERR_NONFINITE = 0, 1, 2, 3
 FDE_ERR_CUDA, FDE_ERR_TIMEOUT, FDE_ERR_UNSUPPORTED = 4, 5, 6
 FDE_PRECOND_NONE, FDE_PRECOND_MG_SG, FDE_PRECOND_MG_REDISC, FDE_PRECOND_P2 = 0, 1, 2, 3
+FDE_PRECOND_MG_EXACT = 4
 FDE_PREC_FP64, FDE_PREC_FP32, FDE_PREC_BF16, FDE_PREC_FP16, FDE_PREC_BF16X3 = 0, 1, 2, 3, 4
 FDE_PATH_AUTO, FDE_PATH_GEMM, FDE_PATH_FFT, FDE_PATH_DIRECT, FDE_PATH_TUNE = 0, 1, 2, 3, 4
 FDE_OUTER_FP64, FDE_OUTER_DF32 = 0, 1

@@ -75,6 +75,11 @@ class Case:
         c, s = self.sc["c"], self.sc["sigma"]
         if p.precond == fde.FDE_PRECOND_P2:
             return mg.band_p2(self.n1, self.n2, c, s, self.coef_new, p.coarsest_n)
+        if p.precond == fde.FDE_PRECOND_MG_EXACT:
+            from oracle.operator import assemble_M, toeplitz_A
+            K0 = assemble_M(toeplitz_A(self.wx, self.n1), toeplitz_A(self.wy, self.n2), c, s,
+                            *self.coef_new)
+            return mg.exact_galerkin(K0, self.n1, self.n2, p.coarsest_n)
         if p.precond == fde.FDE_PRECOND_MG_SG:
             return mg.structured_galerkin(self.wx, self.wy, self.n1, self.n2, c, s,
                                           self.coef_new, p.coarsest_n)

@@ -27,7 +27,8 @@ def _vcycles(hier, R, omega, cycles):
     return X
 
 
-@pytest.mark.parametrize("n1,n2", [(63, 63), (127, 127), (31, 63), (255, 255), (511, 127)])
+@pytest.mark.parametrize("n1,n2", [(63, 63), (127, 127), (31, 63), (255, 255), (511, 127),
+                                   (64, 64), (32, 48), (100, 36)])
 def test_fp64_levels_and_vcycle(n1, n2):
     # stencil levels: the Galerkin products are formed in FP64 from at most 81
     # terms per entry, the applies sum nine products: relative 1e-13 against

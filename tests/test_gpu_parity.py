@@ -85,6 +85,71 @@ def test_outer_apply_and_rhs(name, mk, outer):
 def test_fp64_vcycle_matches_oracle(precond, n1, n2):
     # one V-cycle (Sec. 4) in FP64: same algorithm, rounding-order differences
     # only (FFT vs matmul products): relative 1e-11
+    _fp64_vcycle_check(precond, n1, n2)
+
+
+@pytest.mark.parametrize("n1,n2", [(64, 64), (128, 128), (32, 48), (100, 36), (16, 16)])
+def test_fp64_vcycle_even_sizes(n1, n2):
+    # even and mixed-parity grids (the paper's n = 16 .. 128): coarse j on fine
+    # 2j - 1 and the bilinear stencil truncated at the low end (Sec. 4.1's K
+    # matrix), rediscretised coarse operators; the same bars as odd sizes
+    _fp64_vcycle_check(fde.FDE_PRECOND_MG_REDISC, n1, n2)
+
+
+@pytest.mark.parametrize("n1,n2", [(31, 31), (32, 32), (63, 63), (16, 48), (64, 64)])
+def test_exact_galerkin_levels_and_vcycle(n1, n2):
+    # the exact Galerkin hierarchy (dense P^T A P on the device, FP64) for
+    # variable coefficients, either parity: every level operator within 1e-12
+    # of the oracle's dense triple products (rounding order only: each entry
+    # sums at most 81 products per level), one V-cycle within 1e-11
+    _fp64_vcycle_check(fde.FDE_PRECOND_MG_EXACT, n1, n2)
+
+
+def test_exact_galerkin_differs_from_structured_for_variable_coefficients():
+    # Sec. 4.2 calls the exact Galerkin operator of variable coefficients
+    # infeasible at scale; the structured reading injects the coefficients
+    # instead: on level 1 the two differ by far more than rounding (and agree
+    # exactly for constant coefficients, tested separately)
+    import torch
+    rng = np.random.default_rng(8)
+    outs = {}
+    for pc in (fde.FDE_PRECOND_MG_SG, fde.FDE_PRECOND_MG_EXACT):
+        case = Case(inputs.perturbed_power_law(), 63, precond=pc)
+        h = case.handle()
+        try:
+            X = rng.standard_normal((31, 31)) if not outs else outs["X"]
+            y = torch.empty_like(dev(X))
+            fde.fde_level_apply(h, 1, dev(X), y)
+            torch.cuda.synchronize()
+            outs[pc] = host(y)
+            outs["X"] = X
+        finally:
+            fde.fde_destroy(h)
+    d = np.linalg.norm(outs[fde.FDE_PRECOND_MG_SG] - outs[fde.FDE_PRECOND_MG_EXACT])
+    assert d > 1e-4 * np.linalg.norm(outs[fde.FDE_PRECOND_MG_EXACT])
+
+
+def test_exact_galerkin_limits():
+    case = Case(inputs.perturbed_power_law(), 65, precond=fde.FDE_PRECOND_MG_EXACT)
+    with pytest.raises(fde.FDEError) as e:
+        fde.fde_create(case.params)  # 65^2 > 4096: dense levels refused
+    assert e.value.code == fde.FDE_ERR_UNSUPPORTED
+    case = Case(inputs.perturbed_power_law(), 31, precond=fde.FDE_PRECOND_MG_EXACT,
+                precision=fde.FDE_PREC_FP32)
+    with pytest.raises(fde.FDEError) as e:
+        fde.fde_create(case.params)
+    assert e.value.code == fde.FDE_ERR_ARG
+
+
+def test_structured_galerkin_rejects_even_levels():
+    # projecting a Toeplitz factor of an even level is no longer Toeplitz
+    case = Case(inputs.perturbed_power_law(), 64, precond=fde.FDE_PRECOND_MG_SG)
+    with pytest.raises(fde.FDEError) as e:
+        fde.fde_create(case.params)
+    assert e.value.code == fde.FDE_ERR_UNSUPPORTED
+
+
+def _fp64_vcycle_check(precond, n1, n2):
     import torch
     from oracle import multigrid as mg
     case = Case(inputs.perturbed_power_law(), n1, n2, precond=precond)
