@@ -261,10 +261,11 @@ int fde_profile_query(fde_handle* h, int kclass, long long* launches, double* ms
 long long fde_launch_count(const fde_handle* h);
 
 /* Batch of independent problems (Sec. 2's scheme on each, sizes, orders and
- * coefficients may all differ), stepped concurrently: up to 16 host worker
- * threads (the environment variable FDE_BATCH_WORKERS, 1..256, read at
- * creation, overrides the cap), each with its own CUDA stream, run disjoint
- * subsets of the problems (largest first).  params[0..count) are copied; problem i gets a
+ * coefficients may all differ), stepped together: by the grouped engine (see
+ * fde_batch_engine) or by up to 16 host worker threads (the environment
+ * variable FDE_BATCH_WORKERS, 1..256, read at creation, overrides the cap),
+ * each with its own CUDA stream, running disjoint subsets of the problems
+ * (largest first).  params[0..count) are copied; problem i gets a
  * handle of its own (fde_batch_handle) on which the caller sets coefficients
  * or state as for a single problem.  Work of fde_batch_step starts after the
  * work already enqueued on `stream` and `stream` waits for all of it before
@@ -287,6 +288,21 @@ fde_handle* fde_batch_handle(fde_batch* b, int i);
 int fde_batch_step(fde_batch* b, const double* const* u_prev, const double* const* v_half,
                    double* const* u_next, fde_stats* st);
 int fde_batch_status(const fde_batch* b, int i);
+/* Which engine stepped the batch: 0 none yet, 1 grouped (every stage of all
+ * problems' solves -- Toeplitz passes, transposes, smoothing, transfers, the
+ * V-cycle tail, matvecs, Gram-Schmidt passes, Givens updates -- one launch for
+ * the whole batch, FGMRES iterations in lockstep with per-problem gates on the
+ * device, one restart cycle of the batch replayed from a CUDA graph), 2 worker
+ * threads.  The grouped engine is used when every problem runs the FP32
+ * V-cycle (MG_SG or MG_REDISC, FFT or direct-sum products above the
+ * one-launch tail, one cycle per application), the double-float outer apply,
+ * FGMRES with one restart length <= 32 and no warm start, unless the
+ * environment variable FDE_BATCH_ENGINE=threads (read at the first step) asks
+ * for the worker threads; fde_batch_engine_note says why an engine was chosen. */
+int fde_batch_engine(const fde_batch* b);
+const char* fde_batch_engine_note(const fde_batch* b);
+/* Kernels launched for the batch so far (both engines, graph nodes counted). */
+long long fde_batch_launch_count(const fde_batch* b);
 
 /* y = M x (Eq. M) with the given coefficients (device arrays d+, d-, e+, e-,
  * n2 x n1, as for fde_set_coefficients) in FP64, WITHOUT a handle and WITHOUT

@@ -11,7 +11,7 @@ OUT = os.path.join(HERE, "libfde.so")
 OBJ = os.path.join(HERE, "_build")
 SOURCES = ["fde.cu", "kernels_toeplitz.cu", "kernels_mg.cu", "kernels_krylov.cu", "tc_gemm.cu",
            "kernels_stencil.cu", "kernels_tail.cu", "fde_batch.cu",
-           "fde_noalloc.cu"]
+           "fde_group.cu", "fde_noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

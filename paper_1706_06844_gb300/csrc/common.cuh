@@ -295,4 +295,167 @@ cudaError_t launch_arnoldi_start(const ArnoldiState& st, const double* beta_dev,
 cudaError_t launch_arnoldi_lsq(const ArnoldiState& st, int k, double* y, cudaStream_t s);
 int cgs_blocks();
 
+// ---------------------------------------------------------------- grouped launches
+// Many independent problems advanced by one launch per stage (the batch
+// engine): a launch takes an array of per-call argument records ("entries",
+// one per problem, the same arguments the single-problem launcher takes) and
+// a work list of (entry, unit) items; a unit is a vector pair of an FFT pass,
+// a vector of a direct pass, a 32 x 32 tile of a transpose or a chunk of an
+// element-wise stage.  An entry runs only while its problem is active
+// (gate.active[prob] != 0) and, when want >= 0, while gate.relax[prob] == want.
+struct GGate {
+  const int* active;
+  const int* relax;
+};
+struct GItem {
+  int e;     // entry index
+  int unit;  // unit within the entry
+};
+__device__ __forceinline__ bool gate_open(const GGate& g, int prob, int want) {
+  return g.active[prob] != 0 && (want < 0 || g.relax[prob] == want);
+}
+constexpr int kGChunk = 2048;  // elements per chunk of an element-wise stage
+
+template <typename T, typename R, typename C>
+struct GFftPass {
+  const T* X;
+  int es, vs, nvec, n, logL;
+  const cx<R>*S1, *S2, *tw;
+  const C *cp, *cm;
+  const T* M;
+  double cmass;
+  T* Y;
+  int accumulate, prob, want;
+};
+// the largest logL of the entries sets the shared memory (two padded buffers)
+template <typename T, typename R, typename C>
+cudaError_t launch_g_fft_pass(const GFftPass<T, R, C>* ent, const GItem* items, int nitems,
+                              int max_logL, GGate gate, cudaStream_t st);
+
+template <typename T>
+struct GDirectPass {
+  const T* X;
+  int es, vs, nvec, n;
+  const T *t, *cp, *cm, *M;
+  double cmass;
+  T* Y;
+  int accumulate, prob, want;
+};
+template <typename T>
+cudaError_t launch_g_direct_pass(const GDirectPass<T>* ent, const GItem* items, int nitems,
+                                 int max_n, GGate gate, cudaStream_t st);
+
+template <typename T>
+struct GTranspose {
+  const T* in;
+  int rows, cols;
+  T* out;
+  int add, prob, want;
+};
+template <typename T>
+cudaError_t launch_g_transpose(const GTranspose<T>* ent, const GItem* items, int nitems,
+                               GGate gate, cudaStream_t st);
+
+// element-wise and stencil stages of a V-cycle level, one record per problem
+enum GOp : int {
+  G_MUL = 0,       // x = W b
+  G_RESID = 1,     // kx = b - kx
+  G_SMOOTH = 2,    // x = x + W (b - kx)
+  G_MASS = 3,      // xby, xbx, mass from x (structured-Galerkin level > 0)
+  G_RESTRICT = 4,  // bc = rscale P^T kx (units over the coarse grid)
+  G_PROLONG = 5,   // x += P xc
+};
+template <typename T>
+struct GLevelOp {
+  int n1, n2;
+  T *x, *b, *kx, *W;
+  T *xby, *xbx, *mass;
+  T bx0, bx1, by0, by1, c;
+  T *bc, *xc;  // next level's right-hand side and solution
+  T rscale;
+  int prob;
+};
+template <typename T>
+cudaError_t launch_g_level_op(int op, const GLevelOp<T>* ent, const GItem* items, int nitems,
+                              GGate gate, cudaStream_t st);
+
+// ---- grouped FGMRES (Sec. 5) of many problems in lockstep: iteration j of
+// every active problem in one launch per pass; per-problem reductions finish
+// in the block that completes a problem's chunks last
+constexpr int kGKChunk = 4096;  // double2 pairs per chunk of a Krylov pass
+struct GSolveState {
+  double bnorm;         // ||b||
+  double beta;          // residual norm at the start of the current cycle
+  double tol;           // rtol ||b||
+  double rel_residual;  // ||b - M x|| / ||b|| of the last true residual
+  int its;              // inner iterations of this solve
+  int k;                // columns of the current cycle
+  int restarts, relaxed, converged, failed;  // failed: a non-finite value was met
+};
+struct GKrylov {
+  double *V, *Z;   // padded bases, column pitch ldv (zero padding)
+  size_t ldv, N;   // N: grid points
+  double* part;    // this problem's partial sums: nchunk * 32
+  unsigned* tickets;  // 4 counters, zero at rest
+  double *h, *h2, *y, *scal;  // projections, least-squares solution, scratch scalars
+  ArnoldiState st;
+  GSolveState* ss;
+  double rtol;
+  int maxit, relax_on, restart, nchunk, prob;
+};
+// passes of Arnoldi step j (k = j + 1 <= 32) over the entries' chunks; the
+// last one also updates ss (iterations, k), status and the gates: active =
+// not (|g_{j+1}| <= tol or its >= maxit or breakdown or non-finite), relax =
+// relax_on and |g_{j+1}| <= FDE_RELAX_FACTOR tol
+cudaError_t launch_g_cgs2(const GKrylov* ent, const GItem* items, int nitems, int j, GGate gate,
+                          int* active, int* relax, cudaStream_t st);
+// element-wise vector stages of the grouped solve
+enum GVOp : int {
+  GV_D2F = 0,        // yf = (float) a
+  GV_F2D = 1,        // y = (double) af
+  GV_SUB = 2,        // y = a - b
+  GV_LINCOMB = 3,    // y = s0 a + s1 b + s2 c
+  GV_SCALE_INV = 4,  // y = a / sptr[0]
+  GV_ZERO = 5,       // y = 0
+  GV_COPY = 6,       // y = a
+};
+struct GVec {
+  const double *a, *b, *c;
+  const float* af;
+  double* y;
+  float* yf;
+  double s0, s1, s2;
+  const double* sptr;
+  size_t N;
+  int prob;
+};
+cudaError_t launch_g_vec(int op, const GVec* ent, const GItem* items, int nitems, GGate gate,
+                         cudaStream_t st);
+// out[e] = ||a_e|| per entry (deterministic per-problem reduction); ent[e].y
+// receives the norm at ent[e].y[0]; uses ticket slot 3 of the problem's
+// GKrylov (same index) and its partials
+cudaError_t launch_g_norm(const GVec* ent, const GKrylov* kry, const GItem* items, int nitems,
+                          GGate gate, cudaStream_t st);
+// start of a solve: ss = ||b|| (scal[0]), tol; problems with b = 0 finish at
+// once (x = 0 written by the caller); gates active = incycle = (b != 0)
+cudaError_t launch_g_solve_start(const GKrylov* ent, int count, int* active, int* incycle,
+                                 cudaStream_t st);
+// start of a cycle: g = (beta, 0, ...), beta = scal[1] (or ||b|| on the first
+// cycle), k = 0, restarts += 1, active = incycle, relax from |g_0| = beta
+cudaError_t launch_g_cycle_start(const GKrylov* ent, int count, int first, const int* incycle,
+                                 int* active, int* relax, cudaStream_t st);
+// end of a cycle: y = R^{-1} g over the problem's k columns
+cudaError_t launch_g_lsq(const GKrylov* ent, int count, const int* incycle, cudaStream_t st);
+// x += Z y over k columns (items over the grid, x the problem's solution)
+cudaError_t launch_g_update(const GKrylov* ent, double* const* x, const GItem* items, int nitems,
+                            const int* incycle, cudaStream_t st);
+// after the true residual norm (scal[1]): rel_residual, converged; incycle =
+// not converged and its < maxit and not failed
+cudaError_t launch_g_cycle_end(const GKrylov* ent, int count, int* incycle, cudaStream_t st);
+
+// the one-launch end of every problem's cycle: one CTA per entry
+template <typename T>
+cudaError_t launch_g_mg_tail(const TailArgs<T>* args, const int* probs, int count, GGate gate,
+                             cudaStream_t st);
+
 }  // namespace fde

@@ -19,7 +19,15 @@
 
 namespace fde {
 void set_global_error(const char* msg);
-}
+struct GroupEngine;
+GroupEngine* group_engine_create(const std::vector<fde_handle*>& hs, cudaStream_t st,
+                                 std::string& why);
+void group_engine_destroy(GroupEngine* e);
+int group_engine_step(GroupEngine* e, const double* const* u_prev, const double* const* v_half,
+                      double* const* u_next, cudaStream_t st, std::vector<int>& rc,
+                      fde_stats* stats);
+long long group_engine_launches(const GroupEngine* e);
+}  // namespace fde
 
 struct fde_batch {
   int device = 0;
@@ -30,6 +38,12 @@ struct fde_batch {
   std::vector<cudaEvent_t> done;         // one per worker
   cudaEvent_t start = nullptr;
   std::vector<int> rc;                   // last status per problem
+  // grouped engine (fde_group.cu): built at the first step when every problem
+  // qualifies and FDE_BATCH_ENGINE is not "threads"; engine_state 0 = not
+  // decided, 1 = grouped, 2 = worker threads
+  fde::GroupEngine* engine = nullptr;
+  int engine_state = 0;
+  std::string engine_why;
 };
 
 namespace {
@@ -37,6 +51,10 @@ constexpr int kMaxWorkers = 16;
 
 void destroy(fde_batch* b) {
   if (!b) return;
+  if (b->engine) {
+    cudaStreamSynchronize(b->user);
+    fde::group_engine_destroy(b->engine);
+  }
   for (fde_handle* h : b->h) fde_destroy(h);
   for (cudaStream_t s : b->streams) {
     cudaStreamSynchronize(s);
@@ -128,6 +146,19 @@ fde_handle* fde_batch_handle(fde_batch* b, int i) {
   return b->h[i];
 }
 
+int fde_batch_engine(const fde_batch* b) { return b ? b->engine_state : 0; }
+
+const char* fde_batch_engine_note(const fde_batch* b) {
+  return b ? b->engine_why.c_str() : "";
+}
+
+long long fde_batch_launch_count(const fde_batch* b) {
+  if (!b) return 0;
+  long long n = fde::group_engine_launches(b->engine);
+  for (fde_handle* h : b->h) n += fde_launch_count(h);
+  return n;
+}
+
 int fde_batch_status(const fde_batch* b, int i) {
   if (!b || i < 0 || i >= (int)b->rc.size()) return FDE_ERR_ARG;
   return b->rc[i];
@@ -140,6 +171,40 @@ int fde_batch_step(fde_batch* b, const double* const* u_prev, const double* cons
   if (!u_prev || !v_half || !u_next) {
     fde::set_global_error("fde_batch_step: null pointer array");
     return FDE_ERR_ARG;
+  }
+  if (b->engine_state == 0) {
+    const char* env = std::getenv("FDE_BATCH_ENGINE");
+    b->engine_state = 2;
+    if (!(env && std::string(env) == "threads")) {
+      // coefficients may still be in flight on the problems' own streams
+      for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
+      b->engine = fde::group_engine_create(b->h, b->user, b->engine_why);
+      if (b->engine) b->engine_state = 1;
+    } else {
+      b->engine_why = "FDE_BATCH_ENGINE=threads";
+    }
+  }
+  if (b->engine_state == 1) {
+    // the problems' own streams may hold coefficient updates: the caller's
+    // stream waits for them, then runs the grouped step
+    for (int w = 0; w < (int)b->streams.size(); ++w) {
+      if (cudaEventRecord(b->done[w], b->streams[w]) != cudaSuccess ||
+          cudaStreamWaitEvent(b->user, b->done[w], 0) != cudaSuccess)
+        return FDE_ERR_CUDA;
+    }
+    const int r = fde::group_engine_step(b->engine, u_prev, v_half, u_next, b->user, b->rc, st);
+    if (r != FDE_OK) {
+      fde::set_global_error("fde_batch_step: the grouped engine failed");
+      return r;
+    }
+    for (int i = 0; i < count; ++i)
+      if (b->rc[i] != FDE_OK) {
+        char buf[600];
+        snprintf(buf, sizeof(buf), "fde_batch_step: problem %d: %s", i, fde_last_error(b->h[i]));
+        fde::set_global_error(buf);
+        return b->rc[i];
+      }
+    return FDE_OK;
   }
   // the workers' streams start after the caller's stream work that precedes this call
   if (cudaEventRecord(b->start, b->user) != cudaSuccess) return FDE_ERR_CUDA;

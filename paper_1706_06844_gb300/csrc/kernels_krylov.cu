@@ -8,6 +8,7 @@
 #include <utility>
 
 #include "common.cuh"
+#include "../../include/fde.h"
 
 namespace fde {
 
@@ -567,6 +568,397 @@ cudaError_t launch_arnoldi_start(const ArnoldiState& st, const double* beta_dev,
 
 cudaError_t launch_arnoldi_lsq(const ArnoldiState& st, int k, double* y, cudaStream_t s) {
   arnoldi_lsq_kernel<<<1, 32, 0, s>>>(st, k, y);
+  return cudaGetLastError();
+}
+
+// ============================================================================
+// grouped FGMRES (many problems in lockstep): the passes above over items
+// (problem entry, chunk of kGKChunk double2 pairs); each problem reduces its
+// partials in the block that finishes its last chunk, in chunk order
+
+namespace {
+
+__device__ __forceinline__ bool publish_partials_at(const double* sred, int cnt, double* part,
+                                                    int nb, int slot, unsigned* ticket) {
+  __shared__ unsigned last;
+  if ((int)threadIdx.x < cnt) {
+    double t = 0.0;
+    for (int w = 0; w < CT / 32; ++w) t += sred[threadIdx.x * (CT / 32) + w];
+    part[(size_t)threadIdx.x * nb + slot] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == (unsigned)(nb - 1)) ? 1u : 0u;
+  __syncthreads();
+  if (last) __threadfence();
+  return last != 0;
+}
+
+__device__ __forceinline__ void chunk_range(const GKrylov& e, int chunk, size_t& lo, size_t& hi) {
+  const size_t n2 = (e.N + 1) / 2;
+  lo = (size_t)chunk * kGKChunk;
+  hi = lo + kGKChunk < n2 ? lo + kGKChunk : n2;
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(CT) g_cgs_project_kernel(const GKrylov* __restrict__ ent,
+                                                           const GItem* __restrict__ items,
+                                                           int nitems, int j, GGate gate) {
+  __shared__ double sred[KMAX * (CT / 32)];
+  const int k = j + 1;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GItem g = items[it];
+    const GKrylov& e = ent[g.e];
+    if (!gate_open(gate, e.prob, -1)) continue;
+    size_t lo, hi;
+    chunk_range(e, g.unit, lo, hi);
+    const double* w = e.V + (size_t)(j + 1) * e.ldv;
+    double acc[KMAX];
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) acc[q] = 0.0;
+    for (size_t q = lo + threadIdx.x; q < hi; q += CT) {
+      const double2 wv = ld2(w, q);
+#pragma unroll
+      for (int gg = 0; gg < KMAX; ++gg)
+        if (gg < k) {
+          const double2 v = ld2(e.V + (size_t)gg * e.ldv, q);
+          acc[gg] = fma(v.x, wv.x, fma(v.y, wv.y, acc[gg]));
+        }
+    }
+    block_reduce_vec<KMAX>(acc, k, sred);
+    if (publish_partials_at(sred, k, e.part, e.nchunk, g.unit, e.tickets)) {
+      final_sums(e.part, k, e.nchunk, e.h);
+      if (threadIdx.x == 0) e.tickets[0] = 0u;
+    }
+    __syncthreads();
+  }
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(CT) g_cgs_subproj_kernel(const GKrylov* __restrict__ ent,
+                                                           const GItem* __restrict__ items,
+                                                           int nitems, int j, GGate gate) {
+  __shared__ double sred[KMAX * (CT / 32)];
+  __shared__ double hs[KMAX];
+  const int k = j + 1;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GItem g = items[it];
+    const GKrylov& e = ent[g.e];
+    if (!gate_open(gate, e.prob, -1)) continue;
+    if ((int)threadIdx.x < KMAX) hs[threadIdx.x] = (int)threadIdx.x < k ? e.h[threadIdx.x] : 0.0;
+    __syncthreads();
+    size_t lo, hi;
+    chunk_range(e, g.unit, lo, hi);
+    double* w = e.V + (size_t)(j + 1) * e.ldv;
+    double acc[KMAX];
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) acc[q] = 0.0;
+    for (size_t q = 2 * lo + threadIdx.x; q < 2 * hi; q += CT) {  // scalar elements
+      double v[KMAX];
+#pragma unroll
+      for (int gg = 0; gg < KMAX; ++gg) v[gg] = gg < k ? e.V[(size_t)gg * e.ldv + q] : 0.0;
+      double wv = w[q];
+#pragma unroll
+      for (int gg = 0; gg < KMAX; ++gg) wv = fma(-hs[gg], v[gg], wv);
+      w[q] = wv;
+#pragma unroll
+      for (int gg = 0; gg < KMAX; ++gg) acc[gg] = fma(v[gg], wv, acc[gg]);
+    }
+    block_reduce_vec<KMAX>(acc, k, sred);
+    if (publish_partials_at(sred, k, e.part, e.nchunk, g.unit, e.tickets + 1)) {
+      final_sums(e.part, k, e.nchunk, e.h2);
+      if (threadIdx.x == 0) e.tickets[1] = 0u;
+    }
+    __syncthreads();
+  }
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(CT) g_cgs_subnorm_kernel(const GKrylov* __restrict__ ent,
+                                                           const GItem* __restrict__ items,
+                                                           int nitems, int j, GGate gate,
+                                                           int* active, int* relax) {
+  __shared__ double sred[CT / 32];
+  __shared__ double hs[KMAX];
+  __shared__ double nrm2;
+  const int k = j + 1;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GItem g = items[it];
+    const GKrylov& e = ent[g.e];
+    if (!gate_open(gate, e.prob, -1)) continue;
+    if ((int)threadIdx.x < KMAX) hs[threadIdx.x] = (int)threadIdx.x < k ? e.h2[threadIdx.x] : 0.0;
+    __syncthreads();
+    size_t lo, hi;
+    chunk_range(e, g.unit, lo, hi);
+    double2* w2 = reinterpret_cast<double2*>(e.V + (size_t)(j + 1) * e.ldv);
+    double acc[1] = {0.0};
+    for (size_t q = lo + threadIdx.x; q < hi; q += CT) {
+      double2 wv = w2[q];
+#pragma unroll
+      for (int gg = 0; gg < KMAX; ++gg)
+        if (gg < k) {
+          const double2 v = ld2(e.V + (size_t)gg * e.ldv, q);
+          wv.x = fma(-hs[gg], v.x, wv.x);
+          wv.y = fma(-hs[gg], v.y, wv.y);
+        }
+      w2[q] = wv;
+      acc[0] = fma(wv.x, wv.x, fma(wv.y, wv.y, acc[0]));
+    }
+    block_reduce_vec<1>(acc, 1, sred);
+    if (publish_partials_at(sred, 1, e.part, e.nchunk, g.unit, e.tickets + 2)) {
+      final_sums(e.part, 1, e.nchunk, &nrm2);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        e.tickets[2] = 0u;
+        arnoldi_column(e.st, j, e.h, e.h2, nrm2);
+        GSolveState& ss = *e.ss;
+        const ArnoldiStatus as = *e.st.status;
+        ss.its += 1;
+        ss.k = k;
+        if (as.nonfinite) ss.failed = 1;
+        const bool stop = as.gabs <= ss.tol || ss.its >= e.maxit || as.hnext == 0.0 ||
+                          as.nonfinite || k >= e.restart;
+        if (relax[e.prob]) ss.relaxed += 1;  // this step's matvec ran in FP32
+        active[e.prob] = stop ? 0 : 1;
+        relax[e.prob] = (e.relax_on && as.gabs <= FDE_RELAX_FACTOR * ss.tol) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void g_scale_kernel(const GKrylov* __restrict__ ent, const GItem* __restrict__ items,
+                               int nitems, int j, GGate gate) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GItem g = items[it];
+    const GKrylov& e = ent[g.e];
+    // the step's last pass closed the gate of a problem that stopped: its
+    // newest vector is not used, so leaving it unscaled is harmless
+    if (gate.active[e.prob] == 0 && e.ss->k != j + 1) continue;
+    size_t lo, hi;
+    chunk_range(e, g.unit, lo, hi);
+    const double inv = e.st.status->inv_norm;
+    double2* w2 = reinterpret_cast<double2*>(e.V + (size_t)(j + 1) * e.ldv);
+    for (size_t q = lo + threadIdx.x; q < hi; q += CT) {
+      double2 v = w2[q];
+      v.x *= inv;
+      v.y *= inv;
+      w2[q] = v;
+    }
+  }
+}
+
+__global__ void g_vec_kernel(int op, const GVec* __restrict__ ent, const GItem* __restrict__ items,
+                             int nitems, GGate gate) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GItem g = items[it];
+    const GVec& e = ent[g.e];
+    if (!gate_open(gate, e.prob, -1)) continue;
+    const size_t lo = (size_t)g.unit * kGChunk;
+    const size_t hi = lo + kGChunk < e.N ? lo + kGChunk : e.N;
+    for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      switch (op) {
+        case GV_D2F: e.yf[i] = (float)e.a[i]; break;
+        case GV_F2D: e.y[i] = (double)e.af[i]; break;
+        case GV_SUB: e.y[i] = e.a[i] - e.b[i]; break;
+        case GV_LINCOMB: e.y[i] = e.s0 * e.a[i] + e.s1 * e.b[i] + e.s2 * e.c[i]; break;
+        case GV_SCALE_INV: e.y[i] = e.a[i] * (1.0 / e.sptr[0]); break;
+        case GV_ZERO: e.y[i] = 0.0; break;
+        default: e.y[i] = e.a[i]; break;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(CT) g_norm_kernel(const GVec* __restrict__ ent,
+                                                    const GKrylov* __restrict__ kry,
+                                                    const GItem* __restrict__ items, int nitems,
+                                                    GGate gate) {
+  __shared__ double sred[CT / 32];
+  __shared__ double tot;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GItem g = items[it];
+    const GVec& e = ent[g.e];
+    const GKrylov& kk = kry[g.e];
+    if (!gate_open(gate, e.prob, -1)) continue;
+    const int nb = (int)((e.N + kGChunk - 1) / kGChunk);
+    const size_t lo = (size_t)g.unit * kGChunk;
+    const size_t hi = lo + kGChunk < e.N ? lo + kGChunk : e.N;
+    double acc[1] = {0.0};
+    for (size_t i = lo + threadIdx.x; i < hi; i += CT) acc[0] = fma(e.a[i], e.a[i], acc[0]);
+    block_reduce_vec<1>(acc, 1, sred);
+    if (publish_partials_at(sred, 1, kk.part, nb, g.unit, kk.tickets + 3)) {
+      final_sums(kk.part, 1, nb, &tot);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        kk.tickets[3] = 0u;
+        e.y[0] = sqrt(tot);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void g_solve_start_kernel(const GKrylov* __restrict__ ent, int count, int* active,
+                                     int* incycle) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+    const GKrylov& e = ent[q];
+    GSolveState& ss = *e.ss;
+    ss.bnorm = e.scal[0];
+    ss.tol = e.rtol * ss.bnorm;
+    ss.beta = ss.bnorm;
+    ss.its = ss.k = ss.restarts = ss.relaxed = 0;
+    ss.failed = isfinite(ss.bnorm) ? 0 : 1;
+    ss.converged = (ss.bnorm == 0.0) ? 1 : 0;
+    ss.rel_residual = 0.0;
+    const int go = (!ss.converged && !ss.failed) ? 1 : 0;
+    active[e.prob] = go;
+    incycle[e.prob] = go;
+  }
+}
+
+__global__ void g_cycle_start_kernel(const GKrylov* __restrict__ ent, int count, int first,
+                                     const int* incycle, int* active, int* relax) {
+  const int p = blockIdx.x;
+  if (p >= count) return;
+  const GKrylov& e = ent[p];
+  if (!incycle[e.prob]) return;
+  GSolveState& ss = *e.ss;
+  const double beta = first ? ss.bnorm : e.scal[1];
+  for (int i = threadIdx.x; i <= e.st.m; i += blockDim.x) e.st.g[i] = i == 0 ? beta : 0.0;
+  if (threadIdx.x == 0) {
+    e.st.status->gabs = beta;
+    ss.beta = beta;
+    ss.k = 0;
+    ss.restarts += 1;
+    active[e.prob] = 1;
+    // the first matvec's precision follows the residual estimate |g_0| = beta
+    relax[e.prob] = (e.relax_on && beta <= FDE_RELAX_FACTOR * ss.tol) ? 1 : 0;
+  }
+}
+
+__global__ void g_lsq_kernel(const GKrylov* __restrict__ ent, int count, const int* incycle) {
+  const int p = blockIdx.x;
+  if (p >= count || threadIdx.x != 0) return;
+  const GKrylov& e = ent[p];
+  if (!incycle[e.prob]) return;
+  const int k = e.ss->k, m = e.st.m;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = e.st.g[i];
+    for (int l = i + 1; l < k; ++l) s -= e.st.R[(size_t)l * (m + 1) + i] * e.y[l];
+    e.y[i] = s / e.st.R[(size_t)i * (m + 1) + i];
+  }
+}
+
+__global__ void g_update_kernel(const GKrylov* __restrict__ ent, double* const* __restrict__ xs,
+                                const GItem* __restrict__ items, int nitems, const int* incycle) {
+  __shared__ double cs[ArnoldiState::kMaxM];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GItem g = items[it];
+    const GKrylov& e = ent[g.e];
+    if (!incycle[e.prob]) continue;
+    const int k = e.ss->k;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = e.y[i];
+    __syncthreads();
+    double* x = xs[g.e];
+    const size_t lo = (size_t)g.unit * kGChunk;
+    const size_t hi = lo + kGChunk < e.N ? lo + kGChunk : e.N;
+    for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      double s = x[i];
+      for (int q = 0; q < k; ++q) s += cs[q] * e.Z[(size_t)q * e.ldv + i];
+      x[i] = s;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void g_cycle_end_kernel(const GKrylov* __restrict__ ent, int count, int* incycle) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+    const GKrylov& e = ent[q];
+    if (!incycle[e.prob]) continue;
+    GSolveState& ss = *e.ss;
+    const double beta = e.scal[1];
+    if (!isfinite(beta)) ss.failed = 1;
+    ss.rel_residual = ss.bnorm > 0.0 ? beta / ss.bnorm : 0.0;
+    ss.converged = beta <= ss.tol ? 1 : 0;
+    incycle[e.prob] = (!ss.converged && !ss.failed && ss.its < e.maxit) ? 1 : 0;
+  }
+}
+
+int g_grid(int nitems, const void* kernel) {
+  const int nb = resident_blocks(kernel);
+  return nitems < nb ? nitems : nb;
+}
+
+}  // namespace
+
+cudaError_t launch_g_cgs2(const GKrylov* ent, const GItem* items, int nitems, int j, GGate gate,
+                          int* active, int* relax, cudaStream_t st) {
+  const int k = j + 1;
+  if (nitems <= 0) return cudaSuccess;
+  if (k < 1 || k > 32) return cudaErrorInvalidValue;
+#define G_CGS(KM)                                                                               \
+  {                                                                                            \
+    g_cgs_project_kernel<KM><<<g_grid(nitems, (const void*)g_cgs_project_kernel<KM>), CT, 0,  \
+                               st>>>(ent, items, nitems, j, gate);                            \
+    g_cgs_subproj_kernel<KM><<<g_grid(nitems, (const void*)g_cgs_subproj_kernel<KM>), CT, 0,  \
+                               st>>>(ent, items, nitems, j, gate);                            \
+    g_cgs_subnorm_kernel<KM><<<g_grid(nitems, (const void*)g_cgs_subnorm_kernel<KM>), CT, 0,  \
+                               st>>>(ent, items, nitems, j, gate, active, relax);             \
+  }
+  if (k <= 4) G_CGS(4)
+  else if (k <= 8) G_CGS(8)
+  else if (k <= 16) G_CGS(16)
+  else G_CGS(32)
+#undef G_CGS
+  g_scale_kernel<<<g_grid(nitems, (const void*)g_scale_kernel), CT, 0, st>>>(ent, items, nitems, j,
+                                                                            gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g_vec(int op, const GVec* ent, const GItem* items, int nitems, GGate gate,
+                         cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  const int grid = nitems < 152 * 16 ? nitems : 152 * 16;
+  g_vec_kernel<<<grid, 256, 0, st>>>(op, ent, items, nitems, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g_norm(const GVec* ent, const GKrylov* kry, const GItem* items, int nitems,
+                          GGate gate, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  g_norm_kernel<<<g_grid(nitems, (const void*)g_norm_kernel), CT, 0, st>>>(ent, kry, items,
+                                                                            nitems, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g_solve_start(const GKrylov* ent, int count, int* active, int* incycle,
+                                 cudaStream_t st) {
+  g_solve_start_kernel<<<(count + 127) / 128, 128, 0, st>>>(ent, count, active, incycle);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g_cycle_start(const GKrylov* ent, int count, int first, const int* incycle,
+                                 int* active, int* relax, cudaStream_t st) {
+  g_cycle_start_kernel<<<count, 64, 0, st>>>(ent, count, first, incycle, active, relax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g_lsq(const GKrylov* ent, int count, const int* incycle, cudaStream_t st) {
+  g_lsq_kernel<<<count, 32, 0, st>>>(ent, count, incycle);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g_update(const GKrylov* ent, double* const* x, const GItem* items, int nitems,
+                            const int* incycle, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  const int grid = nitems < 152 * 8 ? nitems : 152 * 8;
+  g_update_kernel<<<grid, 256, 0, st>>>(ent, x, items, nitems, incycle);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g_cycle_end(const GKrylov* ent, int count, int* incycle, cudaStream_t st) {
+  g_cycle_end_kernel<<<(count + 127) / 128, 128, 0, st>>>(ent, count, incycle);
   return cudaGetLastError();
 }
 

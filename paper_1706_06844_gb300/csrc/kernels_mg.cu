@@ -509,6 +509,129 @@ cudaError_t launch_coarse_solve(const double* inv, int N, const T* b, T* x, cuda
 }
 
 // ---------------------------------------------------------------- instantiations
+// ============================================================================
+// grouped stages (many problems per launch; see GItem / GGate)
+
+template <typename T>
+__global__ void g_transpose_kernel(const GTranspose<T>* __restrict__ ent,
+                                   const GItem* __restrict__ items, int nitems, GGate gate) {
+  __shared__ T tile[32][33];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GItem g = items[it];
+    const GTranspose<T> e = ent[g.e];
+    if (!gate_open(gate, e.prob, e.want)) continue;
+    const int tc = (e.cols + 31) / 32;
+    const int c0 = (g.unit % tc) * 32, r0 = (g.unit / tc) * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+      const int r = r0 + k, c = c0 + threadIdx.x;
+      if (r < e.rows && c < e.cols) tile[k][threadIdx.x] = e.in[(size_t)r * e.cols + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+      const int c = c0 + k, r = r0 + threadIdx.x;
+      if (r < e.rows && c < e.cols) {
+        const size_t o = (size_t)c * e.rows + r;
+        e.out[o] = e.add ? e.out[o] + tile[threadIdx.x][k] : tile[threadIdx.x][k];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+cudaError_t launch_g_transpose(const GTranspose<T>* ent, const GItem* items, int nitems,
+                               GGate gate, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  const int grid = nitems < 152 * 16 ? nitems : 152 * 16;
+  g_transpose_kernel<T><<<grid, dim3(32, 8), 0, st>>>(ent, items, nitems, gate);
+  return cudaGetLastError();
+}
+
+// one chunk (kGChunk points of the fine grid, or of the coarse grid for the
+// restriction) of a level stage, the same arithmetic as the single-problem
+// kernels above
+template <typename T>
+__global__ void g_level_op_kernel(int op, const GLevelOp<T>* __restrict__ ent,
+                                  const GItem* __restrict__ items, int nitems, GGate gate) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GItem g = items[it];
+    const GLevelOp<T>& e = ent[g.e];
+    if (!gate_open(gate, e.prob, -1)) continue;
+    if (op == G_MASS && !e.xby) continue;  // no mass terms on this problem's level
+    const int n1 = e.n1, n2 = e.n2;
+    const size_t N = op == G_RESTRICT ? (size_t)coarse_n(n1) * coarse_n(n2) : (size_t)n1 * n2;
+    const size_t lo = (size_t)g.unit * kGChunk;
+    const size_t hi = lo + kGChunk < N ? lo + kGChunk : N;
+    for (size_t idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
+      if (op == G_MUL) {
+        e.x[idx] = e.W[idx] * e.b[idx];
+      } else if (op == G_RESID) {
+        e.kx[idx] = e.b[idx] - e.kx[idx];
+      } else if (op == G_SMOOTH) {
+        e.x[idx] = e.x[idx] + e.W[idx] * (e.b[idx] - e.kx[idx]);
+      } else if (op == G_MASS) {
+        const int i = (int)(idx % n1), j = (int)(idx / n1);
+        const T* X = e.x;
+        auto at = [&](int jj, int ii) -> T {
+          return (ii >= 0 && ii < n1 && jj >= 0 && jj < n2) ? X[(size_t)jj * n1 + ii] : T(0);
+        };
+        const T xc = X[idx];
+        const T up = at(j - 1, i), dn = at(j + 1, i), lf = at(j, i - 1), rt = at(j, i + 1);
+        e.xby[idx] = e.by1 * up + e.by0 * xc + e.by1 * dn;
+        e.xbx[idx] = e.bx1 * lf + e.bx0 * xc + e.bx1 * rt;
+        const T rowm = e.bx1 * at(j - 1, i - 1) + e.bx0 * up + e.bx1 * at(j - 1, i + 1);
+        const T row0 = e.bx1 * lf + e.bx0 * xc + e.bx1 * rt;
+        const T rowp = e.bx1 * at(j + 1, i - 1) + e.bx0 * dn + e.bx1 * at(j + 1, i + 1);
+        e.mass[idx] = e.c * (e.by1 * rowm + e.by0 * row0 + e.by1 * rowp);
+      } else if (op == G_RESTRICT) {
+        const int m1 = coarse_n(n1);
+        const int ic = (int)(idx % m1), jc = (int)(idx / m1);
+        const int i = coarse_at(n1, ic), j = coarse_at(n2, jc);
+        const T h = T(0.5);
+        T acc = T(0);
+        for (int dj = -1; dj <= 1; ++dj) {
+          const int jj = j + dj;
+          if (jj < 0 || jj >= n2) continue;
+          const T* r = e.kx + (size_t)jj * n1;
+          T sr = r[i];
+          if (i > 0) sr += h * r[i - 1];
+          if (i + 1 < n1) sr += h * r[i + 1];
+          acc += (dj ? h : T(1)) * sr;
+        }
+        e.bc[idx] = e.rscale * acc;
+      } else {  // G_PROLONG
+        const int m1 = coarse_n(n1);
+        const int i = (int)(idx % n1), j = (int)(idx / n1);
+        int ci[2], cj[2];
+        T wi[2], wj[2];
+        const int ni = coarse_parents<T>(n1, i, ci, wi);
+        const int nj = coarse_parents<T>(n2, j, cj, wj);
+        T sum = T(0);
+        for (int bb = 0; bb < nj; ++bb)
+          for (int a = 0; a < ni; ++a) sum += wj[bb] * wi[a] * e.xc[(size_t)cj[bb] * m1 + ci[a]];
+        e.x[idx] += sum;
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_g_level_op(int op, const GLevelOp<T>* ent, const GItem* items, int nitems,
+                              GGate gate, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  if (op < G_MUL || op > G_PROLONG) return cudaErrorInvalidValue;
+  const int grid = nitems < 152 * 16 ? nitems : 152 * 16;
+  g_level_op_kernel<T><<<grid, 256, 0, st>>>(op, ent, items, nitems, gate);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_g_transpose<float>(const GTranspose<float>*, const GItem*, int, GGate,
+                                               cudaStream_t);
+template cudaError_t launch_g_transpose<double>(const GTranspose<double>*, const GItem*, int,
+                                                GGate, cudaStream_t);
+template cudaError_t launch_g_level_op<float>(int, const GLevelOp<float>*, const GItem*, int,
+                                              GGate, cudaStream_t);
+
 #define INST_T(T)                                                                               \
   template cudaError_t launch_mass_prepass<T>(const T*, int, int, double, double, double, double, \
                                               double, T*, T*, T*, cudaStream_t);                  \

@@ -138,10 +138,7 @@ __device__ void blk_prolong_add(const T* XC, int n1, int n2, T* X) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) mg_tail_kernel(const TailArgs<T> a) {
-  __shared__ double bs[1024];
-  __shared__ T xs[kTailN * kTailN];
-  __shared__ T ts[kTailN + 2];
+__device__ __forceinline__ void mg_tail_body(const TailArgs<T>& a, double* bs, T* xs, T* ts) {
   const int last = a.nlev - 1;
   const T c = T(a.c);
   // down: pre-smoothing, residual, restriction
@@ -182,7 +179,40 @@ __global__ void __launch_bounds__(1024) mg_tail_kernel(const TailArgs<T> a) {
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(1024) mg_tail_kernel(const TailArgs<T> a) {
+  __shared__ double bs[1024];
+  __shared__ T xs[kTailN * kTailN];
+  __shared__ T ts[kTailN + 2];
+  mg_tail_body<T>(a, bs, xs, ts);
+}
+
+// grouped: one CTA per problem, each running its own tail from device memory
+template <typename T>
+__global__ void __launch_bounds__(1024) g_mg_tail_kernel(const TailArgs<T>* __restrict__ args,
+                                                         const int* __restrict__ probs, int count,
+                                                         GGate gate) {
+  __shared__ double bs[1024];
+  __shared__ T xs[kTailN * kTailN];
+  __shared__ T ts[kTailN + 2];
+  for (int k = blockIdx.x; k < count; k += gridDim.x) {
+    if (!gate_open(gate, probs[k], -1)) continue;
+    mg_tail_body<T>(args[k], bs, xs, ts);
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_g_mg_tail(const TailArgs<T>* args, const int* probs, int count, GGate gate,
+                             cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  g_mg_tail_kernel<T><<<count, 1024, 0, st>>>(args, probs, count, gate);
+  return cudaGetLastError();
+}
+template cudaError_t launch_g_mg_tail<float>(const TailArgs<float>*, const int*, int, GGate,
+                                             cudaStream_t);
 
 template <typename T>
 cudaError_t launch_mg_tail(const TailArgs<T>& a, cudaStream_t st) {

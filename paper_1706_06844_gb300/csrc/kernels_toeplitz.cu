@@ -202,6 +202,56 @@ __device__ void fft_dit_inv2(cx<R>* a, cx<R>* c, int logL, const cx<R>* __restri
   }
 }
 
+// one vector pair of a pass: x_va + i x_vb transformed, multiplied by the
+// spectra of A and A^T, transformed back, scaled and written (two buffers a, c
+// of padded_len(L) in shared memory)
+template <typename T, typename R, typename C>
+__device__ __forceinline__ void fft_pass_pair(const T* __restrict__ X, int es, int vs, int nvec,
+                                              int n, int logL, const cx<R>* __restrict__ S1,
+                                              const cx<R>* __restrict__ S2,
+                                              const cx<R>* __restrict__ tw,
+                                              const C* __restrict__ cp, const C* __restrict__ cm,
+                                              const T* __restrict__ M, R cmass, T* Y,
+                                              int accumulate, int pair, cx<R>* a, cx<R>* c) {
+  const int L = 1 << logL;
+  const int va = 2 * pair;
+  const bool hasb = va + 1 < nvec;
+  const size_t oa = (size_t)va * vs, ob = oa + vs;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    cx<R> z = {R(0), R(0)};
+    if (i < n) {  // x_v[i] packed as re (vector va) + i im (vector va + 1)
+      z.re = R(X[oa + (size_t)i * es]);
+      if (hasb) z.im = R(X[ob + (size_t)i * es]);
+    }
+    a[pad(i)] = z;
+  }
+  __syncthreads();
+  fft_dif(a, logL, tw);
+  for (int p = threadIdx.x; p < L; p += blockDim.x) {
+    const cx<R> z = a[pad(p)];
+    c[pad(p)] = cmul(z, S2[p]);
+    a[pad(p)] = cmul(z, S1[p]);
+  }
+  __syncthreads();
+  fft_dit_inv2(a, c, logL, tw);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const size_t ia = oa + (size_t)i * es;
+    const cx<R> ya_ = a[pad(i)], yc_ = c[pad(i)];
+    R y = ya_.re * coef<R, C>(cp, ia) + yc_.re * coef<R, C>(cm, ia);
+    if (M) y += cmass * R(M[ia]);
+    if (accumulate) y += R(Y[ia]);
+    Y[ia] = T(y);
+    if (hasb) {
+      const size_t ib = ob + (size_t)i * es;
+      R yb = ya_.im * coef<R, C>(cp, ib) + yc_.im * coef<R, C>(cm, ib);
+      if (M) yb += cmass * R(M[ib]);
+      if (accumulate) yb += R(Y[ib]);
+      Y[ib] = T(yb);
+    }
+  }
+  __syncthreads();
+}
+
 template <typename T, typename R, typename C>
 __global__ void __launch_bounds__(512)
 fft_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int logL,
@@ -211,48 +261,46 @@ fft_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int lo
                 int accumulate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 1 << logL;
-  const R cmass = R(cmass_d);
   cx<R>* a = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* c = a + padded_len(L);
   const int npairs = (nvec + 1) >> 1;
-  for (int pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
-    const int va = 2 * pair;
-    const bool hasb = va + 1 < nvec;
-    const size_t oa = (size_t)va * vs, ob = oa + vs;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-      cx<R> z = {R(0), R(0)};
-      if (i < n) {  // x_v[i] packed as re (vector va) + i im (vector va + 1)
-        z.re = R(X[oa + (size_t)i * es]);
-        if (hasb) z.im = R(X[ob + (size_t)i * es]);
-      }
-      a[pad(i)] = z;
-    }
-    __syncthreads();
-    fft_dif(a, logL, tw);
-    for (int p = threadIdx.x; p < L; p += blockDim.x) {
-      const cx<R> z = a[pad(p)];
-      c[pad(p)] = cmul(z, S2[p]);
-      a[pad(p)] = cmul(z, S1[p]);
-    }
-    __syncthreads();
-    fft_dit_inv2(a, c, logL, tw);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const size_t ia = oa + (size_t)i * es;
-      const cx<R> ya_ = a[pad(i)], yc_ = c[pad(i)];
-      R y = ya_.re * coef<R, C>(cp, ia) + yc_.re * coef<R, C>(cm, ia);
-      if (M) y += cmass * R(M[ia]);
-      if (accumulate) y += R(Y[ia]);
-      Y[ia] = T(y);
-      if (hasb) {
-        const size_t ib = ob + (size_t)i * es;
-        R yb = ya_.im * coef<R, C>(cp, ib) + yc_.im * coef<R, C>(cm, ib);
-        if (M) yb += cmass * R(M[ib]);
-        if (accumulate) yb += R(Y[ib]);
-        Y[ib] = T(yb);
-      }
-    }
-    __syncthreads();
+  for (int pair = blockIdx.x; pair < npairs; pair += gridDim.x)
+    fft_pass_pair<T, R, C>(X, es, vs, nvec, n, logL, S1, S2, tw, cp, cm, M, R(cmass_d), Y,
+                           accumulate, pair, a, c);
+}
+
+// grouped: item (entry, pair) of many problems' passes in one launch
+template <typename T, typename R, typename C>
+__global__ void __launch_bounds__(256)
+g_fft_pass_kernel(const GFftPass<T, R, C>* __restrict__ ent, const GItem* __restrict__ items,
+                  int nitems, GGate gate) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GItem g = items[it];
+    const GFftPass<T, R, C> e = ent[g.e];
+    if (!gate_open(gate, e.prob, e.want)) continue;
+    cx<R>* a = reinterpret_cast<cx<R>*>(smem_raw);
+    cx<R>* c = a + padded_len(1 << e.logL);
+    fft_pass_pair<T, R, C>(e.X, e.es, e.vs, e.nvec, e.n, e.logL, e.S1, e.S2, e.tw, e.cp, e.cm,
+                           e.M, R(e.cmass), e.Y, e.accumulate, g.unit, a, c);
   }
+}
+
+template <typename T, typename R, typename C>
+cudaError_t launch_g_fft_pass(const GFftPass<T, R, C>* ent, const GItem* items, int nitems,
+                              int max_logL, GGate gate, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  const size_t smem = fft_pass_two_buffer_bytes(max_logL, sizeof(cx<R>));
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = ensure_max_smem((const void*)g_fft_pass_kernel<T, R, C>);
+    if (e != cudaSuccess) return e;
+  }
+  const int per_sm = (int)((227 * 1024) / (smem + 1024));
+  int grid = 152 * (per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm));
+  if (grid > nitems) grid = nitems;
+  g_fft_pass_kernel<T, R, C><<<grid, 256, smem, st>>>(ent, items, nitems, gate);
+  return cudaGetLastError();
 }
 
 // The same pass with one shared buffer: the forward spectrum of a pair is
@@ -441,6 +489,29 @@ cudaError_t launch_build_spectra(const double* t, int n, int logL, double scale,
 
 // ---------------------------------------------------------------- direct
 template <typename T>
+__device__ __forceinline__ void direct_pass_vector(const T* __restrict__ X, int es, int vs, int n,
+                                                   const T* ts, const T* __restrict__ cp,
+                                                   const T* __restrict__ cm,
+                                                   const T* __restrict__ M, T cmass, T* Y,
+                                                   int accumulate, int v, T* xs) {
+  const size_t o = (size_t)v * vs;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) xs[k] = X[o + (size_t)k * es];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    T s1 = T(0), s2 = T(0);
+    const int k1 = (i + 1 < n - 1) ? i + 1 : n - 1;
+    for (int k = 0; k <= k1; ++k) s1 += ts[i - k + 1] * xs[k];  // (A x)_i, t_{i-k}
+    for (int k = (i > 0 ? i - 1 : 0); k < n; ++k) s2 += ts[k - i + 1] * xs[k];  // (A^T x)_i
+    const size_t ia = o + (size_t)i * es;
+    T y = s1 * (cp ? cp[ia] : T(1)) + s2 * (cm ? cm[ia] : T(1));
+    if (M) y += cmass * M[ia];
+    if (accumulate) y += Y[ia];
+    Y[ia] = y;
+  }
+  __syncthreads();
+}
+
+template <typename T>
 __global__ void direct_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n,
                                    const T* __restrict__ t, const T* __restrict__ cp,
                                    const T* __restrict__ cm, const T* __restrict__ M, T cmass,
@@ -449,23 +520,40 @@ __global__ void direct_pass_kernel(const T* __restrict__ X, int es, int vs, int 
   T* ts = reinterpret_cast<T*>(smem_raw);  // t_d at ts[d+1], d = -1..n-1
   T* xs = ts + (n + 1);
   for (int k = threadIdx.x; k <= n; k += blockDim.x) ts[k] = t[k];
-  for (int v = blockIdx.x; v < nvec; v += gridDim.x) {
-    const size_t o = (size_t)v * vs;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) xs[k] = X[o + (size_t)k * es];
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      T s1 = T(0), s2 = T(0);
-      const int k1 = (i + 1 < n - 1) ? i + 1 : n - 1;
-      for (int k = 0; k <= k1; ++k) s1 += ts[i - k + 1] * xs[k];  // (A x)_i, t_{i-k}
-      for (int k = (i > 0 ? i - 1 : 0); k < n; ++k) s2 += ts[k - i + 1] * xs[k];  // (A^T x)_i
-      const size_t ia = o + (size_t)i * es;
-      T y = s1 * (cp ? cp[ia] : T(1)) + s2 * (cm ? cm[ia] : T(1));
-      if (M) y += cmass * M[ia];
-      if (accumulate) y += Y[ia];
-      Y[ia] = y;
-    }
-    __syncthreads();
+  for (int v = blockIdx.x; v < nvec; v += gridDim.x)
+    direct_pass_vector<T>(X, es, vs, n, ts, cp, cm, M, cmass, Y, accumulate, v, xs);
+}
+
+// grouped: item (entry, vector); the generator is staged per item
+template <typename T>
+__global__ void g_direct_pass_kernel(const GDirectPass<T>* __restrict__ ent,
+                                     const GItem* __restrict__ items, int nitems, int max_n,
+                                     GGate gate) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ts = reinterpret_cast<T*>(smem_raw);
+  T* xs = ts + (max_n + 1);
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GItem g = items[it];
+    const GDirectPass<T> e = ent[g.e];
+    if (!gate_open(gate, e.prob, e.want)) continue;
+    for (int k = threadIdx.x; k <= e.n; k += blockDim.x) ts[k] = e.t[k];
+    direct_pass_vector<T>(e.X, e.es, e.vs, e.n, ts, e.cp, e.cm, e.M, T(e.cmass), e.Y,
+                          e.accumulate, g.unit, xs);
   }
+}
+
+template <typename T>
+cudaError_t launch_g_direct_pass(const GDirectPass<T>* ent, const GItem* items, int nitems,
+                                 int max_n, GGate gate, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(2 * max_n + 1) * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = ensure_max_smem((const void*)g_direct_pass_kernel<T>);
+    if (e != cudaSuccess) return e;
+  }
+  int grid = nitems < 152 * 8 ? nitems : 152 * 8;
+  g_direct_pass_kernel<T><<<grid, 128, smem, st>>>(ent, items, nitems, max_n, gate);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -512,6 +600,16 @@ template cudaError_t launch_build_spectra<double>(const double*, int, int, doubl
 template cudaError_t launch_build_spectra<float>(const double*, int, int, double, cx<float>*,
                                                  cx<float>*, cx<float>*, cudaStream_t,
                                                  cx<double>*);
+template cudaError_t launch_g_fft_pass<float, float, float>(const GFftPass<float, float, float>*,
+                                                            const GItem*, int, int, GGate,
+                                                            cudaStream_t);
+template cudaError_t launch_g_fft_pass<double, float, float>(
+    const GFftPass<double, float, float>*, const GItem*, int, int, GGate, cudaStream_t);
+template cudaError_t launch_g_fft_pass<double, df, df>(const GFftPass<double, df, df>*,
+                                                       const GItem*, int, int, GGate,
+                                                       cudaStream_t);
+template cudaError_t launch_g_direct_pass<float>(const GDirectPass<float>*, const GItem*, int,
+                                                 int, GGate, cudaStream_t);
 template cudaError_t launch_direct_pass<double>(const double*, int, int, int, int, const double*,
                                                 const double*, const double*, const double*,
                                                 double, double*, int, cudaStream_t);

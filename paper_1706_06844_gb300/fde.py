@@ -83,6 +83,9 @@ SIGNATURES = {
     "fde_batch_step": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                       ctypes.POINTER(_VP), ctypes.POINTER(fde_stats)]),
     "fde_batch_status": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "fde_batch_engine": (ctypes.c_int, [_VP]),
+    "fde_batch_engine_note": (ctypes.c_char_p, [_VP]),
+    "fde_batch_launch_count": (ctypes.c_longlong, [_VP]),
 }
 
 
@@ -305,3 +308,16 @@ def fde_batch_step(b, u_prev, v_half, u_next, allow_not_converged=False):
 
 def fde_level_path(h, level):
     return lib().fde_level_path(h, level)
+
+
+def fde_batch_engine(b):
+    return lib().fde_batch_engine(b)
+
+
+def fde_batch_engine_note(b):
+    m = lib().fde_batch_engine_note(b)
+    return m.decode() if m else ""
+
+
+def fde_batch_launch_count(b):
+    return lib().fde_batch_launch_count(b)
