@@ -702,8 +702,14 @@ class BatchRun:
         self.u, self.nxt = self.nxt, self.u
 
     def launches(self):
-        return sum(self.fde.fde_launch_count(self.fde.fde_batch_handle(self.b, k))
-                   for k in range(len(self.mine)))
+        return self.fde.fde_batch_launch_count(self.b)
+
+    def engine(self):
+        return {1: "grouped: one launch per stage for all problems, restart cycles replayed "
+                   "from a CUDA graph", 2: "worker threads"}.get(
+            self.fde.fde_batch_engine(self.b), "none") + \
+            (f" ({self.fde.fde_batch_engine_note(self.b)})"
+             if self.fde.fde_batch_engine_note(self.b) else "")
 
     def close(self):
         self.fde.fde_batch_destroy(self.b)
@@ -752,7 +758,7 @@ def run_batch(args, rank, world, dist):
                            "l2": "inputs larger than L2 (256 problems' Krylov bases)"},
                 "inner_iterations_per_batch_step_rank0": br.its[args.warmup:],
                 "wall_s": round(wall, 3), "gpu_launches": int(launches),
-                "clocks": clk.summary()}
+                "engine": br.engine(), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
 
 
@@ -796,6 +802,7 @@ def sub_batch(reps=3):
                 "unit": "problem-steps/s", "ms_per_batch_step": round(ms / k, 3),
                 "inner_iterations_per_batch_step": br.its[1:reps],
                 "gpu_launches_per_batch_step": int(launches / k),
+                "engine": br.engine(),
                 "oracle_true_residual_sample": [float(f"{r:.3e}") for r in res],
                 "workload": BATCH_WORKLOAD}
     finally:

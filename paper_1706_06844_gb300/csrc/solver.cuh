@@ -624,6 +624,9 @@ struct MG : MGBase {
       h->pend(gi);
       h->launches++;
       if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core products failed (%d)", r);
+      r = tc::level_finish(&L.gemm, (const float*)M, cm, (float*)kx, st);
+      if (L.gemm.splits > 1) h->launches++;
+      if (r != 0) return h->fail(FDE_ERR_CUDA, "tensor-core split reduction failed (%d)", r);
     }
     h->pend(pi);
     return FDE_OK;

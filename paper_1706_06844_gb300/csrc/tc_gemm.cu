@@ -43,9 +43,14 @@
 namespace fde {
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 64;
+// Output tiles of 128 x 240: at n = 2047 a launch has 9 x 16 = 144 CTAs for
+// the 152 SMs (256-wide tiles would leave 24 idle), and the smaller Toeplitz
+// operand leaves room for a third X-tile stage.
+constexpr int BM = 128, BN = 240, BK = 64;
+constexpr int ACC_COLS = 256;          // TMEM columns between the two accumulators
+constexpr int BH = 128;                // epilogue column split: [0, BH) and [BH, BN)
 constexpr int A_BYTES = BM * BK * 2;   // 16 KB
-constexpr int B_BYTES = BN * BK * 2;   // 32 KB
+constexpr int B_BYTES = BN * BK * 2;   // 30 KB
 constexpr int NUM_THREADS = 320;  // 2 + 8 warps
 constexpr int NSYN = 8;            // synthesis / epilogue warps
 constexpr uint32_t TMEM_COLS = 512;
@@ -58,19 +63,26 @@ constexpr int GEN_PAD = 1024;          // total padding elements
 constexpr int WIN = 336;               // entries (16-bit) per window
 constexpr int WIN_BYTES = WIN * 2;     // 672: a multiple of 16
 
+// Two rings: the X tiles (A operand) and the generator windows in SA slots,
+// filled by TMA up to SA jobs ahead; the synthesised Toeplitz tiles (B
+// operand) in SB slots.  An X slot is released when the job's MMAs complete,
+// a Toeplitz slot likewise.
 template <int NT>
 struct Cfg {
-  static constexpr int STAGES = NT == 1 ? 3 : 2;
-  static constexpr int STAGE_BYTES = NT * (A_BYTES + B_BYTES);  // 1 KB multiple
-  // + 1 KB alignment slack + 256 B barriers + one generator window per stage and term
-  static constexpr size_t FIXED =
-      (size_t)STAGES * STAGE_BYTES + 1024 + 256 + (size_t)STAGES * NT * WIN_BYTES;
+  static constexpr int SA = NT == 1 ? 4 : 3;
+  static constexpr int SB = NT == 1 ? 3 : 2;
+  static constexpr int A_STAGE = NT * A_BYTES;  // 1 KB multiples
+  static constexpr int B_STAGE = NT * B_BYTES;
+  static constexpr int RINGS = SA * A_STAGE + SB * B_STAGE;
+  // + 1 KB alignment slack + 256 B barriers + one generator window per X slot and term
+  static constexpr size_t FIXED = (size_t)RINGS + 1024 + 256 + (size_t)SA * NT * WIN_BYTES;
 };
 // epilogue staging (DIR 0: transposed accumulators + operand batches; DIR 1:
 // operand blocks) must fit in the pipeline stages it reuses
-static_assert(8 * (2 * 32 * 33 + 3 * 16 * 32) * 4 <= 3 * 1 * (128 * 64 * 2 + 256 * 64 * 2), "NT=1 DIR0");
-static_assert(8 * (2 * 32 * 33 + 3 * 32 * 32) * 4 <= 2 * 2 * (128 * 64 * 2 + 256 * 64 * 2), "NT=2 DIR0");
-static_assert(8 * (3 * 32 * 32) * 4 <= 2 * 2 * (128 * 64 * 2 + 256 * 64 * 2), "DIR1");
+static_assert(8 * (2 * 32 * 33 + 3 * 16 * 32) * 4 <= Cfg<1>::RINGS, "NT=1 DIR0");
+static_assert(8 * (2 * 32 * 33 + 3 * 32 * 32) * 4 <= Cfg<2>::RINGS, "NT=2 DIR0");
+static_assert(8 * (3 * 32 * 32) * 4 <= Cfg<2>::RINGS, "DIR1");
+static_assert(BN % 16 == 0 && BN <= ACC_COLS && 2 * ACC_COLS <= 512, "accumulator layout");
 // padded generator length and the bytes of its forward + reversed copies
 __host__ __device__ constexpr int gen_len(int n) { return (n + GEN_PAD + 7) / 8 * 8; }
 __host__ __device__ constexpr size_t gen_bytes(int n) { return (size_t)2 * gen_len(n) * 2; }
@@ -215,10 +227,10 @@ __device__ __forceinline__ void fence_before() {
 // (tile t[delta + r - k], nonzero for delta >= -256), acc 1 its transpose
 // (t[-delta + k - r], nonzero for delta <= 64); delta = out0 - k0.
 struct JobIter {
-  int out0, nk;
-  int kb = 0, sub = 0;
+  int out0, kb, kb_hi;  // K blocks kb .. kb_hi - 1 (this CTA's share of the K range)
+  int sub = 0;
   __device__ bool next(int& acc, int& k0, int& delta) {
-    while (kb < nk) {
+    while (kb < kb_hi) {
       k0 = kb * BK;
       delta = out0 - k0;
       const int s = sub;
@@ -253,6 +265,11 @@ struct KParams {
   int n1, n2;
   float inv_scale;
   int* err;
+  // split K: splits > 1 CTAs (blockIdx.z) share a tile's K blocks and write
+  // their partial products (coefficients applied, no mass term) to
+  // ws[(DIR * splits + z) * N ..]; a reduction adds the slices in order
+  int splits;
+  float* ws;
 };
 
 // DIR 0: x products (rows j, columns i); DIR 1: transposed y products.
@@ -265,39 +282,44 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
   using C = Cfg<NT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(base + C::STAGES * C::STAGE_BYTES);
-  uint64_t* fullA = bars;
-  uint64_t* fullB = bars + C::STAGES;
-  uint64_t* empty = bars + 2 * C::STAGES;
-  uint64_t* accbar = bars + 3 * C::STAGES;
+  uint64_t* bars = (uint64_t*)(base + C::RINGS);
+  uint64_t* fullA = bars;                 // X slot filled (TMA)      [SA]
+  uint64_t* emptyA = bars + C::SA;        // X slot free (MMAs done)  [SA]
+  uint64_t* fullW = bars + 2 * C::SA;     // generator windows landed [SA]
+  uint64_t* fullB = bars + 3 * C::SA;     // Toeplitz high term built [SB]
   // split precision: the low term of the Toeplitz operand gets its own "full"
   // barrier, so the two products that need only the high term can start
   // while the low term is still being synthesised
-  uint64_t* fullL = bars + 3 * C::STAGES + 1;
-  // generator windows of a stage landed (bulk copies issued by the producer)
-  uint64_t* fullW = bars + 4 * C::STAGES + 1;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 5 * C::STAGES + 1);
+  uint64_t* fullL = bars + 3 * C::SA + C::SB;
+  uint64_t* emptyB = bars + 3 * C::SA + 2 * C::SB;  // Toeplitz slot free [SB]
+  uint64_t* accbar = bars + 3 * C::SA + 3 * C::SB;
+  uint32_t* tmem_slot = (uint32_t*)(accbar + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  // generator window of stage s, term t (WIN 16-bit entries)
-  unsigned char* wins = base + C::STAGES * C::STAGE_BYTES + 256;
+  // generator window of X slot s, term t (WIN 16-bit entries)
+  unsigned char* wins = base + C::RINGS + 256;
   auto win = [&](int s, int t) { return wins + (s * NT + t) * WIN_BYTES; };
-  auto tileA = [&](int s, int t) { return base + s * C::STAGE_BYTES + t * A_BYTES; };
+  auto tileA = [&](int s, int t) { return base + s * C::A_STAGE + t * A_BYTES; };
   auto tileB = [&](int s, int t) {
-    return base + s * C::STAGE_BYTES + NT * A_BYTES + t * B_BYTES;
+    return base + C::SA * C::A_STAGE + s * C::B_STAGE + t * B_BYTES;
   };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // output tile: rows m0 .. m0+127 of the M dimension, columns out0 .. out0+255 of N
   const int out0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
   const int nk = DIR == 0 ? (kp.n1 + BK - 1) / BK : (kp.n2 + BK - 1) / BK;
+  const int kb_lo = (int)((long long)blockIdx.z * nk / kp.splits);
+  const int kb_hi = (int)((long long)(blockIdx.z + 1) * nk / kp.splits);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < C::STAGES; ++s) {
+    for (int s = 0; s < C::SA; ++s) {
       mbar_init(smem_u32(&fullA[s]), 1);
+      mbar_init(smem_u32(&emptyA[s]), 1);
+      mbar_init(smem_u32(&fullW[s]), 1);
+    }
+    for (int s = 0; s < C::SB; ++s) {
       mbar_init(smem_u32(&fullB[s]), NSYN);
       mbar_init(smem_u32(&fullL[s]), NSYN);
-      mbar_init(smem_u32(&fullW[s]), 1);
-      mbar_init(smem_u32(&empty[s]), 1);
+      mbar_init(smem_u32(&emptyB[s]), 1);
     }
     mbar_init(smem_u32(accbar), 1);
     *abort_flag = 0;
@@ -318,13 +340,13 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      JobIter it{out0, nk};
+      JobIter it{out0, kb_lo, kb_hi};
       int acc, k0, delta, n = 0;
       uint32_t issued_mask = 0, parity_mask = 0;
       while (!*abort_flag && it.next(acc, k0, delta)) {
-        const int s = n % C::STAGES;
-        const uint32_t ph = (uint32_t)(n / C::STAGES) & 1u;
-        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag)) break;
+        const int s = n % C::SA;
+        const uint32_t ph = (uint32_t)(n / C::SA) & 1u;
+        if (!mbar_wait(smem_u32(&emptyA[s]), ph ^ 1u, abort_flag)) break;
         {
           // the generator windows this job's Toeplitz tiles are built from
           const int nn = DIR == 0 ? kp.n1 : kp.n2;
@@ -351,7 +373,7 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
         ++n;
       }
       const uint64_t t0 = global_ns();  // every issued copy lands before the CTA exits
-      for (int s = 0; s < C::STAGES; ++s)
+      for (int s = 0; s < C::SA; ++s)
         if (issued_mask & (1u << s)) {
           while (!mbar_try(smem_u32(&fullA[s]), (parity_mask >> s) & 1u))
             if (global_ns() - t0 > 1000000000ull) break;
@@ -362,27 +384,27 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      JobIter it{out0, nk};
+      JobIter it{out0, kb_lo, kb_hi};
       int acc, k0, delta, n = 0;
       bool started[2] = {false, false};
       while (!*abort_flag && it.next(acc, k0, delta)) {
-        const int s = n % C::STAGES;
-        const uint32_t ph = (uint32_t)(n / C::STAGES) & 1u;
+        const int s = n % C::SA, sb = n % C::SB;
+        const uint32_t ph = (uint32_t)(n / C::SA) & 1u, phb = (uint32_t)(n / C::SB) & 1u;
         if (!mbar_wait(smem_u32(&fullA[s]), ph, abort_flag)) break;
-        if (!mbar_wait(smem_u32(&fullB[s]), ph, abort_flag)) break;
+        if (!mbar_wait(smem_u32(&fullB[sb]), phb, abort_flag)) break;
         fence_after();
-        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        const uint32_t d = tmem + (uint32_t)(acc * ACC_COLS);
         // (A term, B term) pairs: hi*hi and lo*hi need only the high Toeplitz
         // term; hi*lo waits for the low term
 #pragma unroll
         for (int p = 0; p < (NT == 1 ? 1 : 3); ++p) {
           if (p == 2) {
-            if (!mbar_wait(smem_u32(&fullL[s]), ph, abort_flag)) break;
+            if (!mbar_wait(smem_u32(&fullL[sb]), phb, abort_flag)) break;
             fence_after();
           }
           const int ta = p == 1 ? 1 : 0, tb = p == 2 ? 1 : 0;
           const uint32_t aA = smem_u32(tileA(s, ta));
-          const uint32_t aB = smem_u32(tileB(s, tb));
+          const uint32_t aB = smem_u32(tileB(sb, tb));
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t da = DIR == 0 ? smem_desc(aA + kk * 32, 16, 1024)
@@ -393,7 +415,8 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
         }
         if (*abort_flag) break;
         started[acc] = true;
-        mma_commit(smem_u32(&empty[s]));
+        mma_commit(smem_u32(&emptyA[s]));
+        mma_commit(smem_u32(&emptyB[sb]));
         ++n;
       }
       mma_commit(smem_u32(accbar));  // completes when every MMA above has completed
@@ -406,14 +429,14 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
       // operands (its 32 rows or columns x 128 of the tile) into L2 now, so the
       // epilogue reads them from L2 instead of waiting on DRAM
       const int g = warp & 3;
-      const int c_lo = (w >> 2) * (BN / 2);
+      const int c_lo = (w >> 2) ? BH : 0, c_w = (w >> 2) ? BN - BH : BH;
       auto pf = [](const float* a) { asm volatile("prefetch.global.L2 [%0];" ::"l"(a)); };
       if (DIR == 0) {
-        // rows rbase + lane, columns out0 + c_lo .. + 127: four 128-byte lines per row
+        // rows rbase + lane, this warp's columns of the tile: 128-byte lines per row
         const int row = m0 + g * 32 + lane;
         if (row < kp.n2) {
           const int c0i = out0 + c_lo;
-          const int c1i = min(kp.n1, c0i + BN / 2) - 1;
+          const int c1i = min(kp.n1, c0i + c_w) - 1;
           if (c0i <= c1i) {
             const size_t rb = (size_t)row * kp.n1;
             for (int c = c0i; c <= c1i + 31; c += 32) {
@@ -425,9 +448,9 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
           }
         }
       } else {
-        // rows out0 + c_lo .. + 127, columns m0 + g * 32 .. + 31: one line per row
+        // this warp's rows of the (transposed) tile, columns m0 + g * 32 .. + 31
         const int col = min(m0 + g * 32, kp.n1 - 1);
-        for (int r = lane; r < BN / 2; r += 32) {
+        for (int r = lane; r < c_w; r += 32) {
           const int row = out0 + c_lo + r;
           if (row < kp.n2) {
             const size_t e = (size_t)row * kp.n1 + col;
@@ -439,13 +462,14 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
       }
     }
     {
-      JobIter it{out0, nk};
+      JobIter it{out0, kb_lo, kb_hi};
       int acc, k0, delta, n = 0;
       while (!*abort_flag && it.next(acc, k0, delta)) {
-        const int s = n % C::STAGES;
-        const uint32_t ph = (uint32_t)(n / C::STAGES) & 1u;
-        // the window arrives after the MMAs released the stage (the producer
-        // waits for that before issuing it)
+        const int s = n % C::SA, sb = n % C::SB;
+        const uint32_t ph = (uint32_t)(n / C::SA) & 1u, phb = (uint32_t)(n / C::SB) & 1u;
+        // the Toeplitz slot is free once the MMAs of job n - SB completed; the
+        // job's generator window was prefetched with its X tiles
+        if (!warp_wait(smem_u32(&emptyB[sb]), phb ^ 1u, abort_flag)) break;
         if (!warp_wait(smem_u32(&fullW[s]), ph, abort_flag)) break;
         // row r, 16-byte chunk c (k = 8c .. 8c+7) of the tile: acc 0 needs
         // t[delta + r - k] = reversed[(n + GEN_OFF) - delta - r + k], acc 1 needs
@@ -461,10 +485,9 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
         // row u then starts 7 - u entries in -- a compile-time word and shift.
         for (int t = 0; t < NT; ++t) {
           const uint32_t* g32 = reinterpret_cast<const uint32_t*>(win(s, t));
-          unsigned char* B = tileB(s, t);
-#pragma unroll
-          for (int it = 0; it < (BN / 8) * 8 / (NSYN * 32); ++it) {
-            const int unit = it * (NSYN * 32) + w * 32 + lane;  // (row block, chunk)
+          unsigned char* B = tileB(sb, t);
+          for (int unit = w * 32 + lane; unit < (BN / 8) * 8; unit += NSYN * 32) {
+            // (row block, chunk)
             const int rb = unit >> 3, c = unit & 7;
             const int r0 = rb * 8;
             const int e0 = base0 - r0 + 8 * c;
@@ -494,14 +517,16 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMA
           __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(t == 0 ? &fullB[s] : &fullL[s]));
+          if (lane == 0) mbar_arrive(smem_u32(t == 0 ? &fullB[sb] : &fullL[sb]));
         }
         ++n;
       }
     }
     // ------------------------------------------------------------ epilogue
     const int g = warp & 3;          // TMEM lane group this warp may access
-    const int c_lo = (w >> 2) * (BN / 2), c_hi = c_lo + BN / 2;  // its half of the columns
+    // its part of the columns: [0, BH) or [BH, BN); the last 32-column block of
+    // the upper part is partial (BN = 240)
+    const int c_lo = (w >> 2) ? BH : 0, c_hi = (w >> 2) ? BN : BH;
     int okw = 1;
     if (lane == 0) {
       const uint64_t t0 = global_ns();
@@ -515,6 +540,17 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
     fence_after();
     if (ok && !*abort_flag) {
       const uint32_t tl = tmem + ((uint32_t)(g * 32) << 16);
+      // an accumulator none of this CTA's jobs wrote (possible with split K)
+      // holds no product: it reads as zero
+      float on[2] = {0.f, 0.f};
+      {
+        JobIter it{out0, kb_lo, kb_hi};
+        int acc, k0, delta;
+        while (it.next(acc, k0, delta)) on[acc] = 1.f;
+      }
+      const bool split = kp.splits > 1;
+      float* __restrict__ wsl =
+          split ? kp.ws + ((size_t)DIR * kp.splits + blockIdx.z) * ((size_t)kp.n1 * kp.n2) : nullptr;
       // The freed pipeline stages hold the epilogue's operands: each lane
       // copies its elements of a block with 4-byte cp.async (rows of a length
       // that is no multiple of 16 bytes rule out bulk copies), so all of a
@@ -527,19 +563,20 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
         float* stg = reinterpret_cast<float*>(base) + w * (2 * 32 * 33);
         constexpr int RB = NT == 2 ? 32 : 16;  // rows per batch of copies (fits the stages)
         float* opd = reinterpret_cast<float*>(base) + NSYN * (2 * 32 * 33) + w * (3 * RB * 32);
-        const float* __restrict__ Mm = kp.M;
+        const float* __restrict__ Mm = split ? nullptr : kp.M;
+        float* __restrict__ dst = split ? wsl : out;
         const int rbase = m0 + g * 32;
         const int nr = kp.n2 - rbase < 32 ? kp.n2 - rbase : 32;
         for (int cb = c_lo; cb < c_hi; cb += 32) {
           const int col = out0 + cb + lane;
-          const bool live = col < kp.n1;
+          const bool live = col < kp.n1 && cb + lane < BN;
 #pragma unroll
           for (int a = 0; a < 2; ++a) {
             float v[32];
-            tmem_ld32(tl + a * BN + cb, v);
+            tmem_ld32(tl + a * ACC_COLS + cb, v);
             tmem_wait_ld();
 #pragma unroll
-            for (int q = 0; q < 32; ++q) stg[(a * 32 + lane) * 33 + q] = v[q];
+            for (int q = 0; q < 32; ++q) stg[(a * 32 + lane) * 33 + q] = on[a] * v[q];
           }
           __syncwarp();
 #pragma unroll
@@ -556,7 +593,7 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
               for (int rr = 0; rr < RB && h + rr < nr; ++rr) {
                 const size_t idx = (size_t)(rbase + h + rr) * kp.n1 + col;
                 const float m = Mm ? opd[(2 * RB + rr) * 32 + lane] : 0.f;
-                out[idx] = kp.inv_scale * (opd[(0 * RB + rr) * 32 + lane] * stg[(h + rr) * 33 + lane] +
+                dst[idx] = kp.inv_scale * (opd[(0 * RB + rr) * 32 + lane] * stg[(h + rr) * 33 + lane] +
                                            opd[(1 * RB + rr) * 32 + lane] *
                                                stg[(32 + h + rr) * 33 + lane]) +
                            kp.cm * m;
@@ -570,17 +607,18 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
         const int col = m0 + g * 32 + lane;
         const bool live = col < kp.n1;
         for (int cb = c_lo; cb < c_hi; cb += 32) {
-          const int nr = kp.n2 - (out0 + cb) < 32 ? kp.n2 - (out0 + cb) : 32;
+          int nr = kp.n2 - (out0 + cb) < 32 ? kp.n2 - (out0 + cb) : 32;
+          if (nr > BN - cb) nr = BN - cb;
           if (live)
             for (int q = 0; q < nr; ++q) {
               const size_t idx = (size_t)(out0 + cb + q) * kp.n1 + col;
               cp_async4(opd + (0 * 32 + q) * 32 + lane, c0 + idx);
               cp_async4(opd + (1 * 32 + q) * 32 + lane, c1 + idx);
-              cp_async4(opd + (2 * 32 + q) * 32 + lane, out + idx);
+              if (!split) cp_async4(opd + (2 * 32 + q) * 32 + lane, out + idx);
             }
           float a0[32], a1[32];
           tmem_ld32(tl + cb, a0);
-          tmem_ld32(tl + BN + cb, a1);
+          tmem_ld32(tl + ACC_COLS + cb, a1);
           tmem_wait_ld();
           cp_async_wait_all();
           if (live) {
@@ -588,9 +626,10 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
             for (int q = 0; q < 32; ++q) {
               if (q < nr) {
                 const size_t idx = (size_t)(out0 + cb + q) * kp.n1 + col;
-                out[idx] = opd[(2 * 32 + q) * 32 + lane] +
-                           kp.inv_scale * (opd[(0 * 32 + q) * 32 + lane] * a0[q] +
-                                           opd[(1 * 32 + q) * 32 + lane] * a1[q]);
+                const float prod = kp.inv_scale * (opd[(0 * 32 + q) * 32 + lane] * on[0] * a0[q] +
+                                                   opd[(1 * 32 + q) * 32 + lane] * on[1] * a1[q]);
+                if (split) wsl[idx] = prod;
+                else out[idx] = opd[(2 * 32 + q) * 32 + lane] + prod;
               }
             }
           }
@@ -648,6 +687,18 @@ __global__ void pack_kernel(const float* __restrict__ X, int n1, int n2, int ld,
     const H h = to_h<H>(v);
     hi[(size_t)j * ld + i] = h;
     if (lo) lo[(size_t)j * ld + i] = to_h<H>(v - from_h<H>(h));
+  }
+}
+
+// kx = cm M + sum over both directions and every split of the partial
+// products, in a fixed order
+__global__ void split_reduce_kernel(const float* __restrict__ ws, int splits, size_t N,
+                                    const float* __restrict__ M, float cm, float* __restrict__ kx) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float v = M ? cm * M[i] : 0.f;
+    for (int q = 0; q < 2 * splits; ++q) v += ws[(size_t)q * N + i];
+    kx[i] = v;
   }
 }
 
@@ -772,6 +823,22 @@ int level_create(ToeplitzGemmLevel* L, int n1, int n2, int prec, bool mass) {
     if (cudaFuncSetAttribute(kfun[k], cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
         cudaSuccess)
       return 12;
+  // split K when the tiles of a launch leave most SMs idle (e.g. n = 1023:
+  // 5 x 8 tiles per direction): up to 4 CTAs per tile, each with at least
+  // four K blocks
+  {
+    const int t0 = ((n1 + BN - 1) / BN) * ((n2 + BM - 1) / BM);
+    const int t1 = ((n2 + BN - 1) / BN) * ((n1 + BM - 1) / BM);
+    const int tiles = t0 > t1 ? t0 : t1;
+    const int nk = ((n1 < n2 ? n1 : n2) + BK - 1) / BK;
+    int sp = 152 / tiles;
+    if (sp > 4) sp = 4;
+    if (sp > nk / 4) sp = nk / 4;
+    L->splits = sp > 1 ? sp : 1;
+    if (L->splits > 1 &&
+        cudaMalloc(&L->ws, (size_t)2 * L->splits * n1 * n2 * sizeof(float)) != cudaSuccess)
+      return 1;
+  }
   L->built = true;
   return 0;
 }
@@ -807,13 +874,15 @@ static void launch_dir(ToeplitzGemmLevel* L, Maps* m, int dir, const float* M, d
   kp.out = kx;
   kp.c0 = c0;
   kp.c1 = c1;
+  kp.splits = L->splits;
+  kp.ws = L->ws;
   if (dir == 0) {
     // x products: kx = cm M + dp (X A_x^T) + dm (X A_x)
     kp.M = M;
     kp.gen_hi = (const uint16_t*)m->genx_hi;
     kp.gen_lo = (const uint16_t*)(NT == 2 ? m->genx_lo : m->genx_hi);
     kp.glen = m->glen_x;
-    dim3 gx((L->n1 + BN - 1) / BN, (L->n2 + BM - 1) / BM);
+    dim3 gx((L->n1 + BN - 1) / BN, (L->n2 + BM - 1) / BM, L->splits);
     toeplitz_gemm_kernel<0, NT><<<gx, NUM_THREADS, Cfg<NT>::FIXED, st>>>(
         m->ax[0], m->ax[1], kp, make_idesc(false, f16));
   } else {
@@ -822,7 +891,7 @@ static void launch_dir(ToeplitzGemmLevel* L, Maps* m, int dir, const float* M, d
     kp.gen_hi = (const uint16_t*)m->geny_hi;
     kp.gen_lo = (const uint16_t*)(NT == 2 ? m->geny_lo : m->geny_hi);
     kp.glen = m->glen_y;
-    dim3 gy((L->n2 + BN - 1) / BN, (L->n1 + BM - 1) / BM);
+    dim3 gy((L->n2 + BN - 1) / BN, (L->n1 + BM - 1) / BM, L->splits);
     toeplitz_gemm_kernel<1, NT><<<gy, NUM_THREADS, Cfg<NT>::FIXED, st>>>(
         m->ay[0], m->ay[1], kp, make_idesc(true, f16));
   }
@@ -860,6 +929,16 @@ int level_gemm(ToeplitzGemmLevel* L, int dir, const float* M, double cm, const f
   return cudaGetLastError() == cudaSuccess ? 0 : 31;
 }
 
+int level_finish(ToeplitzGemmLevel* L, const float* M, double cm, float* kx, cudaStream_t st) {
+  if (!L->built) return 30;
+  if (L->splits <= 1) return 0;
+  const size_t N = (size_t)L->n1 * L->n2;
+  int g = (int)((N + 255) / 256);
+  if (g > 152 * 8) g = 152 * 8;
+  split_reduce_kernel<<<g, 256, 0, st>>>(L->ws, L->splits, N, M, (float)cm, kx);
+  return cudaGetLastError() == cudaSuccess ? 0 : 31;
+}
+
 int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y, const float* M,
                    double cm, const float* dp, const float* dm, const float* ep, const float* em,
                    float* kx, cudaStream_t st) {
@@ -867,7 +946,9 @@ int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y,
   if (r) return r;
   r = level_gemm(L, 0, M, cm, dp, dm, kx, st);
   if (r) return r;
-  return level_gemm(L, 1, nullptr, 0.0, ep, em, kx, st);
+  r = level_gemm(L, 1, nullptr, 0.0, ep, em, kx, st);
+  if (r) return r;
+  return level_finish(L, M, cm, kx, st);
 }
 
 int level_error(ToeplitzGemmLevel* L, cudaStream_t st) {
@@ -898,6 +979,8 @@ void level_destroy(ToeplitzGemmLevel* L) {
     cudaFree(m->geny_lo);
     delete m;
   }
+  cudaFree(L->ws);
+  L->ws = nullptr;
   cudaFree(L->xa);
   cudaFree(L->xa_lo);
   cudaFree(L->xb);

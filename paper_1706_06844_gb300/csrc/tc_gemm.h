@@ -26,6 +26,8 @@ struct ToeplitzGemmLevel {
   void* xb = nullptr;     // 16-bit copy of the y-product operand (structured-Galerkin levels)
   void* xb_lo = nullptr;
   void* maps = nullptr;   // tensor maps, generator copies, error flag
+  int splits = 1;         // CTAs sharing a tile's K range (small levels)
+  float* ws = nullptr;    // their partial products: 2 * splits * n1 * n2
 };
 
 // returns 0 on success
@@ -45,6 +47,9 @@ int level_products(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y,
 int level_pack(ToeplitzGemmLevel* L, const float* xin_x, const float* xin_y, cudaStream_t st);
 int level_gemm(ToeplitzGemmLevel* L, int dir, const float* M, double cm, const float* c0,
                const float* c1, float* kx, cudaStream_t st);
+// after both directions: with split K, kx = cm * M + the partial products of
+// every split (fixed order); nothing otherwise
+int level_finish(ToeplitzGemmLevel* L, const float* M, double cm, float* kx, cudaStream_t st);
 // 1 if a capped wait of the level's kernels gave up since the last call (the flag
 // is then cleared), 0 if not, -1 if the flag could not be read; syncs `st`
 int level_error(ToeplitzGemmLevel* L, cudaStream_t st);

@@ -29,10 +29,11 @@ def _abs_level(lev, X):
 
 @pytest.mark.parametrize("precision", [fde.FDE_PREC_BF16, fde.FDE_PREC_FP16, fde.FDE_PREC_BF16X3])
 @pytest.mark.parametrize("precond", [fde.FDE_PRECOND_MG_SG, fde.FDE_PRECOND_MG_REDISC])
-@pytest.mark.parametrize("n1,n2", [(255, 255), (511, 255), (383, 767)])
+@pytest.mark.parametrize("n1,n2", [(255, 255), (511, 255), (383, 767), (511, 511), (1023, 1023)])
 def test_gemm_level_apply(precision, precond, n1, n2):
-    # every level the tensor path serves (n >= 127), incl. ragged tiles (383 = 2*128+127)
-    # and the structured-Galerkin mass terms of coarse levels
+    # every level the tensor path serves (n >= 127), incl. ragged tiles (383 = 240+143),
+    # the structured-Galerkin mass terms of coarse levels, and split K (tiles
+    # of 511 and 1023 leave most SMs idle: 2 and 3 CTAs share a tile's K range)
     import torch
     if (n1 - 1) // 2 % 2 == 0 and n1 > 255:
         pytest.skip("level sizes must stay odd")
