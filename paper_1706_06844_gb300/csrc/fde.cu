@@ -421,10 +421,11 @@ int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
     CCHK(cudaMemsetAsync(h->Z, 0, h->ldv * (size_t)p.restart * sizeof(double), h->st));
     h->nb = krylov_blocks();
     RCHK(h->alloc(&h->part, (size_t)h->nb * (p.restart + 2)));
-    RCHK(h->alloc(&h->hdev, p.restart + 4));
+    // the first Gram-Schmidt pass writes KMAX + 1 <= 33 sums (projections, ||w||^2)
+    RCHK(h->alloc(&h->hdev, std::max(p.restart + 4, 40)));
     RCHK(h->alloc(&h->h2dev, p.restart + 4));
     RCHK(h->alloc(&h->ydev, p.restart + 4));
-    RCHK(h->alloc(&h->cgs_part, (size_t)cgs_blocks() * 32 + 8));
+    RCHK(h->alloc(&h->cgs_part, (size_t)cgs_blocks() * 34 + 8));
     RCHK(h->alloc(&h->tickets, 4));
     CCHK(cudaMemsetAsync(h->tickets, 0, 4 * sizeof(unsigned), h->st));
     {

@@ -301,15 +301,28 @@ __device__ __forceinline__ double2 ld2(const double* p, size_t q) {
   return reinterpret_cast<const double2*>(p)[q];
 }
 
+// Re-orthogonalise only when the first projection removed most of w: with
+// h = V^T w and an orthonormal V, ||w - V h||^2 = ||w||^2 - ||h||^2; when that
+// keeps more than half of ||w||^2 (the classical "twice is enough" test with
+// the factor 1/sqrt(2)) one projection leaves w orthogonal to working
+// accuracy and the second pass is skipped.  ww = ||w||^2; the verdict goes to
+// status->pad (1: project twice).
+__device__ __forceinline__ int needs_second_projection(const double* h, int k, double ww) {
+  double hh = 0.0;
+  for (int i = 0; i < k; ++i) hh = fma(h[i], h[i], hh);
+  return (ww - hh > 0.5 * ww) ? 0 : 1;
+}
+
 template <int KMAX>
 __global__ void __launch_bounds__(CT) cgs_project_kernel(const double* __restrict__ V, size_t ldv,
                                                          int k, const double* __restrict__ w,
                                                          size_t n2, double* part, int nb,
-                                                         unsigned* ticket, double* h) {
-  __shared__ double sred[KMAX * (CT / 32)];
-  double acc[KMAX];
+                                                         unsigned* ticket, double* h,
+                                                         ArnoldiStatus* status) {
+  __shared__ double sred[(KMAX + 1) * (CT / 32)];
+  double acc[KMAX + 1];
 #pragma unroll
-  for (int g = 0; g < KMAX; ++g) acc[g] = 0.0;
+  for (int g = 0; g <= KMAX; ++g) acc[g] = 0.0;
   for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n2; q += (size_t)nb * CT) {
     const double2 wv = ld2(w, q);
 #pragma unroll
@@ -318,24 +331,56 @@ __global__ void __launch_bounds__(CT) cgs_project_kernel(const double* __restric
         const double2 v = ld2(V + (size_t)g * ldv, q);
         acc[g] = fma(v.x, wv.x, fma(v.y, wv.y, acc[g]));
       }
+    acc[KMAX] = fma(wv.x, wv.x, fma(wv.y, wv.y, acc[KMAX]));
   }
-  block_reduce_vec<KMAX>(acc, k, sred);
-  if (publish_partials(sred, k, part, nb, ticket)) {
-    final_sums(part, k, nb, h);
-    if (threadIdx.x == 0) *ticket = 0u;
+  // the KMAX + 1 sums (unused projections are zero, ||w||^2 last) in h[0 .. KMAX]
+  block_reduce_vec<KMAX + 1>(acc, KMAX + 1, sred);
+  if (publish_partials(sred, KMAX + 1, part, nb, ticket)) {
+    final_sums(part, KMAX + 1, nb, h);
+    if (threadIdx.x == 0) {
+      *ticket = 0u;
+      status->pad = needs_second_projection(h, k, h[KMAX]);
+    }
   }
 }
 
 // k in 17 .. 32: the same pass over scalar elements, so the KMAX values a
 // thread keeps for the second projection fit its registers
+__device__ void arnoldi_column(const ArnoldiState& st, int j, const double* h, const double* h2,
+                               double nrm2);
+
+// w -= V h, then either h2 = V^T w (second projection) or, when the first
+// projection sufficed, ||w||^2 and the Givens update of column j in the last block
 template <int KMAX>
 __global__ void __launch_bounds__(CT) cgs_subtract_project1_kernel(
     const double* __restrict__ V, size_t ldv, int k, const double* __restrict__ h, double* w,
-    size_t n, double* part, int nb, unsigned* ticket, double* h2) {
+    size_t n, double* part, int nb, unsigned* ticket, double* h2, ArnoldiState st, int j) {
   __shared__ double sred[KMAX * (CT / 32)];
   __shared__ double hs[KMAX];
+  __shared__ double nrm2;
   if ((int)threadIdx.x < KMAX) hs[threadIdx.x] = (int)threadIdx.x < k ? h[threadIdx.x] : 0.0;
   __syncthreads();
+  if (!st.status->pad) {
+    double a1[1] = {0.0};
+    for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n; q += (size_t)nb * CT) {
+      double wv = w[q];
+#pragma unroll
+      for (int g = 0; g < KMAX; ++g)
+        if (g < k) wv = fma(-hs[g], V[(size_t)g * ldv + q], wv);
+      w[q] = wv;
+      a1[0] = fma(wv, wv, a1[0]);
+    }
+    block_reduce_vec<1>(a1, 1, sred);
+    if (publish_partials(sred, 1, part, nb, ticket)) {
+      final_sums(part, 1, nb, &nrm2);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        *ticket = 0u;
+        arnoldi_column(st, j, h, nullptr, nrm2);
+      }
+    }
+    return;
+  }
   double acc[KMAX];
 #pragma unroll
   for (int g = 0; g < KMAX; ++g) acc[g] = 0.0;
@@ -360,15 +405,41 @@ __global__ void __launch_bounds__(CT) cgs_subtract_project1_kernel(
 template <int KMAX>
 __global__ void __launch_bounds__(CT) cgs_subtract_project_kernel(
     const double* __restrict__ V, size_t ldv, int k, const double* __restrict__ h, double* w,
-    size_t n2, double* part, int nb, unsigned* ticket, double* h2) {
+    size_t n2, double* part, int nb, unsigned* ticket, double* h2, ArnoldiState st, int j) {
   __shared__ double sred[KMAX * (CT / 32)];
   __shared__ double hs[KMAX];
+  __shared__ double nrm2;
   if ((int)threadIdx.x < KMAX) hs[threadIdx.x] = (int)threadIdx.x < k ? h[threadIdx.x] : 0.0;
   __syncthreads();
+  double2* w2 = reinterpret_cast<double2*>(w);
+  if (!st.status->pad) {
+    double a1[1] = {0.0};
+    for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n2; q += (size_t)nb * CT) {
+      double2 wv = w2[q];
+#pragma unroll
+      for (int g = 0; g < KMAX; ++g)
+        if (g < k) {
+          const double2 v = ld2(V + (size_t)g * ldv, q);
+          wv.x = fma(-hs[g], v.x, wv.x);
+          wv.y = fma(-hs[g], v.y, wv.y);
+        }
+      w2[q] = wv;
+      a1[0] = fma(wv.x, wv.x, fma(wv.y, wv.y, a1[0]));
+    }
+    block_reduce_vec<1>(a1, 1, sred);
+    if (publish_partials(sred, 1, part, nb, ticket)) {
+      final_sums(part, 1, nb, &nrm2);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        *ticket = 0u;
+        arnoldi_column(st, j, h, nullptr, nrm2);
+      }
+    }
+    return;
+  }
   double acc[KMAX];
 #pragma unroll
   for (int g = 0; g < KMAX; ++g) acc[g] = 0.0;
-  double2* w2 = reinterpret_cast<double2*>(w);
   for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n2; q += (size_t)nb * CT) {
     double2 v[KMAX];
 #pragma unroll
@@ -400,7 +471,7 @@ __device__ void arnoldi_column(const ArnoldiState& st, int j, const double* h, c
   double col[ArnoldiState::kMaxM + 1];
   int bad = 0;
   for (int i = 0; i <= j; ++i) {
-    col[i] = h[i] + h2[i];
+    col[i] = h2 ? h[i] + h2[i] : h[i];
     if (!isfinite(col[i])) bad = 1;
   }
   const double hnext = sqrt(nrm2);
@@ -433,6 +504,7 @@ __global__ void __launch_bounds__(CT) cgs_subtract_norm_kernel(
   __shared__ double sred[CT / 32];
   __shared__ double hs[KMAX];
   __shared__ double nrm2;
+  if (!st.status->pad) return;  // one projection sufficed: the previous pass closed the step
   if ((int)threadIdx.x < KMAX) hs[threadIdx.x] = (int)threadIdx.x < k ? h2[threadIdx.x] : 0.0;
   __syncthreads();
   double acc[1] = {0.0};
@@ -528,8 +600,9 @@ cudaError_t launch_cgs2(const double* V, size_t ldv, int k, double* w, size_t N,
     const int b1 = resident_blocks((const void*)cgs_project_kernel<KM>);                      \
     const int b2 = resident_blocks((const void*)SP<KM>);                                      \
     const int b3 = resident_blocks((const void*)cgs_subtract_norm_kernel<KM>);                \
-    cgs_project_kernel<KM><<<b1, CT, 0, s>>>(V, ldv, k, w, n2, part, b1, tickets, h);         \
-    SP<KM><<<b2, CT, 0, s>>>(V, ldv, k, h, w, SPN, part, b2, tickets + 1, h2);                \
+    cgs_project_kernel<KM><<<b1, CT, 0, s>>>(V, ldv, k, w, n2, part, b1, tickets, h,          \
+                                             st.status);                                      \
+    SP<KM><<<b2, CT, 0, s>>>(V, ldv, k, h, w, SPN, part, b2, tickets + 1, h2, st, j);         \
     cgs_subtract_norm_kernel<KM><<<b3, CT, 0, s>>>(V, ldv, k, h, h2, w, n2, part, b3,         \
                                                    tickets + 2, st, j);                       \
   }
@@ -604,7 +677,7 @@ template <int KMAX>
 __global__ void __launch_bounds__(CT) g_cgs_project_kernel(const GKrylov* __restrict__ ent,
                                                            const GItem* __restrict__ items,
                                                            int nitems, int j, GGate gate) {
-  __shared__ double sred[KMAX * (CT / 32)];
+  __shared__ double sred[(KMAX + 1) * (CT / 32)];
   const int k = j + 1;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const GItem g = items[it];
@@ -613,9 +686,9 @@ __global__ void __launch_bounds__(CT) g_cgs_project_kernel(const GKrylov* __rest
     size_t lo, hi;
     chunk_range(e, g.unit, lo, hi);
     const double* w = e.V + (size_t)(j + 1) * e.ldv;
-    double acc[KMAX];
+    double acc[KMAX + 1];
 #pragma unroll
-    for (int q = 0; q < KMAX; ++q) acc[q] = 0.0;
+    for (int q = 0; q <= KMAX; ++q) acc[q] = 0.0;
     for (size_t q = lo + threadIdx.x; q < hi; q += CT) {
       const double2 wv = ld2(w, q);
 #pragma unroll
@@ -624,22 +697,46 @@ __global__ void __launch_bounds__(CT) g_cgs_project_kernel(const GKrylov* __rest
           const double2 v = ld2(e.V + (size_t)gg * e.ldv, q);
           acc[gg] = fma(v.x, wv.x, fma(v.y, wv.y, acc[gg]));
         }
+      acc[KMAX] = fma(wv.x, wv.x, fma(wv.y, wv.y, acc[KMAX]));
     }
-    block_reduce_vec<KMAX>(acc, k, sred);
-    if (publish_partials_at(sred, k, e.part, e.nchunk, g.unit, e.tickets)) {
-      final_sums(e.part, k, e.nchunk, e.h);
-      if (threadIdx.x == 0) e.tickets[0] = 0u;
+    block_reduce_vec<KMAX + 1>(acc, KMAX + 1, sred);
+    if (publish_partials_at(sred, KMAX + 1, e.part, e.nchunk, g.unit, e.tickets)) {
+      final_sums(e.part, KMAX + 1, e.nchunk, e.h);
+      if (threadIdx.x == 0) {
+        e.tickets[0] = 0u;
+        e.st.status->pad = needs_second_projection(e.h, k, e.h[KMAX]);
+      }
     }
     __syncthreads();
   }
 }
 
+// close Arnoldi step j of problem e (one thread): Givens update, iteration
+// count, gates for the next step
+__device__ void grouped_close_step(const GKrylov& e, int j, const double* h2, double nrm2,
+                                   int* active, int* relax) {
+  const int k = j + 1;
+  arnoldi_column(e.st, j, e.h, h2, nrm2);
+  GSolveState& ss = *e.ss;
+  const ArnoldiStatus as = *e.st.status;
+  ss.its += 1;
+  ss.k = k;
+  if (as.nonfinite) ss.failed = 1;
+  const bool stop = as.gabs <= ss.tol || ss.its >= e.maxit || as.hnext == 0.0 || as.nonfinite ||
+                    k >= e.restart;
+  if (relax[e.prob]) ss.relaxed += 1;  // this step's matvec ran in FP32
+  active[e.prob] = stop ? 0 : 1;
+  relax[e.prob] = (e.relax_on && as.gabs <= FDE_RELAX_FACTOR * ss.tol) ? 1 : 0;
+}
+
 template <int KMAX>
 __global__ void __launch_bounds__(CT) g_cgs_subproj_kernel(const GKrylov* __restrict__ ent,
                                                            const GItem* __restrict__ items,
-                                                           int nitems, int j, GGate gate) {
+                                                           int nitems, int j, GGate gate,
+                                                           int* active, int* relax) {
   __shared__ double sred[KMAX * (CT / 32)];
   __shared__ double hs[KMAX];
+  __shared__ double nrm2;
   const int k = j + 1;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const GItem g = items[it];
@@ -650,6 +747,29 @@ __global__ void __launch_bounds__(CT) g_cgs_subproj_kernel(const GKrylov* __rest
     size_t lo, hi;
     chunk_range(e, g.unit, lo, hi);
     double* w = e.V + (size_t)(j + 1) * e.ldv;
+    if (!e.st.status->pad) {
+      // one projection sufficed: w -= V h, ||w||^2, and this pass closes the step
+      double a1[1] = {0.0};
+      for (size_t q = 2 * lo + threadIdx.x; q < 2 * hi; q += CT) {
+        double wv = w[q];
+#pragma unroll
+        for (int gg = 0; gg < KMAX; ++gg)
+          if (gg < k) wv = fma(-hs[gg], e.V[(size_t)gg * e.ldv + q], wv);
+        w[q] = wv;
+        a1[0] = fma(wv, wv, a1[0]);
+      }
+      block_reduce_vec<1>(a1, 1, sred);
+      if (publish_partials_at(sred, 1, e.part, e.nchunk, g.unit, e.tickets + 1)) {
+        final_sums(e.part, 1, e.nchunk, &nrm2);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          e.tickets[1] = 0u;
+          grouped_close_step(e, j, nullptr, nrm2, active, relax);
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     double acc[KMAX];
 #pragma unroll
     for (int q = 0; q < KMAX; ++q) acc[q] = 0.0;
@@ -686,6 +806,8 @@ __global__ void __launch_bounds__(CT) g_cgs_subnorm_kernel(const GKrylov* __rest
     const GItem g = items[it];
     const GKrylov& e = ent[g.e];
     if (!gate_open(gate, e.prob, -1)) continue;
+    // a problem whose first projection sufficed closed its step in the previous pass
+    if (!e.st.status->pad) continue;
     if ((int)threadIdx.x < KMAX) hs[threadIdx.x] = (int)threadIdx.x < k ? e.h2[threadIdx.x] : 0.0;
     __syncthreads();
     size_t lo, hi;
@@ -710,17 +832,7 @@ __global__ void __launch_bounds__(CT) g_cgs_subnorm_kernel(const GKrylov* __rest
       __syncthreads();
       if (threadIdx.x == 0) {
         e.tickets[2] = 0u;
-        arnoldi_column(e.st, j, e.h, e.h2, nrm2);
-        GSolveState& ss = *e.ss;
-        const ArnoldiStatus as = *e.st.status;
-        ss.its += 1;
-        ss.k = k;
-        if (as.nonfinite) ss.failed = 1;
-        const bool stop = as.gabs <= ss.tol || ss.its >= e.maxit || as.hnext == 0.0 ||
-                          as.nonfinite || k >= e.restart;
-        if (relax[e.prob]) ss.relaxed += 1;  // this step's matvec ran in FP32
-        active[e.prob] = stop ? 0 : 1;
-        relax[e.prob] = (e.relax_on && as.gabs <= FDE_RELAX_FACTOR * ss.tol) ? 1 : 0;
+        grouped_close_step(e, j, e.h2, nrm2, active, relax);
       }
     }
     __syncthreads();
@@ -902,7 +1014,7 @@ cudaError_t launch_g_cgs2(const GKrylov* ent, const GItem* items, int nitems, in
     g_cgs_project_kernel<KM><<<g_grid(nitems, (const void*)g_cgs_project_kernel<KM>), CT, 0,  \
                                st>>>(ent, items, nitems, j, gate);                            \
     g_cgs_subproj_kernel<KM><<<g_grid(nitems, (const void*)g_cgs_subproj_kernel<KM>), CT, 0,  \
-                               st>>>(ent, items, nitems, j, gate);                            \
+                               st>>>(ent, items, nitems, j, gate, active, relax);             \
     g_cgs_subnorm_kernel<KM><<<g_grid(nitems, (const void*)g_cgs_subnorm_kernel<KM>), CT, 0,  \
                                st>>>(ent, items, nitems, j, gate, active, relax);             \
   }
