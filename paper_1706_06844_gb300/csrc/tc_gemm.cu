@@ -43,20 +43,17 @@
 namespace fde {
 namespace tc {
 
-// Output tiles of 128 x 128 and two CTAs per SM: each CTA holds its two
-// accumulators in 256 TMEM columns and ~100 KB of shared memory, so while one
-// CTA runs its epilogue (coefficient loads and output stores, a third of a
-// tile's time) or waits on its pipeline barriers, the other keeps the tensor
-// core busy.  At n = 2047 a launch has 16 x 16 = 256 CTAs for 304 slots.
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int ACC_COLS = 128;          // TMEM columns between the two accumulators
-constexpr int BH = 64;                 // epilogue column split: [0, BH) and [BH, BN)
-constexpr int CTAS_PER_SM = 2;
+// Output tiles of 128 x 240: at n = 2047 a launch has 9 x 16 = 144 CTAs for
+// the 152 SMs (256-wide tiles would leave 24 idle), and the smaller Toeplitz
+// operand leaves room for a third X-tile stage.
+constexpr int BM = 128, BN = 240, BK = 64;
+constexpr int ACC_COLS = 256;          // TMEM columns between the two accumulators
+constexpr int BH = 128;                // epilogue column split: [0, BH) and [BH, BN)
 constexpr int A_BYTES = BM * BK * 2;   // 16 KB
-constexpr int B_BYTES = BN * BK * 2;   // 16 KB
+constexpr int B_BYTES = BN * BK * 2;   // 30 KB
 constexpr int NUM_THREADS = 320;  // 2 + 8 warps
 constexpr int NSYN = 8;            // synthesis / epilogue warps
-constexpr uint32_t TMEM_COLS = 256;  // per CTA; two CTAs per SM share the 512
+constexpr uint32_t TMEM_COLS = 512;
 constexpr int GEN_OFF = 320;           // zero padding in front of the generator copy
 constexpr int GEN_PAD = 1024;          // total padding elements
 // A job's Toeplitz tile reads generator entries base0 - 255 .. base0 + 68 of
@@ -72,9 +69,8 @@ constexpr int WIN_BYTES = WIN * 2;     // 672: a multiple of 16
 // a Toeplitz slot likewise.
 template <int NT>
 struct Cfg {
-  // two CTAs per SM: at most ~112 KB of shared memory each
-  static constexpr int SA = NT == 1 ? 3 : 2;
-  static constexpr int SB = NT == 1 ? 3 : 1;
+  static constexpr int SA = NT == 1 ? 4 : 3;
+  static constexpr int SB = NT == 1 ? 3 : 2;
   static constexpr int A_STAGE = NT * A_BYTES;  // 1 KB multiples
   static constexpr int B_STAGE = NT * B_BYTES;
   static constexpr int RINGS = SA * A_STAGE + SB * B_STAGE;
@@ -83,14 +79,10 @@ struct Cfg {
 };
 // epilogue staging (DIR 0: transposed accumulators + operand batches; DIR 1:
 // operand blocks) must fit in the pipeline stages it reuses
-constexpr int EPI_RB = 8;  // rows per batch of the epilogue's operand copies
-static_assert(8 * (2 * 32 * 33 + 3 * EPI_RB * 32) * 4 <= Cfg<1>::RINGS, "NT=1 DIR0");
-static_assert(8 * (2 * 32 * 33 + 3 * EPI_RB * 32) * 4 <= Cfg<2>::RINGS, "NT=2 DIR0");
-static_assert(8 * (3 * EPI_RB * 32) * 4 <= Cfg<2>::RINGS, "DIR1");
-static_assert(BN % 16 == 0 && BN <= ACC_COLS && 2 * ACC_COLS <= (int)TMEM_COLS, "accumulators");
-static_assert(CTAS_PER_SM * (Cfg<2>::FIXED + 1024) <= 228 * 1024 &&
-                  CTAS_PER_SM * (Cfg<1>::FIXED + 1024) <= 228 * 1024,
-              "two CTAs per SM");
+static_assert(8 * (2 * 32 * 33 + 3 * 16 * 32) * 4 <= Cfg<1>::RINGS, "NT=1 DIR0");
+static_assert(8 * (2 * 32 * 33 + 3 * 32 * 32) * 4 <= Cfg<2>::RINGS, "NT=2 DIR0");
+static_assert(8 * (3 * 32 * 32) * 4 <= Cfg<2>::RINGS, "DIR1");
+static_assert(BN % 16 == 0 && BN <= ACC_COLS && 2 * ACC_COLS <= 512, "accumulator layout");
 // padded generator length and the bytes of its forward + reversed copies
 __host__ __device__ constexpr int gen_len(int n) { return (n + GEN_PAD + 7) / 8 * 8; }
 __host__ __device__ constexpr size_t gen_bytes(int n) { return (size_t)2 * gen_len(n) * 2; }
@@ -283,7 +275,7 @@ struct KParams {
 // DIR 0: x products (rows j, columns i); DIR 1: transposed y products.
 // NT: number of 16-bit terms per operand (1, or 2 for the 3-product split).
 template <int DIR, int NT>
-__global__ void __launch_bounds__(NUM_THREADS, CTAS_PER_SM)
+__global__ void __launch_bounds__(NUM_THREADS, 1)
 toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
                      const __grid_constant__ CUtensorMap mapA_lo, const KParams kp,
                      uint32_t idesc) {
@@ -569,7 +561,7 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
       if (DIR == 0) {
         // lanes are grid rows in TMEM: stage through shared memory so lane = column
         float* stg = reinterpret_cast<float*>(base) + w * (2 * 32 * 33);
-        constexpr int RB = EPI_RB;  // rows per batch of copies (fits the rings)
+        constexpr int RB = NT == 2 ? 32 : 16;  // rows per batch of copies (fits the stages)
         float* opd = reinterpret_cast<float*>(base) + NSYN * (2 * 32 * 33) + w * (3 * RB * 32);
         const float* __restrict__ Mm = split ? nullptr : kp.M;
         float* __restrict__ dst = split ? wsl : out;
@@ -611,40 +603,35 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
         }
       } else {
         // lanes are grid columns i; TMEM columns are grid rows j
-        float* opd = reinterpret_cast<float*>(base) + w * (3 * EPI_RB * 32);
+        float* opd = reinterpret_cast<float*>(base) + w * (3 * 32 * 32);
         const int col = m0 + g * 32 + lane;
         const bool live = col < kp.n1;
         for (int cb = c_lo; cb < c_hi; cb += 32) {
           int nr = kp.n2 - (out0 + cb) < 32 ? kp.n2 - (out0 + cb) : 32;
           if (nr > BN - cb) nr = BN - cb;
+          if (live)
+            for (int q = 0; q < nr; ++q) {
+              const size_t idx = (size_t)(out0 + cb + q) * kp.n1 + col;
+              cp_async4(opd + (0 * 32 + q) * 32 + lane, c0 + idx);
+              cp_async4(opd + (1 * 32 + q) * 32 + lane, c1 + idx);
+              if (!split) cp_async4(opd + (2 * 32 + q) * 32 + lane, out + idx);
+            }
           float a0[32], a1[32];
           tmem_ld32(tl + cb, a0);
           tmem_ld32(tl + ACC_COLS + cb, a1);
           tmem_wait_ld();
+          cp_async_wait_all();
+          if (live) {
 #pragma unroll
-          for (int hb = 0; hb < 32; hb += EPI_RB) {
-            if (live)
-              for (int q = 0; q < EPI_RB && hb + q < nr; ++q) {
-                const size_t idx = (size_t)(out0 + cb + hb + q) * kp.n1 + col;
-                cp_async4(opd + (0 * EPI_RB + q) * 32 + lane, c0 + idx);
-                cp_async4(opd + (1 * EPI_RB + q) * 32 + lane, c1 + idx);
-                if (!split) cp_async4(opd + (2 * EPI_RB + q) * 32 + lane, out + idx);
-              }
-            cp_async_wait_all();
-            if (live) {
-#pragma unroll
-              for (int q = 0; q < EPI_RB; ++q) {
-                if (hb + q < nr) {
-                  const size_t idx = (size_t)(out0 + cb + hb + q) * kp.n1 + col;
-                  const float prod =
-                      kp.inv_scale * (opd[(0 * EPI_RB + q) * 32 + lane] * on[0] * a0[hb + q] +
-                                      opd[(1 * EPI_RB + q) * 32 + lane] * on[1] * a1[hb + q]);
-                  if (split) wsl[idx] = prod;
-                  else out[idx] = opd[(2 * EPI_RB + q) * 32 + lane] + prod;
-                }
+            for (int q = 0; q < 32; ++q) {
+              if (q < nr) {
+                const size_t idx = (size_t)(out0 + cb + q) * kp.n1 + col;
+                const float prod = kp.inv_scale * (opd[(0 * 32 + q) * 32 + lane] * on[0] * a0[q] +
+                                                   opd[(1 * 32 + q) * 32 + lane] * on[1] * a1[q]);
+                if (split) wsl[idx] = prod;
+                else out[idx] = opd[(2 * 32 + q) * 32 + lane] + prod;
               }
             }
-            __syncwarp();
           }
         }
       }
@@ -844,7 +831,7 @@ int level_create(ToeplitzGemmLevel* L, int n1, int n2, int prec, bool mass) {
     const int t1 = ((n2 + BN - 1) / BN) * ((n1 + BM - 1) / BM);
     const int tiles = t0 > t1 ? t0 : t1;
     const int nk = ((n1 < n2 ? n1 : n2) + BK - 1) / BK;
-    int sp = 152 * CTAS_PER_SM / tiles;
+    int sp = 152 / tiles;
     if (sp > 4) sp = 4;
     if (sp > nk / 4) sp = nk / 4;
     L->splits = sp > 1 ? sp : 1;
