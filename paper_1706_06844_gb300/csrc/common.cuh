@@ -274,6 +274,11 @@ struct ArnoldiState {
   int m;
   double *R, *cs, *sn, *g;
   ArnoldiStatus* status;
+  // delayed re-orthogonalisation (launch_dcgs2): the unrotated Hessenberg
+  // columns ((m + 1) x m, column j at H[j (m + 1) ..]) and g_j as it was before
+  // rotation j, so that column j - 1 can be corrected and re-rotated one step late
+  double* H = nullptr;
+  double* gpre = nullptr;
 };
 // one Arnoldi step j (k = j + 1 basis vectors V_0 .. V_j, w = the new vector):
 // CGS2 in three fused passes over V, the Givens update of column j in the
@@ -284,6 +289,17 @@ struct ArnoldiState {
 cudaError_t launch_cgs2(const double* V, size_t ldv, int k, double* w, size_t N, double* part,
                         unsigned* tickets, double* h, double* h2, const ArnoldiState& st, int j,
                         cudaStream_t s);
+// Arnoldi step j with delayed re-orthogonalisation (DCGS2), two fused passes
+// over V_0 .. V_{j-1}: the first projects both the new vector w = V_{j+1} and
+// the once-orthogonalised V_j, the second re-orthogonalises V_j, orthogonalises
+// w against the corrected basis and takes ||w||; the Givens updates run in the
+// last block of each pass (column j - 1 final, column j provisional), then
+// w /= ||w||.  j < kDcgsMax; ldv and N even; part: cgs_blocks() * (2 kDcgsMax
+// + 2) doubles; coef: kDcgsCoef doubles; tickets[0..1] zero at rest.
+constexpr int kDcgsMax = 32;
+constexpr int kDcgsCoef = 2 * kDcgsMax + 2;
+cudaError_t launch_dcgs2(double* V, size_t ldv, int j, size_t N, double* part, unsigned* tickets,
+                         double* coef, const ArnoldiState& st, cudaStream_t s);
 // k > 32: the same step from separate passes (dots, reduce, axpy); the Givens
 // update and the scaling as above
 cudaError_t launch_arnoldi_column(const ArnoldiState& st, int j, const double* h,

@@ -194,11 +194,17 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
       }
       NvtxRange arnoldi("cgs2");
       int pi = h->pbeg(FDE_KCLASS_KRYLOV);
-      if (j + 1 <= 32) {
+      if (m <= kDcgsMax) {
+        // two fused passes over V (V_j re-orthogonalised one step late), Givens
+        // updates in their last blocks, w /= ||w||
+        LCHK(launch_dcgs2(h->V, ldv, j, Ne, h->cgs_part, h->tickets, h->dcgs_coef, h->ast,
+                          h->st));
+        h->launches += 2;  // three kernels, one counted by LCHK
+      } else if (j + 1 <= 32) {
         // three fused passes over V, Givens update in the last block, w /= ||w||
         LCHK(launch_cgs2(h->V, ldv, j + 1, w, Ne, h->cgs_part, h->tickets, h->hdev, h->h2dev,
                          h->ast, j, h->st));
-        h->launches += 3;
+        h->launches += 3;  // four kernels, one counted by LCHK
       } else {
         // longer bases: separate dot and update passes, then the same column update
         LCHK(launch_dots(h->V, ldv, j + 1, w, N, h->part, h->nb, h->st));
@@ -425,18 +431,21 @@ int fde_create(const fde_params* pin, void* stream, fde_handle** out) {
     RCHK(h->alloc(&h->hdev, std::max(p.restart + 4, 40)));
     RCHK(h->alloc(&h->h2dev, p.restart + 4));
     RCHK(h->alloc(&h->ydev, p.restart + 4));
-    RCHK(h->alloc(&h->cgs_part, (size_t)cgs_blocks() * 34 + 8));
+    RCHK(h->alloc(&h->cgs_part, (size_t)cgs_blocks() * (2 * kDcgsMax + 2) + 8));
+    RCHK(h->alloc(&h->dcgs_coef, kDcgsCoef));
     RCHK(h->alloc(&h->tickets, 4));
     CCHK(cudaMemsetAsync(h->tickets, 0, 4 * sizeof(unsigned), h->st));
     {
       const int mm = p.restart;
       double* a = nullptr;
-      RCHK(h->alloc(&a, (size_t)(mm + 1) * mm + 3 * (size_t)mm + 2));
+      RCHK(h->alloc(&a, 2 * (size_t)(mm + 1) * mm + 4 * (size_t)mm + 2));
       h->ast.m = mm;
       h->ast.R = a;
       h->ast.cs = a + (size_t)(mm + 1) * mm;
       h->ast.sn = h->ast.cs + mm;
-      h->ast.g = h->ast.sn + mm;
+      h->ast.g = h->ast.sn + mm;               // m + 1 entries
+      h->ast.H = h->ast.g + mm + 1;            // (m + 1) x m
+      h->ast.gpre = h->ast.H + (size_t)(mm + 1) * mm;
       RCHK(h->alloc(&h->ast.status, 1));
       CCHK(cudaMallocHost(&h->status_host, sizeof(ArnoldiStatus)));
     }

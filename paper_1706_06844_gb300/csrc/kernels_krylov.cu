@@ -645,6 +645,270 @@ cudaError_t launch_arnoldi_lsq(const ArnoldiState& st, int k, double* y, cudaStr
 }
 
 // ============================================================================
+// Delayed classical Gram-Schmidt with re-orthogonalisation (DCGS2; Bielich,
+// Langou, Thomas, Swirydowicz, Yamazaki and Boman, Parallel Computing 2022)
+// for the Arnoldi steps of FGMRES (Sec. 5).  CGS2 reads the basis three times
+// per step; here the second projection of basis vector v_j is taken one step
+// late, in the same read of V as the first projection of the new vector
+// w = M^(m) z_j, so a step reads V_0 .. V_{j-1} twice:
+//   dots    s = V_{<j}^T v_j, alpha = v_j.v_j, a = V_{<j}^T w, b = v_j.w;
+//           last block: r = sqrt(alpha - s.s) (the norm of v_j - V s),
+//           c = (b - s.a) / r (the projection of w on the corrected v_j),
+//           Hessenberg column j - 1 corrected for v_j's re-orthogonalisation
+//           (h_{i,j-1} += eta s_i, h_{j,j-1} = eta r, eta its old subdiagonal)
+//           and its rotation redone from the unrotated column
+//   update  v_j <- (v_j - V_{<j} s) / r, w <- w - V_{<j} a - c v_j, ||w||^2;
+//           last block: column j = (a, c, ||w||) rotated, the residual
+//           estimate |g_{j+1}| (final once column j is corrected next step)
+// then w /= ||w||.  FGMRES keeps z_j = M^{-1} v_j from before v_j's
+// correction: A Z = V H holds for the corrected H whatever the z_j are.
+// v_0 = r_0 / ||r_0|| is taken as final (r = 1, no correction at j = 0).
+// Cost: both schemes take four FP64 FMAs per basis element and step, and on
+// this GPU (FP64 at 1/64 of the FP32 rate, ~0.5 T FP64 instructions/s) those
+// FMAs, not the bytes, bound the passes; the delayed scheme saves one read of
+// the basis and one serial reduction tail per step.
+namespace {
+
+__host__ __device__ __forceinline__ int dcgs_slot(int t, int j) {
+  // the 2j + 2 sums a step uses, in the slot layout s | a | alpha, b
+  return t < j ? t : t < 2 * j ? kDcgsMax + (t - j) : 2 * kDcgsMax + (t - 2 * j);
+}
+
+// the last block: out[slot] = sum_b part[slot * nb + b] for the step's sums;
+// warp w takes sums w, w + 8, ..., lane l adds b = l, l + 32, ... in order,
+// then a fixed butterfly: the same result every run
+__device__ __forceinline__ void dcgs_final_sums(const double* part, int nb, int j, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int cnt = 2 * j + 2;
+  for (int t = wid; t < cnt; t += CT / 32) {
+    const int slot = dcgs_slot(t, j);
+    const double* p = part + (size_t)slot * nb;
+    double s = 0.0;
+#pragma unroll 8
+    for (int b = lane; b < nb; b += 32) s += __ldcg(p + b);
+    s = warp_sum(s);
+    if (lane == 0) out[slot] = s;
+  }
+  __syncthreads();
+}
+
+// rotations 0 .. j-1 applied to the unrotated column j of H, rotation j
+// computed from it, R's column j stored; g_j (as it was before rotation j) is
+// saved and rotated.  Returns |g_{j+1}|.
+__device__ double dcgs_rotate_column(const ArnoldiState& st, int j) {
+  const int m = st.m;
+  double col[ArnoldiState::kMaxM + 1];
+  for (int i = 0; i <= j + 1; ++i) col[i] = st.H[(size_t)j * (m + 1) + i];
+  for (int i = 0; i < j; ++i) {
+    const double t = st.cs[i] * col[i] + st.sn[i] * col[i + 1];
+    col[i + 1] = -st.sn[i] * col[i] + st.cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double rho = hypot(col[j], col[j + 1]);
+  st.cs[j] = col[j] / rho;
+  st.sn[j] = col[j + 1] / rho;
+  col[j] = rho;
+  for (int i = 0; i <= j; ++i) st.R[(size_t)j * (m + 1) + i] = col[i];
+  const double gj = st.gpre[j];
+  st.g[j + 1] = -st.sn[j] * gj;
+  st.g[j] = st.cs[j] * gj;
+  return fabs(st.g[j + 1]);
+}
+
+// the dots pass's scalar work (one thread): d holds the slots of the step's sums
+__device__ void dcgs_correct(const ArnoldiState& st, int j, const double* d, double* coef) {
+  constexpr int kmax = kDcgsMax;
+  const int m = st.m;
+  int bad = 0;
+  double r = 1.0, c = d[2 * kmax + 1];
+  if (j > 0) {
+    double ss = 0.0, sa = 0.0;
+    for (int i = 0; i < j; ++i) {
+      ss = fma(d[i], d[i], ss);
+      sa = fma(d[i], d[kmax + i], sa);
+    }
+    const double rr = d[2 * kmax] - ss;
+    if (!(rr > 0.0)) bad = 1;  // v_j numerically inside span(V_{<j}), or not finite
+    r = sqrt(rr);
+    c = (d[2 * kmax + 1] - sa) / r;
+    // column j - 1: v_j^old = r v_j^new + V_{<j} s
+    double* hc = st.H + (size_t)(j - 1) * (m + 1);
+    const double eta = hc[j];
+    for (int i = 0; i < j; ++i) hc[i] = fma(eta, d[i], hc[i]);
+    hc[j] = eta * r;
+    // redo rotation j - 1 from g_{j-1} as it was before it
+    dcgs_rotate_column(st, j - 1);
+  }
+  double* hj = st.H + (size_t)j * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    coef[i] = d[i] / r;  // v_j / r - sum_i (s_i / r) V_i
+    coef[kDcgsMax + i] = d[kmax + i];
+    hj[i] = d[kmax + i];
+    if (!isfinite(d[i]) || !isfinite(d[kmax + i])) bad = 1;
+  }
+  hj[j] = c;
+  if (!isfinite(c) || !isfinite(r)) bad = 1;
+  coef[2 * kDcgsMax] = 1.0 / r;
+  coef[2 * kDcgsMax + 1] = c;
+  st.status->nonfinite = bad;
+}
+
+// J = j exactly (one instantiation per basis length): no predicated work for
+// unused vectors -- on this GPU the FP64 FMAs, not the bytes, bound the pass
+template <int J>
+__global__ void __launch_bounds__(CT) dcgs_dots_kernel(const double* __restrict__ V, size_t ldv,
+                                                       size_t n2, double* part, int nb,
+                                                       unsigned* ticket, double* coef,
+                                                       ArnoldiState st) {
+  constexpr int NS = 2 * kDcgsMax + 2;
+  constexpr int JA = J > 0 ? J : 1;
+  __shared__ double sred[(2 * J + 2) * (CT / 32)];
+  __shared__ double d[NS];
+  __shared__ unsigned last;
+  const double* __restrict__ vj = V + (size_t)J * ldv;
+  const double* __restrict__ w = V + (size_t)(J + 1) * ldv;
+  double as[JA], aw[JA], al = 0.0, bw = 0.0;
+#pragma unroll
+  for (int g = 0; g < JA; ++g) as[g] = aw[g] = 0.0;
+  for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n2; q += (size_t)nb * CT) {
+    const double2 vv = ld2(vj, q), wv = ld2(w, q);
+#pragma unroll
+    for (int g = 0; g < J; ++g) {
+      const double2 x = ld2(V + (size_t)g * ldv, q);
+      as[g] = fma(x.x, vv.x, fma(x.y, vv.y, as[g]));
+      aw[g] = fma(x.x, wv.x, fma(x.y, wv.y, aw[g]));
+    }
+    al = fma(vv.x, vv.x, fma(vv.y, vv.y, al));
+    bw = fma(vv.x, wv.x, fma(vv.y, wv.y, bw));
+  }
+  // block sums in compact order (s_0 .. s_{J-1}, a_0 .. a_{J-1}, alpha, b)
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int g = 0; g < J; ++g) {
+      const double x = warp_sum(as[g]), y = warp_sum(aw[g]);
+      if (lane == 0) {
+        sred[g * (CT / 32) + wid] = x;
+        sred[(J + g) * (CT / 32) + wid] = y;
+      }
+    }
+    const double x = warp_sum(al), y = warp_sum(bw);
+    if (lane == 0) {
+      sred[2 * J * (CT / 32) + wid] = x;
+      sred[(2 * J + 1) * (CT / 32) + wid] = y;
+    }
+    __syncthreads();
+  }
+  if ((int)threadIdx.x < 2 * J + 2) {
+    const int t = threadIdx.x;
+    double v = 0.0;
+    for (int ww = 0; ww < CT / 32; ++ww) v += sred[t * (CT / 32) + ww];
+    part[(size_t)dcgs_slot(t, J) * nb + blockIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == (unsigned)(nb - 1)) ? 1u : 0u;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  dcgs_final_sums(part, nb, J, d);
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    dcgs_correct(st, J, d, coef);
+  }
+}
+
+// v_j <- v_j / r - sum_g (s_g / r) V_g and w <- w - sum_g a_g V_g - c v_j over
+// a run-time j (two FMAs per basis element; the sums need no registers per g)
+__global__ void __launch_bounds__(CT) dcgs_update_kernel(double* V, size_t ldv, int j, size_t n2,
+                                                         double* part, int nb, unsigned* ticket,
+                                                         const double* __restrict__ coef,
+                                                         ArnoldiState st) {
+  __shared__ double cs_[kDcgsMax], ca_[kDcgsMax];
+  __shared__ double sred[CT / 32];
+  __shared__ double nrm2;
+  if ((int)threadIdx.x < kDcgsMax) {
+    const int g = threadIdx.x;
+    cs_[g] = g < j ? coef[g] : 0.0;
+    ca_[g] = g < j ? coef[kDcgsMax + g] : 0.0;
+  }
+  __syncthreads();
+  const double rinv = coef[2 * kDcgsMax], c = coef[2 * kDcgsMax + 1];
+  double2* vj = reinterpret_cast<double2*>(V + (size_t)j * ldv);
+  double2* w = reinterpret_cast<double2*>(V + (size_t)(j + 1) * ldv);
+  double acc[1] = {0.0};
+  for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n2; q += (size_t)nb * CT) {
+    double2 vv = vj[q], wv = w[q];
+    if (j > 0) {
+      vv.x *= rinv;
+      vv.y *= rinv;
+#pragma unroll 4
+      for (int g = 0; g < j; ++g) {
+        const double2 x = ld2(V + (size_t)g * ldv, q);
+        vv.x = fma(-cs_[g], x.x, vv.x);
+        vv.y = fma(-cs_[g], x.y, vv.y);
+        wv.x = fma(-ca_[g], x.x, wv.x);
+        wv.y = fma(-ca_[g], x.y, wv.y);
+      }
+      vj[q] = vv;
+    }
+    wv.x = fma(-c, vv.x, wv.x);
+    wv.y = fma(-c, vv.y, wv.y);
+    w[q] = wv;
+    acc[0] = fma(wv.x, wv.x, fma(wv.y, wv.y, acc[0]));
+  }
+  block_reduce_vec<1>(acc, 1, sred);
+  if (publish_partials(sred, 1, part, nb, ticket)) {
+    final_sums(part, 1, nb, &nrm2);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *ticket = 0u;
+      const int m = st.m;
+      const double hnext = sqrt(nrm2);
+      st.H[(size_t)j * (m + 1) + j + 1] = hnext;
+      st.gpre[j] = st.g[j];
+      st.status->gabs = dcgs_rotate_column(st, j);
+      st.status->hnext = hnext;
+      st.status->inv_norm = 1.0 / hnext;
+      if (!isfinite(hnext)) st.status->nonfinite = 1;
+    }
+  }
+}
+
+template <int J>
+void launch_dcgs_dots(const double* V, size_t ldv, size_t n2, double* part, unsigned* ticket,
+                      double* coef, const ArnoldiState& st, cudaStream_t s) {
+  const int nb = resident_blocks((const void*)dcgs_dots_kernel<J>);
+  dcgs_dots_kernel<J><<<nb, CT, 0, s>>>(V, ldv, n2, part, nb, ticket, coef, st);
+}
+
+}  // namespace
+
+cudaError_t launch_dcgs2(double* V, size_t ldv, int j, size_t N, double* part, unsigned* tickets,
+                         double* coef, const ArnoldiState& st, cudaStream_t s) {
+  if (j < 0 || j >= kDcgsMax || j >= st.m || !st.H || !st.gpre || (ldv & 1) || (N & 1))
+    return cudaErrorInvalidValue;
+  const size_t n2 = N / 2;
+  using Dots = void (*)(const double*, size_t, size_t, double*, unsigned*, double*,
+                        const ArnoldiState&, cudaStream_t);
+  static const Dots dots[kDcgsMax] = {
+      launch_dcgs_dots<0>,  launch_dcgs_dots<1>,  launch_dcgs_dots<2>,  launch_dcgs_dots<3>,
+      launch_dcgs_dots<4>,  launch_dcgs_dots<5>,  launch_dcgs_dots<6>,  launch_dcgs_dots<7>,
+      launch_dcgs_dots<8>,  launch_dcgs_dots<9>,  launch_dcgs_dots<10>, launch_dcgs_dots<11>,
+      launch_dcgs_dots<12>, launch_dcgs_dots<13>, launch_dcgs_dots<14>, launch_dcgs_dots<15>,
+      launch_dcgs_dots<16>, launch_dcgs_dots<17>, launch_dcgs_dots<18>, launch_dcgs_dots<19>,
+      launch_dcgs_dots<20>, launch_dcgs_dots<21>, launch_dcgs_dots<22>, launch_dcgs_dots<23>,
+      launch_dcgs_dots<24>, launch_dcgs_dots<25>, launch_dcgs_dots<26>, launch_dcgs_dots<27>,
+      launch_dcgs_dots<28>, launch_dcgs_dots<29>, launch_dcgs_dots<30>, launch_dcgs_dots<31>};
+  static_assert(kDcgsMax == 32, "one dots instantiation per basis length");
+  dots[j](V, ldv, n2, part, tickets, coef, st, s);
+  const int nb = resident_blocks((const void*)dcgs_update_kernel);
+  dcgs_update_kernel<<<nb, CT, 0, s>>>(V, ldv, j, n2, part, nb, tickets + 1, coef, st);
+  scale_by_kernel<<<152 * 4, 256, 0, s>>>(V + (size_t)(j + 1) * ldv, n2, st.status);
+  return cudaGetLastError();
+}
+
+// ============================================================================
 // grouped FGMRES (many problems in lockstep): the passes above over items
 // (problem entry, chunk of kGKChunk double2 pairs); each problem reduces its
 // partials in the block that finishes its last chunk, in chunk order

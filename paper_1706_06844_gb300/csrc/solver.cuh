@@ -100,6 +100,7 @@ struct fde_handle {
   // Arnoldi state on the device (rotated Hessenberg matrix, rotations, g)
   ArnoldiState ast{};
   double* cgs_part = nullptr;
+  double* dcgs_coef = nullptr;  // the delayed scheme's projection coefficients
   unsigned* tickets = nullptr;
   ArnoldiStatus* status_host = nullptr;  // pinned: the status read after each step
 
