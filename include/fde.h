@@ -243,6 +243,20 @@ int fde_set_state(fde_handle* h, int m);
  * on a launch error.  Does not synchronise. */
 int fde_wait_selftest(fde_handle* h, int complete);
 
+/* Self-test of the integer-only number conversions the kernels use instead
+ * of FP64 instructions (no paper passage: GB300 runs FP64 arithmetic and
+ * conversions at 1/64 of the FP32 rate).  On the current device, n seeded
+ * inputs (random bit patterns of every exponent, values near the FP32 range
+ * and its edges, rounding ties, zeros, subnormals, infinities, NaN) compare
+ * double -> float (round to nearest even) and float -> double with the CUDA
+ * conversions bit for bit (NaN as NaN), and the double -> double-float split
+ * with its bounds |hi + lo - x| <= 2^-47 |x| for 2^-73 <= |x| <= 2^100 and
+ * <= 2^-97 below.
+ * *mismatches (host) receives the number of failures.  Returns FDE_OK,
+ * FDE_ERR_ARG for n < 1 or a NULL pointer, FDE_ERR_CUDA on a CUDA error.
+ * Synchronises the device. */
+int fde_conversion_selftest(long long n, long long* mismatches);
+
 /* Kernel-level timing with CUDA events on the handle's stream (off by
  * default).  Kernel classes: FDE_KCLASS_*.  fde_profile_query returns the
  * number of launches and their summed event time since the last reset. */

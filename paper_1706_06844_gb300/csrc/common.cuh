@@ -294,12 +294,20 @@ cudaError_t launch_cgs2(const double* V, size_t ldv, int k, double* w, size_t N,
 // the once-orthogonalised V_j, the second re-orthogonalises V_j, orthogonalises
 // w against the corrected basis and takes ||w||; the Givens updates run in the
 // last block of each pass (column j - 1 final, column j provisional), then
-// w /= ||w||.  j < kDcgsMax; ldv and N even; part: cgs_blocks() * (2 kDcgsMax
-// + 2) doubles; coef: kDcgsCoef doubles; tickets[0..1] zero at rest.
+// w /= ||w||.  df_store: the basis holds double-float vectors (hi, lo FP32
+// pairs, 8 bytes an element like FP64) and the passes compute in double-float
+// on the FP32 pipes; otherwise FP64 vectors and arithmetic.  j < kDcgsMax;
+// ldv and N even; part: cgs_blocks() * (2 kDcgsMax + 2) doubles; coef:
+// kDcgsCoef doubles; tickets[0..1] zero at rest.
 constexpr int kDcgsMax = 32;
 constexpr int kDcgsCoef = 2 * kDcgsMax + 2;
 cudaError_t launch_dcgs2(double* V, size_t ldv, int j, size_t N, double* part, unsigned* tickets,
-                         double* coef, const ArnoldiState& st, cudaStream_t s);
+                         double* coef, const ArnoldiState& st, bool df_store, cudaStream_t s);
+// y_df = x / *s (FP64 in, double-float out); x += Z_df c (k <= kDcgsMax)
+cudaError_t launch_scale_inv_df(size_t N, const double* x, const double* s, double* y_df,
+                                cudaStream_t st);
+cudaError_t launch_update_df(const double* Z_df, size_t ldz, int k, const double* c, double* x,
+                             size_t N, cudaStream_t st);
 // k > 32: the same step from separate passes (dots, reduce, axpy); the Givens
 // update and the scaling as above
 cudaError_t launch_arnoldi_column(const ArnoldiState& st, int j, const double* h,
@@ -310,6 +318,8 @@ cudaError_t launch_arnoldi_start(const ArnoldiState& st, const double* beta_dev,
 // y = R^{-1} g for the first k columns
 cudaError_t launch_arnoldi_lsq(const ArnoldiState& st, int k, double* y, cudaStream_t s);
 int cgs_blocks();
+// integer conversions against the CUDA ones (fde_conversion_selftest); 0 on success
+int conversion_selftest(long long n, long long* mismatches);
 
 // ---------------------------------------------------------------- grouped launches
 // Many independent problems advanced by one launch per stage (the batch

@@ -51,6 +51,51 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
   return FDE_OK;
 }
 
+// y = M^(m) x on double-float vectors (x, y: 8-byte hi, lo pairs), the
+// double-float outer operator without conversions at its ends
+static int outer_apply_df(fde_handle* h, const double* x_, double* y_) {
+  NvtxRange range("matvec");
+  const df* x = reinterpret_cast<const df*>(x_);
+  df* y = reinterpret_cast<df*>(y_);
+  df* xT = reinterpret_cast<df*>(h->xT);
+  df* yT = reinterpret_cast<df*>(h->yT);
+  const int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
+  cx<df>* ws = reinterpret_cast<cx<df>*>(h->fft_ws);
+  LCHK((launch_fft_pass<df, df, df>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1xd, h->S2xd,
+                                    h->twxd, h->cfN[0], h->cfN[1], x, h->c, y, 0, h->st, ws,
+                                    h->fft_ws_elems)));
+  LCHK(launch_transpose<df>(x, h->n2, h->n1, xT, 0, h->st));
+  LCHK((launch_fft_pass<df, df, df>(xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1yd, h->S2yd,
+                                    h->twyd, h->cfNT[0], h->cfNT[1], nullptr, 0.0, yT, 0, h->st,
+                                    ws, h->fft_ws_elems)));
+  LCHK(launch_transpose<df>(yT, h->n1, h->n2, y, 1, h->st));  // y += yT^T in double-float
+  h->pend(pi);
+  return FDE_OK;
+}
+
+// the relaxed matvec on double-float vectors (FP32 arithmetic, FP32 result
+// widened)
+static int outer_apply32_df(fde_handle* h, const double* x_, double* y_) {
+  NvtxRange range("matvec_fp32");
+  const df* x = reinterpret_cast<const df*>(x_);
+  df* y = reinterpret_cast<df*>(y_);
+  cx<float>* ws = reinterpret_cast<cx<float>*>(h->fft_ws);
+  const size_t wse = h->fft_ws_elems * 2;
+  int pi = h->pbeg(FDE_KCLASS_OUTER_FP32);
+  LCHK((launch_fft_pass<df, float, float>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x32,
+                                          h->S2x32, h->twx32, h->cf32[0], h->cf32[1], x, h->c,
+                                          y, 0, h->st, ws, wse)));
+  df* xT = reinterpret_cast<df*>(h->xT);
+  df* yT = reinterpret_cast<df*>(h->yT);
+  LCHK(launch_transpose<df>(x, h->n2, h->n1, xT, 0, h->st));
+  LCHK((launch_fft_pass<df, float, float>(xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1y32,
+                                          h->S2y32, h->twy32, h->cf32T[0], h->cf32T[1], nullptr,
+                                          0.0, yT, 0, h->st, ws, wse)));
+  LCHK(launch_transpose<df>(yT, h->n1, h->n2, y, 1, h->st));
+  h->pend(pi);
+  return FDE_OK;
+}
+
 // y = M^(m) x with FP32 arithmetic on FP64 data (relaxed Krylov matvec)
 static int outer_apply32(fde_handle* h, const double* x, double* y) {
   NvtxRange range("matvec_fp32");
@@ -81,13 +126,13 @@ static int norm2(fde_handle* h, const double* x, double* dev_out, double* host_o
   return FDE_OK;
 }
 
-static int precond(fde_handle* h, const double* v, double* z) {
+static int precond(fde_handle* h, const double* v, double* z, bool df_io = false) {
   NvtxRange range("vcycle");
   if (!h->mg) {
     CCHK(cudaMemcpyAsync(z, v, h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     return FDE_OK;
   }
-  return h->mg->vcycle(h, v, z);
+  return h->mg->vcycle(h, v, z, df_io);
 }
 
 // Multigrid as the solver (fde_params.solver = FDE_SOLVER_MG): the stationary
@@ -139,6 +184,16 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
   const size_t N = h->N;
   const int m = p.restart;
   fde_stats st{0, 0, 0, 0.0, 0};
+  // With the double-float outer operator the Krylov vectors V and Z are kept
+  // in double-float (hi, lo FP32 pairs in the same 8 bytes an element): the
+  // Gram-Schmidt passes, matvecs and V-cycle ends then run on the FP32 pipes
+  // (GB300 issues FP64 at 1/64 of the FP32 rate).  x, b and the true residual
+  // stay FP64.
+  const bool dfk = p.outer == FDE_OUTER_DF32 && m <= kDcgsMax;
+  auto start_basis = [&](const double* r, const double* nrm_dev) {
+    return dfk ? launch_scale_inv_df(N, r, nrm_dev, h->V, h->st)
+               : launch_scale_inv(N, r, nrm_dev, h->V, h->st);
+  };
   double bnorm = 0.0;
   RCHK(norm2(h, b, h->hdev, &bnorm));
   if (!std::isfinite(bnorm)) return h->fail(FDE_ERR_NONFINITE, "right-hand side is not finite");
@@ -163,11 +218,11 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
       if (st_out) *st_out = st;
       return FDE_OK;
     }
-    LCHK(launch_scale_inv(N, h->tmp, h->h2dev, h->V, h->st));
+    LCHK(start_basis(h->tmp, h->h2dev));
   } else {
     CCHK(cudaMemsetAsync(x, 0, N * sizeof(double), h->st));
     // V_0 = b / ||b||
-    LCHK(launch_scale_inv(N, b, h->hdev, h->V, h->st));
+    LCHK(start_basis(b, h->hdev));
   }
   const double tol = p.rtol * bnorm;
   const size_t ldv = h->ldv;
@@ -184,20 +239,20 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
       double* Vj = h->V + (size_t)j * ldv;
       double* Zj = h->Z + (size_t)j * ldv;
       double* w = h->V + (size_t)(j + 1) * ldv;
-      RCHK(precond(h, Vj, Zj));
+      RCHK(precond(h, Vj, Zj, dfk));
       // relaxed matvec once the residual estimate is near the target
       if (p.relax && gprev <= FDE_RELAX_FACTOR * tol) {
-        RCHK(outer_apply32(h, Zj, w));
+        RCHK(dfk ? outer_apply32_df(h, Zj, w) : outer_apply32(h, Zj, w));
         st.relaxed++;
       } else {
-        RCHK(outer_apply(h, Zj, w, false));
+        RCHK(dfk ? outer_apply_df(h, Zj, w) : outer_apply(h, Zj, w, false));
       }
       NvtxRange arnoldi("cgs2");
       int pi = h->pbeg(FDE_KCLASS_KRYLOV);
       if (m <= kDcgsMax) {
         // two fused passes over V (V_j re-orthogonalised one step late), Givens
         // updates in their last blocks, w /= ||w||
-        LCHK(launch_dcgs2(h->V, ldv, j, Ne, h->cgs_part, h->tickets, h->dcgs_coef, h->ast,
+        LCHK(launch_dcgs2(h->V, ldv, j, Ne, h->cgs_part, h->tickets, h->dcgs_coef, h->ast, dfk,
                           h->st));
         h->launches += 2;  // three kernels, one counted by LCHK
       } else if (j + 1 <= 32) {
@@ -233,7 +288,8 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
     // y = R^{-1} g, x += Z y (on the device)
     int pi = h->pbeg(FDE_KCLASS_KRYLOV);
     LCHK(launch_arnoldi_lsq(h->ast, k, h->ydev, h->st));
-    LCHK(launch_update(h->Z, ldv, k, h->ydev, x, N, h->st));
+    LCHK(dfk ? launch_update_df(h->Z, ldv, k, h->ydev, x, N, h->st)
+             : launch_update(h->Z, ldv, k, h->ydev, x, N, h->st));
     h->pend(pi);
     // true residual in FP64
     RCHK(outer_apply(h, x, h->tmp, false));
@@ -247,7 +303,7 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
       break;
     }
     if (st.iterations >= p.maxit) break;
-    LCHK(launch_scale_inv(N, h->tmp, h->h2dev, h->V, h->st));
+    LCHK(start_basis(h->tmp, h->h2dev));
     beta_dev = h->h2dev;
   }
   if (st_out) *st_out = st;
@@ -629,6 +685,12 @@ int fde_solve(fde_handle* h, const double* b, double* x, fde_stats* st) {
   if (h->mg && h->mg->device_error(h))
     return h->fail(FDE_ERR_TIMEOUT, "a capped device-side wait gave up during the solve");
   return r;
+}
+
+int fde_conversion_selftest(long long n, long long* mismatches) {
+  if (n < 1 || !mismatches) return FDE_ERR_ARG;
+  if (conversion_selftest(n, mismatches)) return FDE_ERR_CUDA;
+  return FDE_OK;
 }
 
 int fde_wait_selftest(fde_handle* h, int complete) {

@@ -8,6 +8,7 @@
 #include <utility>
 
 #include "common.cuh"
+#include "df32.cuh"
 #include "../../include/fde.h"
 
 namespace fde {
@@ -753,13 +754,64 @@ __device__ void dcgs_correct(const ArnoldiState& st, int j, const double* d, dou
   st.status->nonfinite = bad;
 }
 
-// J = j exactly (one instantiation per basis length): no predicated work for
-// unused vectors -- on this GPU the FP64 FMAs, not the bytes, bound the pass
-template <int J>
+// Storage and arithmetic of the passes: FP64 vectors, or double-float vectors
+// (hi, lo FP32 pairs, ~2^-48, 8 bytes an element like FP64) computed on the
+// FP32 pipes.  Two elements per 16-byte load either way.
+template <typename S>
+struct Store;
+template <>
+struct Store<double> {
+  using A = double;
+  static __device__ __forceinline__ void ld(const double* p, size_t q, A& a0, A& a1) {
+    const double2 v = reinterpret_cast<const double2*>(p)[q];
+    a0 = v.x;
+    a1 = v.y;
+  }
+  static __device__ __forceinline__ void st(double* p, size_t q, A a0, A a1) {
+    reinterpret_cast<double2*>(p)[q] = make_double2(a0, a1);
+  }
+  static __device__ __forceinline__ A from(double x) { return x; }
+  static __device__ __forceinline__ A zero() { return 0.0; }
+  static __device__ __forceinline__ A fma(A a, A b, A c) { return ::fma(a, b, c); }
+  static __device__ __forceinline__ A mul(A a, A b) { return a * b; }
+  static __device__ __forceinline__ A neg(A a) { return -a; }
+  // warp sum (every lane gets it)
+  static __device__ __forceinline__ double wsum(A a) { return warp_sum(a); }
+};
+template <>
+struct Store<df> {
+  using A = df;
+  static __device__ __forceinline__ void ld(const double* p, size_t q, A& a0, A& a1) {
+    const float4 v = reinterpret_cast<const float4*>(p)[q];
+    a0 = df(v.x, v.y);
+    a1 = df(v.z, v.w);
+  }
+  static __device__ __forceinline__ void st(double* p, size_t q, A a0, A a1) {
+    reinterpret_cast<float4*>(p)[q] = make_float4(a0.hi, a0.lo, a1.hi, a1.lo);
+  }
+  static __device__ __forceinline__ A from(double x) { return df_from_bits(x); }
+  static __device__ __forceinline__ A zero() { return df(0.f, 0.f); }
+  static __device__ __forceinline__ A fma(A a, A b, A c) { return df_fma(a, b, c); }
+  static __device__ __forceinline__ A mul(A a, A b) { return a * b; }
+  static __device__ __forceinline__ A neg(A a) { return -a; }
+  static __device__ __forceinline__ double wsum(A a) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const df b(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
+      a = a + b;
+    }
+    return (double)a;
+  }
+};
+
+// J = j exactly (one instantiation per basis length): no predicated loads of
+// unused vectors
+template <int J, typename S>
 __global__ void __launch_bounds__(CT) dcgs_dots_kernel(const double* __restrict__ V, size_t ldv,
                                                        size_t n2, double* part, int nb,
                                                        unsigned* ticket, double* coef,
                                                        ArnoldiState st) {
+  using K = Store<S>;
+  using A = typename K::A;
   constexpr int NS = 2 * kDcgsMax + 2;
   constexpr int JA = J > 0 ? J : 1;
   __shared__ double sred[(2 * J + 2) * (CT / 32)];
@@ -767,32 +819,35 @@ __global__ void __launch_bounds__(CT) dcgs_dots_kernel(const double* __restrict_
   __shared__ unsigned last;
   const double* __restrict__ vj = V + (size_t)J * ldv;
   const double* __restrict__ w = V + (size_t)(J + 1) * ldv;
-  double as[JA], aw[JA], al = 0.0, bw = 0.0;
+  A as[JA], aw[JA], al = K::zero(), bw = K::zero();
 #pragma unroll
-  for (int g = 0; g < JA; ++g) as[g] = aw[g] = 0.0;
+  for (int g = 0; g < JA; ++g) as[g] = aw[g] = K::zero();
   for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n2; q += (size_t)nb * CT) {
-    const double2 vv = ld2(vj, q), wv = ld2(w, q);
+    A v0, v1, w0, w1;
+    K::ld(vj, q, v0, v1);
+    K::ld(w, q, w0, w1);
 #pragma unroll
     for (int g = 0; g < J; ++g) {
-      const double2 x = ld2(V + (size_t)g * ldv, q);
-      as[g] = fma(x.x, vv.x, fma(x.y, vv.y, as[g]));
-      aw[g] = fma(x.x, wv.x, fma(x.y, wv.y, aw[g]));
+      A x0, x1;
+      K::ld(V + (size_t)g * ldv, q, x0, x1);
+      as[g] = K::fma(x1, v1, K::fma(x0, v0, as[g]));
+      aw[g] = K::fma(x1, w1, K::fma(x0, w0, aw[g]));
     }
-    al = fma(vv.x, vv.x, fma(vv.y, vv.y, al));
-    bw = fma(vv.x, wv.x, fma(vv.y, wv.y, bw));
+    al = K::fma(v1, v1, K::fma(v0, v0, al));
+    bw = K::fma(v1, w1, K::fma(v0, w0, bw));
   }
   // block sums in compact order (s_0 .. s_{J-1}, a_0 .. a_{J-1}, alpha, b)
   {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int g = 0; g < J; ++g) {
-      const double x = warp_sum(as[g]), y = warp_sum(aw[g]);
+      const double x = K::wsum(as[g]), y = K::wsum(aw[g]);
       if (lane == 0) {
         sred[g * (CT / 32) + wid] = x;
         sred[(J + g) * (CT / 32) + wid] = y;
       }
     }
-    const double x = warp_sum(al), y = warp_sum(bw);
+    const double x = K::wsum(al), y = K::wsum(bw);
     if (lane == 0) {
       sred[2 * J * (CT / 32) + wid] = x;
       sred[(2 * J + 1) * (CT / 32) + wid] = y;
@@ -820,44 +875,54 @@ __global__ void __launch_bounds__(CT) dcgs_dots_kernel(const double* __restrict_
 
 // v_j <- v_j / r - sum_g (s_g / r) V_g and w <- w - sum_g a_g V_g - c v_j over
 // a run-time j (two FMAs per basis element; the sums need no registers per g)
+template <typename S>
 __global__ void __launch_bounds__(CT) dcgs_update_kernel(double* V, size_t ldv, int j, size_t n2,
                                                          double* part, int nb, unsigned* ticket,
                                                          const double* __restrict__ coef,
                                                          ArnoldiState st) {
-  __shared__ double cs_[kDcgsMax], ca_[kDcgsMax];
+  using K = Store<S>;
+  using A = typename K::A;
+  __shared__ A cs_[kDcgsMax], ca_[kDcgsMax];
   __shared__ double sred[CT / 32];
   __shared__ double nrm2;
   if ((int)threadIdx.x < kDcgsMax) {
     const int g = threadIdx.x;
-    cs_[g] = g < j ? coef[g] : 0.0;
-    ca_[g] = g < j ? coef[kDcgsMax + g] : 0.0;
+    cs_[g] = K::neg(K::from(g < j ? coef[g] : 0.0));
+    ca_[g] = K::neg(K::from(g < j ? coef[kDcgsMax + g] : 0.0));
   }
   __syncthreads();
-  const double rinv = coef[2 * kDcgsMax], c = coef[2 * kDcgsMax + 1];
-  double2* vj = reinterpret_cast<double2*>(V + (size_t)j * ldv);
-  double2* w = reinterpret_cast<double2*>(V + (size_t)(j + 1) * ldv);
-  double acc[1] = {0.0};
+  const A rinv = K::from(coef[2 * kDcgsMax]), mc = K::neg(K::from(coef[2 * kDcgsMax + 1]));
+  double* vj = V + (size_t)j * ldv;
+  double* w = V + (size_t)(j + 1) * ldv;
+  A acc = K::zero();
   for (size_t q = blockIdx.x * (size_t)CT + threadIdx.x; q < n2; q += (size_t)nb * CT) {
-    double2 vv = vj[q], wv = w[q];
+    A v0, v1, w0, w1;
+    K::ld(vj, q, v0, v1);
+    K::ld(w, q, w0, w1);
     if (j > 0) {
-      vv.x *= rinv;
-      vv.y *= rinv;
+      v0 = K::mul(v0, rinv);
+      v1 = K::mul(v1, rinv);
 #pragma unroll 4
       for (int g = 0; g < j; ++g) {
-        const double2 x = ld2(V + (size_t)g * ldv, q);
-        vv.x = fma(-cs_[g], x.x, vv.x);
-        vv.y = fma(-cs_[g], x.y, vv.y);
-        wv.x = fma(-ca_[g], x.x, wv.x);
-        wv.y = fma(-ca_[g], x.y, wv.y);
+        A x0, x1;
+        K::ld(V + (size_t)g * ldv, q, x0, x1);
+        v0 = K::fma(cs_[g], x0, v0);
+        v1 = K::fma(cs_[g], x1, v1);
+        w0 = K::fma(ca_[g], x0, w0);
+        w1 = K::fma(ca_[g], x1, w1);
       }
-      vj[q] = vv;
+      K::st(vj, q, v0, v1);
     }
-    wv.x = fma(-c, vv.x, wv.x);
-    wv.y = fma(-c, vv.y, wv.y);
-    w[q] = wv;
-    acc[0] = fma(wv.x, wv.x, fma(wv.y, wv.y, acc[0]));
+    w0 = K::fma(mc, v0, w0);
+    w1 = K::fma(mc, v1, w1);
+    K::st(w, q, w0, w1);
+    acc = K::fma(w1, w1, K::fma(w0, w0, acc));
   }
-  block_reduce_vec<1>(acc, 1, sred);
+  {
+    const double x = K::wsum(acc);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = x;
+    __syncthreads();
+  }
   if (publish_partials(sred, 1, part, nb, ticket)) {
     final_sums(part, 1, nb, &nrm2);
     __syncthreads();
@@ -875,36 +940,99 @@ __global__ void __launch_bounds__(CT) dcgs_update_kernel(double* V, size_t ldv, 
   }
 }
 
-template <int J>
+// w <- w / ||w|| for double-float vectors
+__global__ void scale_by_df_kernel(double* w, size_t n2, const ArnoldiStatus* s) {
+  const df inv = df_from_bits(s->inv_norm);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n2;
+       q += (size_t)gridDim.x * blockDim.x) {
+    df a0, a1;
+    Store<df>::ld(w, q, a0, a1);
+    Store<df>::st(w, q, a0 * inv, a1 * inv);
+  }
+}
+
+template <int J, typename S>
 void launch_dcgs_dots(const double* V, size_t ldv, size_t n2, double* part, unsigned* ticket,
                       double* coef, const ArnoldiState& st, cudaStream_t s) {
-  const int nb = resident_blocks((const void*)dcgs_dots_kernel<J>);
-  dcgs_dots_kernel<J><<<nb, CT, 0, s>>>(V, ldv, n2, part, nb, ticket, coef, st);
+  const int nb = resident_blocks((const void*)dcgs_dots_kernel<J, S>);
+  dcgs_dots_kernel<J, S><<<nb, CT, 0, s>>>(V, ldv, n2, part, nb, ticket, coef, st);
+}
+
+template <typename S>
+void launch_dcgs_step(double* V, size_t ldv, int j, size_t n2, double* part, unsigned* tickets,
+                      double* coef, const ArnoldiState& st, cudaStream_t s) {
+  using Dots = void (*)(const double*, size_t, size_t, double*, unsigned*, double*,
+                        const ArnoldiState&, cudaStream_t);
+  static const Dots dots[kDcgsMax] = {
+      launch_dcgs_dots<0, S>,  launch_dcgs_dots<1, S>,  launch_dcgs_dots<2, S>,
+      launch_dcgs_dots<3, S>,  launch_dcgs_dots<4, S>,  launch_dcgs_dots<5, S>,
+      launch_dcgs_dots<6, S>,  launch_dcgs_dots<7, S>,  launch_dcgs_dots<8, S>,
+      launch_dcgs_dots<9, S>,  launch_dcgs_dots<10, S>, launch_dcgs_dots<11, S>,
+      launch_dcgs_dots<12, S>, launch_dcgs_dots<13, S>, launch_dcgs_dots<14, S>,
+      launch_dcgs_dots<15, S>, launch_dcgs_dots<16, S>, launch_dcgs_dots<17, S>,
+      launch_dcgs_dots<18, S>, launch_dcgs_dots<19, S>, launch_dcgs_dots<20, S>,
+      launch_dcgs_dots<21, S>, launch_dcgs_dots<22, S>, launch_dcgs_dots<23, S>,
+      launch_dcgs_dots<24, S>, launch_dcgs_dots<25, S>, launch_dcgs_dots<26, S>,
+      launch_dcgs_dots<27, S>, launch_dcgs_dots<28, S>, launch_dcgs_dots<29, S>,
+      launch_dcgs_dots<30, S>, launch_dcgs_dots<31, S>};
+  static_assert(kDcgsMax == 32, "one dots instantiation per basis length");
+  dots[j](V, ldv, n2, part, tickets, coef, st, s);
+  const int nb = resident_blocks((const void*)dcgs_update_kernel<S>);
+  dcgs_update_kernel<S><<<nb, CT, 0, s>>>(V, ldv, j, n2, part, nb, tickets + 1, coef, st);
+}
+
+// y = x / *s as double-float (the first basis vector of a restart cycle)
+__global__ void scale_inv_df_kernel(size_t N, const double* __restrict__ x,
+                                    const double* __restrict__ s, df* y) {
+  const double inv = 1.0 / s[0];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = df_from_bits(x[i] * inv);
+}
+
+// x += Z c with double-float Z: the combination in double-float, one FP64 add
+__global__ void update_df_kernel(const df* __restrict__ Z, size_t ldz, int k,
+                                 const double* __restrict__ c, double* x, size_t N) {
+  __shared__ df cs[kDcgsMax];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = df_from_bits(c[i]);
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N;
+       e += (size_t)gridDim.x * blockDim.x) {
+    df s(0.f, 0.f);
+    for (int i = 0; i < k; ++i) s = df_fma(cs[i], Z[(size_t)i * ldz + e], s);
+    x[e] = x[e] + (double)s;
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_dcgs2(double* V, size_t ldv, int j, size_t N, double* part, unsigned* tickets,
-                         double* coef, const ArnoldiState& st, cudaStream_t s) {
+                         double* coef, const ArnoldiState& st, bool df_store, cudaStream_t s) {
   if (j < 0 || j >= kDcgsMax || j >= st.m || !st.H || !st.gpre || (ldv & 1) || (N & 1))
     return cudaErrorInvalidValue;
   const size_t n2 = N / 2;
-  using Dots = void (*)(const double*, size_t, size_t, double*, unsigned*, double*,
-                        const ArnoldiState&, cudaStream_t);
-  static const Dots dots[kDcgsMax] = {
-      launch_dcgs_dots<0>,  launch_dcgs_dots<1>,  launch_dcgs_dots<2>,  launch_dcgs_dots<3>,
-      launch_dcgs_dots<4>,  launch_dcgs_dots<5>,  launch_dcgs_dots<6>,  launch_dcgs_dots<7>,
-      launch_dcgs_dots<8>,  launch_dcgs_dots<9>,  launch_dcgs_dots<10>, launch_dcgs_dots<11>,
-      launch_dcgs_dots<12>, launch_dcgs_dots<13>, launch_dcgs_dots<14>, launch_dcgs_dots<15>,
-      launch_dcgs_dots<16>, launch_dcgs_dots<17>, launch_dcgs_dots<18>, launch_dcgs_dots<19>,
-      launch_dcgs_dots<20>, launch_dcgs_dots<21>, launch_dcgs_dots<22>, launch_dcgs_dots<23>,
-      launch_dcgs_dots<24>, launch_dcgs_dots<25>, launch_dcgs_dots<26>, launch_dcgs_dots<27>,
-      launch_dcgs_dots<28>, launch_dcgs_dots<29>, launch_dcgs_dots<30>, launch_dcgs_dots<31>};
-  static_assert(kDcgsMax == 32, "one dots instantiation per basis length");
-  dots[j](V, ldv, n2, part, tickets, coef, st, s);
-  const int nb = resident_blocks((const void*)dcgs_update_kernel);
-  dcgs_update_kernel<<<nb, CT, 0, s>>>(V, ldv, j, n2, part, nb, tickets + 1, coef, st);
-  scale_by_kernel<<<152 * 4, 256, 0, s>>>(V + (size_t)(j + 1) * ldv, n2, st.status);
+  double* w = V + (size_t)(j + 1) * ldv;
+  if (df_store) {
+    launch_dcgs_step<df>(V, ldv, j, n2, part, tickets, coef, st, s);
+    scale_by_df_kernel<<<152 * 4, 256, 0, s>>>(w, n2, st.status);
+  } else {
+    launch_dcgs_step<double>(V, ldv, j, n2, part, tickets, coef, st, s);
+    scale_by_kernel<<<152 * 4, 256, 0, s>>>(w, n2, st.status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_inv_df(size_t N, const double* x, const double* s, double* y_df,
+                                cudaStream_t st) {
+  scale_inv_df_kernel<<<krylov_blocks(), KT, 0, st>>>(N, x, s, reinterpret_cast<df*>(y_df));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_df(const double* Z_df, size_t ldz, int k, const double* c, double* x,
+                             size_t N, cudaStream_t st) {
+  if (k > kDcgsMax) return cudaErrorInvalidValue;
+  update_df_kernel<<<krylov_blocks(), KT, 0, st>>>(reinterpret_cast<const df*>(Z_df), ldz, k, c,
+                                                   x, N);
   return cudaGetLastError();
 }
 

@@ -164,11 +164,15 @@ cudaError_t launch_prolong_add(const T* XC, int n1, int n2, T* X, cudaStream_t s
   return cudaGetLastError();
 }
 
+// Y = scale X; at scale 1 (the V-cycle's input and output) FP32 <-> FP64 runs
+// through the integer conversions, bit-identical to the FP64 instructions,
+// which run at the FP64 rate on GB300
 template <typename TI, typename TO>
 __global__ void convert_kernel(size_t N, const TI* __restrict__ X, double scale, TO* Y) {
+  const bool unit = scale == 1.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
        i += (size_t)gridDim.x * blockDim.x)
-    Y[i] = (TO)(scale * (double)X[i]);
+    Y[i] = unit ? cvt<TO>(X[i]) : (TO)(scale * (double)X[i]);
 }
 
 template <typename TI, typename TO>
@@ -651,6 +655,72 @@ template cudaError_t launch_g_level_op<float>(int, const GLevelOp<float>*, const
 INST_T(double)
 INST_T(float)
 template cudaError_t launch_transpose<df>(const df*, int, int, df*, int, cudaStream_t);
+// ---------------------------------------------------------------- conversion self-test
+// input i: 64 bits of splitmix64 (Steele, Lea and Flood 2014) of seed + i,
+// shaped by i mod 4 into a raw bit pattern, a value with exponent in
+// [-160, 160], a round-to-nearest tie of the FP32 significand, or a value
+// with exponent in [-100, 100] for the double-float split
+__global__ void conversion_selftest_kernel(unsigned long long seed, long long n,
+                                           unsigned long long* bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + (unsigned long long)i * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const int mode = (int)(i & 3);
+    const unsigned long long sign = z & (1ull << 63);
+    unsigned long long mant = z & 0xFFFFFFFFFFFFFull;
+    long long ex;
+    if (mode == 0) ex = (long long)((z >> 52) & 0x7FF);
+    else if (mode == 3) ex = 1023 + (long long)((z >> 52) % 201) - 100;
+    else ex = 1023 + (long long)((z >> 52) % 321) - 160;
+    if (mode == 2) mant = (mant & ~0x1FFFFFFFull) | (1ull << 28);  // exact tie
+    if (i < 16) {  // zeros, infinities, NaN, extreme subnormal / normal doubles
+      const unsigned long long sp[8] = {0ull, 0x7FFull << 52, (0x7FFull << 52) | 1ull, 1ull,
+                                        0xFFFFFFFFFFFFFull, 1ull << 52, 0x7FEFFFFFFFFFFFFFull,
+                                        0x3810000000000000ull};
+      ex = -1;
+      z = sp[i & 7] | ((i & 8) ? (1ull << 63) : 0ull);
+    }
+    const double x = ex < 0 ? __longlong_as_double((long long)z)
+                            : __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | mant));
+    unsigned long long nbad = 0;
+    const float a = d2f_bits(x), b = __double2float_rn(x);
+    if (!((isnan(a) && isnan(b)) || __float_as_uint(a) == __float_as_uint(b))) ++nbad;
+    const float f = __uint_as_float((unsigned)(z >> 32));
+    const double c = f2d_bits(f), d = (double)f;
+    if (!((isnan(c) && isnan(d)) ||
+          __double_as_longlong(c) == __double_as_longlong(d)))
+      ++nbad;
+    const double ax = fabs(x);
+    if (ax <= 0x1p100) {
+      const df s = df_from_bits(x);
+      const double err = fabs(((double)s.hi + (double)s.lo) - x);
+      if (!(err <= (ax >= 0x1p-73 ? 0x1p-47 * ax : 0x1p-97))) ++nbad;
+    }
+    if (nbad) atomicAdd(bad, nbad);
+  }
+}
+
+int conversion_selftest(long long n, long long* mismatches) {
+  unsigned long long* bad = nullptr;
+  if (cudaMalloc(&bad, sizeof(unsigned long long)) != cudaSuccess) return 1;
+  cudaMemset(bad, 0, sizeof(unsigned long long));
+  conversion_selftest_kernel<<<152 * 8, 256>>>(0x243F6A8885A308D3ull, n, bad);
+  unsigned long long h = 0;
+  const cudaError_t e1 = cudaGetLastError();
+  const cudaError_t e2 = cudaMemcpy(&h, bad, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(bad);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) return 1;
+  *mismatches = (long long)h;
+  return 0;
+}
+
+template cudaError_t launch_convert<df, float>(size_t, const df*, double, float*, cudaStream_t);
+template cudaError_t launch_convert<float, df>(size_t, const float*, double, df*, cudaStream_t);
+template cudaError_t launch_convert<df, double>(size_t, const df*, double, double*, cudaStream_t);
+template cudaError_t launch_convert<double, df>(size_t, const double*, double, df*, cudaStream_t);
 template cudaError_t launch_convert<double, float>(size_t, const double*, double, float*,
                                                    cudaStream_t);
 template cudaError_t launch_convert<float, double>(size_t, const float*, double, double*,

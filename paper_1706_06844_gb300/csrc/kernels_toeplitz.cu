@@ -220,8 +220,8 @@ __device__ __forceinline__ void fft_pass_pair(const T* __restrict__ X, int es, i
   for (int i = threadIdx.x; i < L; i += blockDim.x) {
     cx<R> z = {R(0), R(0)};
     if (i < n) {  // x_v[i] packed as re (vector va) + i im (vector va + 1)
-      z.re = R(X[oa + (size_t)i * es]);
-      if (hasb) z.im = R(X[ob + (size_t)i * es]);
+      z.re = cvt<R>(X[oa + (size_t)i * es]);
+      if (hasb) z.im = cvt<R>(X[ob + (size_t)i * es]);
     }
     a[pad(i)] = z;
   }
@@ -238,15 +238,15 @@ __device__ __forceinline__ void fft_pass_pair(const T* __restrict__ X, int es, i
     const size_t ia = oa + (size_t)i * es;
     const cx<R> ya_ = a[pad(i)], yc_ = c[pad(i)];
     R y = ya_.re * coef<R, C>(cp, ia) + yc_.re * coef<R, C>(cm, ia);
-    if (M) y += cmass * R(M[ia]);
-    if (accumulate) y += R(Y[ia]);
-    Y[ia] = T(y);
+    if (M) y += cmass * cvt<R>(M[ia]);
+    if (accumulate) y += cvt<R>(Y[ia]);
+    Y[ia] = cvt<T>(y);
     if (hasb) {
       const size_t ib = ob + (size_t)i * es;
       R yb = ya_.im * coef<R, C>(cp, ib) + yc_.im * coef<R, C>(cm, ib);
-      if (M) yb += cmass * R(M[ib]);
-      if (accumulate) yb += R(Y[ib]);
-      Y[ib] = T(yb);
+      if (M) yb += cmass * cvt<R>(M[ib]);
+      if (accumulate) yb += cvt<R>(Y[ib]);
+      Y[ib] = cvt<T>(yb);
     }
   }
   __syncthreads();
@@ -326,8 +326,8 @@ fft_pass_seq_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, in
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
       cx<R> z = {R(0), R(0)};
       if (i < n) {
-        z.re = R(X[oa + (size_t)i * es]);
-        if (hasb) z.im = R(X[ob + (size_t)i * es]);
+        z.re = cvt<R>(X[oa + (size_t)i * es]);
+        if (hasb) z.im = cvt<R>(X[ob + (size_t)i * es]);
       }
       a[pad(i)] = z;
     }
@@ -344,15 +344,15 @@ fft_pass_seq_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, in
       const size_t ia = oa + (size_t)i * es;
       const cx<R> ya_ = a[pad(i)];
       R y = ya_.re * coef<R, C>(cp, ia);
-      if (M) y += cmass * R(M[ia]);
-      if (accumulate) y += R(Y[ia]);
-      Y[ia] = T(y);
+      if (M) y += cmass * cvt<R>(M[ia]);
+      if (accumulate) y += cvt<R>(Y[ia]);
+      Y[ia] = cvt<T>(y);
       if (hasb) {
         const size_t ib = ob + (size_t)i * es;
         R yb = ya_.im * coef<R, C>(cp, ib);
-        if (M) yb += cmass * R(M[ib]);
-        if (accumulate) yb += R(Y[ib]);
-        Y[ib] = T(yb);
+        if (M) yb += cmass * cvt<R>(M[ib]);
+        if (accumulate) yb += cvt<R>(Y[ib]);
+        Y[ib] = cvt<T>(yb);
       }
     }
     __syncthreads();
@@ -362,10 +362,10 @@ fft_pass_seq_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, in
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const size_t ia = oa + (size_t)i * es;
       const cx<R> yc_ = a[pad(i)];
-      Y[ia] = T(R(Y[ia]) + yc_.re * coef<R, C>(cm, ia));
+      Y[ia] = cvt<T>(cvt<R>(Y[ia]) + yc_.re * coef<R, C>(cm, ia));
       if (hasb) {
         const size_t ib = ob + (size_t)i * es;
-        Y[ib] = T(R(Y[ib]) + yc_.im * coef<R, C>(cm, ib));
+        Y[ib] = cvt<T>(cvt<R>(Y[ib]) + yc_.im * coef<R, C>(cm, ib));
       }
     }
     __syncthreads();
@@ -591,6 +591,14 @@ template cudaError_t launch_fft_pass<double, df, df>(const double*, int, int, in
                                                      const cx<df>*, const cx<df>*,
                                                      const cx<df>*, const df*, const df*,
                                                      const double*, double, double*, int,
+                                                     cudaStream_t, cx<df>*, size_t);
+template cudaError_t launch_fft_pass<df, float, float>(
+    const df*, int, int, int, int, int, const cx<float>*, const cx<float>*, const cx<float>*,
+    const float*, const float*, const df*, double, df*, int, cudaStream_t, cx<float>*, size_t);
+template cudaError_t launch_fft_pass<df, df, df>(const df*, int, int, int, int, int,
+                                                     const cx<df>*, const cx<df>*,
+                                                     const cx<df>*, const df*, const df*,
+                                                     const df*, double, df*, int,
                                                      cudaStream_t, cx<df>*, size_t);
 template cudaError_t launch_build_spectra<df>(const double*, int, int, double, cx<df>*, cx<df>*,
                                               cx<df>*, cudaStream_t, cx<double>*);

@@ -196,12 +196,26 @@ struct fde_handle {
 // ============================================================================
 // multigrid hierarchy
 
+// the finest level's right-hand side from the Krylov vector r, and the
+// Krylov vector z from the cycle's result (FP64 or double-float vectors)
+template <typename T>
+inline cudaError_t vcycle_in(bool df_io, size_t N, const double* r, T* b, cudaStream_t st) {
+  return df_io ? launch_convert<df, T>(N, reinterpret_cast<const df*>(r), 1.0, b, st)
+               : launch_convert<double, T>(N, r, 1.0, b, st);
+}
+template <typename T>
+inline cudaError_t vcycle_out(bool df_io, size_t N, const T* x, double* z, cudaStream_t st) {
+  return df_io ? launch_convert<T, df>(N, x, 1.0, reinterpret_cast<df*>(z), st)
+               : launch_convert<T, double>(N, x, 1.0, z, st);
+}
+
 struct MGBase {
   virtual ~MGBase() {
     if (graph) cudaGraphExecDestroy(graph);
   }
   virtual int setup(fde_handle* h) = 0;  // from h->dpN.. (FP64, unscaled)
-  virtual int vcycle(fde_handle* h, const double* r, double* z) = 0;
+  // z = V(r); df_io: r and z hold double-float vectors (8 bytes an element)
+  virtual int vcycle(fde_handle* h, const double* r, double* z, bool df_io) = 0;
   virtual int level_apply(fde_handle* h, int l, const double* x, double* y) = 0;
   // one V-cycle on the finest level's (b -> x) buffers: a fixed sequence of
   // launches on fixed buffers, so it can be replayed from a CUDA graph
@@ -719,9 +733,9 @@ struct MG : MGBase {
 
   int cycle_root(fde_handle* h) override { return cycle(h, 0); }
 
-  int vcycle(fde_handle* h, const double* r, double* z) override {
+  int vcycle(fde_handle* h, const double* r, double* z, bool df_io) override {
     Lv& L = lv[0];
-    LCHK((launch_convert<double, T>(L.N, r, 1.0, L.b, h->st)));
+    LCHK(vcycle_in<T>(df_io, L.N, r, L.b, h->st));
     RCHK(run_cycle(h));
     // a one-level hierarchy is the coarsest-grid solve itself, exact up to
     // rounding: further cycles are skipped (level 0 then has no product path)
@@ -738,7 +752,7 @@ struct MG : MGBase {
         LCHK(launch_add<T>(L.N, acc_x, L.x, L.x, h->st));
       }
     }
-    LCHK((launch_convert<T, double>(L.N, L.x, 1.0, z, h->st)));
+    LCHK(vcycle_out<T>(df_io, L.N, L.x, z, h->st));
     return FDE_OK;
   }
 
@@ -912,9 +926,9 @@ struct StencilMG : MGBase {
   T* root_out = nullptr;  // finest-level buffer holding a cycle's result
   int cycle_root(fde_handle* h) override { return cycle(h, 0, &root_out); }
 
-  int vcycle(fde_handle* h, const double* r, double* z) override {
+  int vcycle(fde_handle* h, const double* r, double* z, bool df_io) override {
     Lv& L = lv[0];
-    LCHK((launch_convert<double, T>(L.N, r, 1.0, L.b, h->st)));
+    LCHK(vcycle_in<T>(df_io, L.N, r, L.b, h->st));
     RCHK(run_cycle(h));
     const int cycles = h->p.cycles > 1 ? h->p.cycles : 1;
     if (cycles > 1) {
@@ -927,7 +941,7 @@ struct StencilMG : MGBase {
         LCHK(launch_add<T>(L.N, acc_x, root_out, root_out, h->st));
       }
     }
-    LCHK((launch_convert<T, double>(L.N, root_out, 1.0, z, h->st)));
+    LCHK(vcycle_out<T>(df_io, L.N, root_out, z, h->st));
     return FDE_OK;
   }
 
@@ -1079,9 +1093,10 @@ struct DenseMG : MGBase {
   double* root_out = nullptr;
   int cycle_root(fde_handle* h) override { return cycle(h, 0, &root_out); }
 
-  int vcycle(fde_handle* h, const double* r, double* z) override {
+  int vcycle(fde_handle* h, const double* r, double* z, bool df_io) override {
     Lv& L = lv[0];
-    CCHK(cudaMemcpyAsync(L.b, r, L.N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    if (df_io) LCHK(vcycle_in<double>(true, L.N, r, L.b, h->st));
+    else CCHK(cudaMemcpyAsync(L.b, r, L.N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     RCHK(run_cycle(h));
     const int cycles = (h->p.cycles > 1 && lv.size() > 1) ? h->p.cycles : 1;
     if (cycles > 1) {
@@ -1095,7 +1110,8 @@ struct DenseMG : MGBase {
         LCHK(launch_add<double>(L.N, acc_x, root_out, root_out, h->st));
       }
     }
-    CCHK(cudaMemcpyAsync(z, root_out, L.N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    if (df_io) LCHK(vcycle_out<double>(true, L.N, root_out, z, h->st));
+    else CCHK(cudaMemcpyAsync(z, root_out, L.N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     return FDE_OK;
   }
 

@@ -69,6 +69,7 @@ SIGNATURES = {
     "fde_get_state": (ctypes.c_int, [_VP, _IP, _DP]),
     "fde_set_state": (ctypes.c_int, [_VP, ctypes.c_int]),
     "fde_wait_selftest": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "fde_conversion_selftest": (ctypes.c_int, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
     "fde_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "fde_profile_query": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_double)]),
@@ -223,6 +224,12 @@ def fde_set_state(h, m):
 
 def fde_wait_selftest(h, complete):
     return _check(h, lib().fde_wait_selftest(h, int(complete)))
+
+
+def fde_conversion_selftest(n):
+    bad = ctypes.c_longlong()
+    _check(None, lib().fde_conversion_selftest(int(n), ctypes.byref(bad)))
+    return bad.value
 
 
 def fde_profile_enable(h, on):
