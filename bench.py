@@ -298,11 +298,15 @@ def method_work(n, k, n_outer, n_relaxed):
       outer      FP64-accurate applies (rhs, double-float matvecs, true
                  residuals): read x and four coefficient fields, write y:
                  48 N bytes each;
-      relaxed    FP32 Krylov matvecs on FP64 vectors: x (8 N), four FP32
-                 coefficient fields (16 N), y (8 N): 32 N bytes each;
-      krylov     CGS2: at iteration j (j + 1 basis vectors) two projections
-                 and two updates read the basis four times: sum 4 (j+1) 8 N =
-                 2 k (k+1) 8 N bytes;
+      relaxed    FP32 Krylov matvecs on 8-byte (double-float) vectors: x
+                 (8 N), four FP32 coefficient fields (16 N), y (8 N): 32 N
+                 bytes each;
+      krylov     CGS2 as the method's reference count: at iteration j (j + 1
+                 basis vectors) two projections and two updates read the
+                 basis four times: sum 4 (j+1) 8 N = 2 k (k+1) 8 N bytes (the
+                 delayed scheme that runs reads it twice and writes two
+                 vectors: sum (2 (j+2) + 4) 8 N, about 0.7 of this at k = 13,
+                 so a fraction f here is about 0.7 f of HBM in bytes moved);
       mg         the V-cycle's smoothing and transfers (FP32): per level
                  below the coarsest, Jacobi from zero (W, b -> x: 3 N_l),
                  residual (K x, b -> r: 3 N_l), restriction (r -> b_c: 1.25
@@ -321,6 +325,14 @@ def method_work(n, k, n_outer, n_relaxed):
         "mg": {"work": float(k * (24 * N + sum(14.5 * 4 * m * m for m in lv[:-1]))),
                "unit": "byte"},
     }
+
+
+def level_paths(w):
+    """Product path of every multigrid level of a workload's handle."""
+    fde = w.fde
+    names = {fde.FDE_PATH_GEMM: "gemm", fde.FDE_PATH_FFT: "fft", fde.FDE_PATH_DIRECT: "direct"}
+    return [names.get(fde.fde_level_path(w.h, l), "dense-inverse")
+            for l in range(len(fde.fde_levels(w.h)))]
 
 
 def _sha256(path):
@@ -558,7 +570,6 @@ def sub_n4095(reps=3):
     n = 4095
     out = {"workload": "perturbed power-law, n=4095, alpha=1.9, beta=1.2, FGMRES(20), rtol 1e-8",
            "precision": "BF16x3 tensor-core products read as the TF32-class preconditioner"}
-    names = {fde.FDE_PATH_GEMM: "gemm", fde.FDE_PATH_FFT: "fft", fde.FDE_PATH_DIRECT: "direct"}
     for name, kw in [("gemm", dict(precision=fde.FDE_PREC_BF16X3, path=fde.FDE_PATH_GEMM,
                                    outer=fde.FDE_OUTER_DF32, relax=1)),
                      ("fft", dict(precision=fde.FDE_PREC_BF16X3, path=fde.FDE_PATH_FFT,
@@ -575,8 +586,7 @@ def sub_n4095(reps=3):
             ms, wall, its, launches, hist = time_steps(w, k, 1, None, keep=(name == "gemm"))
             ent = {"value": round(k / (ms * 1e-3), 4), "unit": "steps/s",
                    "ms_per_step": round(ms / k, 3), "iterations_per_step": its,
-                   "level_paths": [names.get(fde.fde_level_path(w.h, l), "dense-inverse")
-                                   for l in range(len(fde.fde_levels(w.h)))]}
+                   "level_paths": level_paths(w)}
             if name == "gemm":
                 prof, pits, prel = profile_step_classes(w, 1)
                 gl, gms = prof["tc_gemm"]
@@ -814,9 +824,28 @@ def kernel_micro(kind, reps, n=N_GRID):
     """One kernel class in isolation, for profiler captures:
     gemm / gemm3 = level-0 V-cycle products (BF16 / BF16x3 tcgen05 GEMM),
     fft32 = FP32 FFT level products, fft64 / fftdf = the outer apply
-    (FP64 / double-float FFT)."""
+    (FP64 / double-float FFT), step = whole CN steps of the headline solver
+    (its Krylov, matvec and V-cycle kernels, e.g. for a capture of the
+    Gram-Schmidt passes at a smaller n)."""
     import torch
     from paper_1706_06844_gb300 import fde
+    if kind == "step":
+        w = Workload(fde.FDE_PREC_BF16X3, outer=fde.FDE_OUTER_DF32, relax=1, n=n)
+        its = [w.step().iterations for _ in range(2)]
+        for m in range(w.m + 1, w.m + reps + 1):
+            w.source(m)  # the sources of the timed steps, sampled on the host beforehand
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            its.append(w.step().iterations)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel": kind, "n": n, "reps": reps, "iterations": its,
+                          "level_paths": level_paths(w),
+                          "ms_per_call": round(e0.elapsed_time(e1) / reps, 4)}))
+        w.close()
+        return
     prec = {"gemm": fde.FDE_PREC_BF16, "gemm3": fde.FDE_PREC_BF16X3, "fft32": fde.FDE_PREC_FP32,
             "fft64": fde.FDE_PREC_FP64, "fftdf": fde.FDE_PREC_FP64}[kind]
     path = {"gemm": fde.FDE_PATH_GEMM, "gemm3": fde.FDE_PATH_GEMM,
@@ -842,11 +871,13 @@ def kernel_micro(kind, reps, n=N_GRID):
 
 
 def dtype_string(args):
-    parts = ["FP64 Krylov vectors (CGS2, Givens)"]
     if args.outer == "df32":
-        parts.append("double-float rhs/true residual/matvecs")
+        parts = ["double-float (FP32-pair) Krylov vectors with DCGS2 on the FP32 pipes, FP64 "
+                 "Hessenberg/Givens/least squares on the device",
+                 "FP64 x, b and true residual from double-float FFT matvecs"]
     else:
-        parts.append("FP64 rhs/true residual/matvecs")
+        parts = ["FP64 Krylov vectors (DCGS2), FP64 Hessenberg/Givens/least squares",
+                 "FP64 rhs/true residual/matvecs"]
     if args.relax:
         parts.append("FP32 relaxed matvecs near convergence")
     prec = {"bf16x3": "BF16x3", "bf16": "BF16", "fp16": "FP16", "fp32": "FP32"}[args.precision]
@@ -860,7 +891,8 @@ def dtype_string(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", default=None, choices=["gemm", "gemm3", "fft32", "fft64", "fftdf"],
+    ap.add_argument("--kernel", default=None,
+                    choices=["gemm", "gemm3", "fft32", "fft64", "fftdf", "step"],
                     help="time one kernel class alone (for profiler captures)")
     ap.add_argument("--kernel-n", type=int, default=N_GRID)
     ap.add_argument("--reps", type=int, default=5)
@@ -944,11 +976,9 @@ def main():
     ms = shard.max_over_ranks(ms, dist)
     value = world * args.steps / (ms * 1e-3)
     e2e_v, h2d, d2h = e2e_steps(w, max(2, min(args.steps, 4)))
-    names = {fde.FDE_PATH_GEMM: "gemm", fde.FDE_PATH_FFT: "fft", fde.FDE_PATH_DIRECT: "direct"}
-    level_paths = [names.get(fde.fde_level_path(w.h, l), "dense-inverse")
-                   for l in range(len(fde.fde_levels(w.h)))]
+    paths = level_paths(w)
     prof, pits, prel = profile_step_classes(w, 3)
-    roof, classes, step_roof = roofline(w, prof, pits, prel, ms / args.steps, level_paths)
+    roof, classes, step_roof = roofline(w, prof, pits, prel, ms / args.steps, paths)
     vhost = w.vhost
     w.close()
     exact = None
@@ -1009,7 +1039,7 @@ def main():
                                        "p2": "P2"}[args.precond],
                            "cycles": args.cycles, "relaxed_matvec": bool(args.relax),
                            "solver": args.solver, "warm_start": bool(args.warm),
-                           "level_paths": level_paths,
+                           "level_paths": paths,
                            "precision": f"{args.precision} V-cycle products (FP32 vectors), "
                                         f"{args.outer} FFT outer apply",
                            "l2": "inputs larger than L2 (Krylov basis 31 x 33.5 MB)",

@@ -873,13 +873,15 @@ __global__ void __launch_bounds__(CT) dcgs_dots_kernel(const double* __restrict_
   }
 }
 
-// v_j <- v_j / r - sum_g (s_g / r) V_g and w <- w - sum_g a_g V_g - c v_j over
-// a run-time j (two FMAs per basis element; the sums need no registers per g)
-template <typename S>
-__global__ void __launch_bounds__(CT) dcgs_update_kernel(double* V, size_t ldv, int j, size_t n2,
+// v_j <- v_j / r - sum_g (s_g / r) V_g and w <- w - sum_g a_g V_g - c v_j
+// (two FMAs per basis element), j = J unrolled so that a thread's loads of
+// all J basis vectors are in flight together
+template <int J, typename S>
+__global__ void __launch_bounds__(CT) dcgs_update_kernel(double* V, size_t ldv, size_t n2,
                                                          double* part, int nb, unsigned* ticket,
                                                          const double* __restrict__ coef,
                                                          ArnoldiState st) {
+  constexpr int j = J;
   using K = Store<S>;
   using A = typename K::A;
   __shared__ A cs_[kDcgsMax], ca_[kDcgsMax];
@@ -902,8 +904,8 @@ __global__ void __launch_bounds__(CT) dcgs_update_kernel(double* V, size_t ldv, 
     if (j > 0) {
       v0 = K::mul(v0, rinv);
       v1 = K::mul(v1, rinv);
-#pragma unroll 4
-      for (int g = 0; g < j; ++g) {
+#pragma unroll
+      for (int g = 0; g < J; ++g) {
         A x0, x1;
         K::ld(V + (size_t)g * ldv, q, x0, x1);
         v0 = K::fma(cs_[g], x0, v0);
@@ -952,33 +954,33 @@ __global__ void scale_by_df_kernel(double* w, size_t n2, const ArnoldiStatus* s)
 }
 
 template <int J, typename S>
-void launch_dcgs_dots(const double* V, size_t ldv, size_t n2, double* part, unsigned* ticket,
+void launch_dcgs_pair(double* V, size_t ldv, size_t n2, double* part, unsigned* tickets,
                       double* coef, const ArnoldiState& st, cudaStream_t s) {
   const int nb = resident_blocks((const void*)dcgs_dots_kernel<J, S>);
-  dcgs_dots_kernel<J, S><<<nb, CT, 0, s>>>(V, ldv, n2, part, nb, ticket, coef, st);
+  dcgs_dots_kernel<J, S><<<nb, CT, 0, s>>>(V, ldv, n2, part, nb, tickets, coef, st);
+  const int nb2 = resident_blocks((const void*)dcgs_update_kernel<J, S>);
+  dcgs_update_kernel<J, S><<<nb2, CT, 0, s>>>(V, ldv, n2, part, nb2, tickets + 1, coef, st);
 }
 
 template <typename S>
 void launch_dcgs_step(double* V, size_t ldv, int j, size_t n2, double* part, unsigned* tickets,
                       double* coef, const ArnoldiState& st, cudaStream_t s) {
-  using Dots = void (*)(const double*, size_t, size_t, double*, unsigned*, double*,
+  using Pair = void (*)(double*, size_t, size_t, double*, unsigned*, double*,
                         const ArnoldiState&, cudaStream_t);
-  static const Dots dots[kDcgsMax] = {
-      launch_dcgs_dots<0, S>,  launch_dcgs_dots<1, S>,  launch_dcgs_dots<2, S>,
-      launch_dcgs_dots<3, S>,  launch_dcgs_dots<4, S>,  launch_dcgs_dots<5, S>,
-      launch_dcgs_dots<6, S>,  launch_dcgs_dots<7, S>,  launch_dcgs_dots<8, S>,
-      launch_dcgs_dots<9, S>,  launch_dcgs_dots<10, S>, launch_dcgs_dots<11, S>,
-      launch_dcgs_dots<12, S>, launch_dcgs_dots<13, S>, launch_dcgs_dots<14, S>,
-      launch_dcgs_dots<15, S>, launch_dcgs_dots<16, S>, launch_dcgs_dots<17, S>,
-      launch_dcgs_dots<18, S>, launch_dcgs_dots<19, S>, launch_dcgs_dots<20, S>,
-      launch_dcgs_dots<21, S>, launch_dcgs_dots<22, S>, launch_dcgs_dots<23, S>,
-      launch_dcgs_dots<24, S>, launch_dcgs_dots<25, S>, launch_dcgs_dots<26, S>,
-      launch_dcgs_dots<27, S>, launch_dcgs_dots<28, S>, launch_dcgs_dots<29, S>,
-      launch_dcgs_dots<30, S>, launch_dcgs_dots<31, S>};
-  static_assert(kDcgsMax == 32, "one dots instantiation per basis length");
-  dots[j](V, ldv, n2, part, tickets, coef, st, s);
-  const int nb = resident_blocks((const void*)dcgs_update_kernel<S>);
-  dcgs_update_kernel<S><<<nb, CT, 0, s>>>(V, ldv, j, n2, part, nb, tickets + 1, coef, st);
+  static const Pair pairs[kDcgsMax] = {
+      launch_dcgs_pair<0, S>,  launch_dcgs_pair<1, S>,  launch_dcgs_pair<2, S>,
+      launch_dcgs_pair<3, S>,  launch_dcgs_pair<4, S>,  launch_dcgs_pair<5, S>,
+      launch_dcgs_pair<6, S>,  launch_dcgs_pair<7, S>,  launch_dcgs_pair<8, S>,
+      launch_dcgs_pair<9, S>,  launch_dcgs_pair<10, S>, launch_dcgs_pair<11, S>,
+      launch_dcgs_pair<12, S>, launch_dcgs_pair<13, S>, launch_dcgs_pair<14, S>,
+      launch_dcgs_pair<15, S>, launch_dcgs_pair<16, S>, launch_dcgs_pair<17, S>,
+      launch_dcgs_pair<18, S>, launch_dcgs_pair<19, S>, launch_dcgs_pair<20, S>,
+      launch_dcgs_pair<21, S>, launch_dcgs_pair<22, S>, launch_dcgs_pair<23, S>,
+      launch_dcgs_pair<24, S>, launch_dcgs_pair<25, S>, launch_dcgs_pair<26, S>,
+      launch_dcgs_pair<27, S>, launch_dcgs_pair<28, S>, launch_dcgs_pair<29, S>,
+      launch_dcgs_pair<30, S>, launch_dcgs_pair<31, S>};
+  static_assert(kDcgsMax == 32, "one instantiation per basis length");
+  pairs[j](V, ldv, n2, part, tickets, coef, st, s);
 }
 
 // y = x / *s as double-float (the first basis vector of a restart cycle)
