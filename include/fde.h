@@ -61,7 +61,7 @@ extern "C" {
                                      (Sec. 4, TGM step 3; the paper's tilde-P_MGM, Sec. 5.1):
                                      a validation mode for small grids, n1 n2 <= 4096, FP64 only */
 
-/* arithmetic of the preconditioner (the outer Krylov method is always FP64) */
+/* arithmetic of the preconditioner (the outer Krylov method is FP64-accurate: see FDE_OUTER_*) */
 #define FDE_PREC_FP64          0  /* V-cycle in FP64 ("plain FP64" solver) */
 #define FDE_PREC_FP32          1  /* V-cycle vectors and Toeplitz products in FP32 */
 #define FDE_PREC_BF16          2  /* FP32 vectors, Toeplitz products on tcgen05 in BF16 with FP32 accumulation */
@@ -81,8 +81,12 @@ extern "C" {
                                      keeps the fastest */
 
 /* arithmetic of the FP64-accurate outer apply (Krylov matvec, true residual, rhs) */
-#define FDE_OUTER_FP64         0  /* FFT in FP64 */
-#define FDE_OUTER_DF32         1  /* FFT in double-float (pairs of FP32), ~48-bit significand */
+#define FDE_OUTER_FP64         0  /* FFT in FP64; FGMRES vectors and Gram-Schmidt in FP64 */
+#define FDE_OUTER_DF32         1  /* FFT in double-float (pairs of FP32), ~48-bit significand;
+                                     with restart <= 32 the single-problem FGMRES also keeps its
+                                     basis vectors in double-float and runs Gram-Schmidt on the
+                                     FP32 pipes (x, b and the true residual stay FP64; the
+                                     Hessenberg matrix, rotations and least squares are FP64) */
 
 /* coefficient time levels */
 #define FDE_COEF_NEW           0  /* d+-, e+- at t^(m): the system matrix M^(m) */
