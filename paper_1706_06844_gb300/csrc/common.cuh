@@ -125,6 +125,15 @@ cudaError_t launch_mul(size_t N, const T* W, const T* B, T* Y, cudaStream_t st);
 // coarse b_c = rscale * P^T r (bilinear P of the transfer above, any fine sizes)
 template <typename T>
 cudaError_t launch_restrict(const T* R, int n1, int n2, double rscale, T* BC, cudaStream_t st);
+// restriction of the residual B - KX without storing it
+template <typename T>
+cudaError_t launch_restrict_residual(const T* B, const T* KX, int n1, int n2, double rscale,
+                                     T* BC, cudaStream_t st);
+// the Jacobi sweep from zero X = W B fused into the mass-term pre-pass of X
+template <typename T>
+cudaError_t launch_jacobi_mass_prepass(const T* W, const T* B, int n1, int n2, double bx0,
+                                       double bx1, double by0, double by1, double c, T* X,
+                                       T* XBY, T* XBX, T* MASS, cudaStream_t st);
 
 // X += P x_c
 template <typename T>

@@ -13,19 +13,26 @@ static inline int grid_for(size_t N, int threads) {
 }
 
 // ---------------------------------------------------------------- level ops
+// W, B non-null: x is first the Jacobi sweep from zero, x = W b, formed at
+// every point it is read and written to X (one pass instead of two; the same
+// products, so the same values)
 template <typename T>
-__global__ void mass_prepass_kernel(const T* __restrict__ X, int n1, int n2, T bx0, T bx1, T by0,
-                                    T by1, T c, T* __restrict__ XBY, T* __restrict__ XBX,
-                                    T* __restrict__ MASS) {
+__global__ void mass_prepass_kernel(T* X, int n1, int n2, T bx0, T bx1, T by0, T by1, T c,
+                                    T* __restrict__ XBY, T* __restrict__ XBX,
+                                    T* __restrict__ MASS, const T* __restrict__ W,
+                                    const T* __restrict__ B) {
   const size_t N = (size_t)n1 * n2;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx % n1), j = (int)(idx / n1);
     auto at = [&](int jj, int ii) -> T {
-      return (ii >= 0 && ii < n1 && jj >= 0 && jj < n2) ? X[(size_t)jj * n1 + ii] : T(0);
+      if (ii < 0 || ii >= n1 || jj < 0 || jj >= n2) return T(0);
+      const size_t k = (size_t)jj * n1 + ii;
+      return W ? W[k] * B[k] : X[k];
     };
     // (B_y (x) I) x: tridiagonal along y;  (I (x) B_x) x: along x
-    const T xc = X[idx];
+    const T xc = at(j, i);
+    if (W) X[idx] = xc;
     const T up = at(j - 1, i), dn = at(j + 1, i), lf = at(j, i - 1), rt = at(j, i + 1);
     XBY[idx] = by1 * up + by0 * xc + by1 * dn;
     XBX[idx] = bx1 * lf + bx0 * xc + bx1 * rt;
@@ -40,8 +47,19 @@ template <typename T>
 cudaError_t launch_mass_prepass(const T* X, int n1, int n2, double bx0, double bx1, double by0,
                                 double by1, double c, T* XBY, T* XBX, T* MASS, cudaStream_t st) {
   const size_t N = (size_t)n1 * n2;
-  mass_prepass_kernel<T><<<grid_for(N, 256), 256, 0, st>>>(X, n1, n2, T(bx0), T(bx1), T(by0),
-                                                           T(by1), T(c), XBY, XBX, MASS);
+  mass_prepass_kernel<T><<<grid_for(N, 256), 256, 0, st>>>(
+      const_cast<T*>(X), n1, n2, T(bx0), T(bx1), T(by0), T(by1), T(c), XBY, XBX, MASS, nullptr,
+      nullptr);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_jacobi_mass_prepass(const T* W, const T* B, int n1, int n2, double bx0,
+                                       double bx1, double by0, double by1, double c, T* X,
+                                       T* XBY, T* XBX, T* MASS, cudaStream_t st) {
+  const size_t N = (size_t)n1 * n2;
+  mass_prepass_kernel<T><<<grid_for(N, 256), 256, 0, st>>>(
+      X, n1, n2, T(bx0), T(bx1), T(by0), T(by1), T(c), XBY, XBX, MASS, W, B);
   return cudaGetLastError();
 }
 
@@ -107,9 +125,11 @@ cudaError_t launch_mul(size_t N, const T* W, const T* B, T* Y, cudaStream_t st) 
 
 // b_c = rscale * (P_y (x) P_x)^T r, P column stencil (1/2, 1, 1/2) centred on
 // fine coarse_at(n, c), truncated at the ends of each axis
+// B non-null: restrict the residual B - R, formed at every point it is read
+// (the same subtraction as a separate residual pass, so the same values)
 template <typename T>
 __global__ void restrict_kernel(const T* __restrict__ R, int n1, int n2, T rscale,
-                                T* __restrict__ BC) {
+                                T* __restrict__ BC, const T* __restrict__ B) {
   const int m1 = coarse_n(n1), m2 = coarse_n(n2);
   const size_t NC = (size_t)m1 * m2;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < NC;
@@ -121,10 +141,11 @@ __global__ void restrict_kernel(const T* __restrict__ R, int n1, int n2, T rscal
     for (int dj = -1; dj <= 1; ++dj) {
       const int jj = j + dj;
       if (jj < 0 || jj >= n2) continue;
-      const T* r = R + (size_t)jj * n1;
-      T sr = r[i];
-      if (i > 0) sr += h * r[i - 1];
-      if (i + 1 < n1) sr += h * r[i + 1];
+      const size_t o = (size_t)jj * n1;
+      auto r = [&](int ii) -> T { return B ? B[o + ii] - R[o + ii] : R[o + ii]; };
+      T sr = r(i);
+      if (i > 0) sr += h * r(i - 1);
+      if (i + 1 < n1) sr += h * r(i + 1);
       acc += (dj ? h : T(1)) * sr;
     }
     BC[idx] = rscale * acc;
@@ -134,7 +155,15 @@ __global__ void restrict_kernel(const T* __restrict__ R, int n1, int n2, T rscal
 template <typename T>
 cudaError_t launch_restrict(const T* R, int n1, int n2, double rscale, T* BC, cudaStream_t st) {
   const size_t NC = (size_t)coarse_n(n1) * coarse_n(n2);
-  restrict_kernel<T><<<grid_for(NC, 256), 256, 0, st>>>(R, n1, n2, T(rscale), BC);
+  restrict_kernel<T><<<grid_for(NC, 256), 256, 0, st>>>(R, n1, n2, T(rscale), BC, nullptr);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict_residual(const T* B, const T* KX, int n1, int n2, double rscale,
+                                     T* BC, cudaStream_t st) {
+  const size_t NC = (size_t)coarse_n(n1) * coarse_n(n2);
+  restrict_kernel<T><<<grid_for(NC, 256), 256, 0, st>>>(KX, n1, n2, T(rscale), BC, B);
   return cudaGetLastError();
 }
 
@@ -643,6 +672,11 @@ template cudaError_t launch_g_level_op<float>(int, const GLevelOp<float>*, const
                                                 const T*, T*, cudaStream_t);                      \
   template cudaError_t launch_mul<T>(size_t, const T*, const T*, T*, cudaStream_t);               \
   template cudaError_t launch_restrict<T>(const T*, int, int, double, T*, cudaStream_t);          \
+  template cudaError_t launch_restrict_residual<T>(const T*, const T*, int, int, double, T*,      \
+                                                   cudaStream_t);                                 \
+  template cudaError_t launch_jacobi_mass_prepass<T>(const T*, const T*, int, int, double, double,\
+                                                     double, double, double, T*, T*, T*, T*,      \
+                                                     cudaStream_t);                               \
   template cudaError_t launch_prolong_add<T>(const T*, int, int, T*, cudaStream_t);               \
   template cudaError_t launch_inject<T>(const T*, int, int, T*, cudaStream_t);                    \
   template cudaError_t launch_level_fields<T>(const double*, const double*, const double*,        \

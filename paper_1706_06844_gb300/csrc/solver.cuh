@@ -594,15 +594,20 @@ struct MG : MGBase {
     return -1;
   }
 
-  // kx = K_l x (products + mass term)
-  int products(fde_handle* h, size_t l, const T* x, T* kx) {
+  // kx = K_l x (products + mass term); jacobi_from_zero (structured-Galerkin
+  // levels l > 0 only): x is first set to W b in the same pass as the mass terms
+  int products(fde_handle* h, size_t l, const T* x, T* kx, bool jacobi_from_zero = false) {
     Lv& L = lv[l];
     cudaStream_t st = h->st;
     const T *xin_x = x, *xin_y = x, *M = x;
     double cm = h->c;
     if (sg && l > 0) {
-      LCHK(launch_mass_prepass<T>(x, L.n1, L.n2, L.bx0, L.bx1, L.by0, L.by1, h->c, L.xby, L.xbx,
-                                  L.mass, st));
+      if (jacobi_from_zero)
+        LCHK(launch_jacobi_mass_prepass<T>(L.W, L.b, L.n1, L.n2, L.bx0, L.bx1, L.by0, L.by1, h->c,
+                                           const_cast<T*>(x), L.xby, L.xbx, L.mass, st));
+      else
+        LCHK(launch_mass_prepass<T>(x, L.n1, L.n2, L.bx0, L.bx1, L.by0, L.by1, h->c, L.xby,
+                                    L.xbx, L.mass, st));
       xin_x = L.xby;
       xin_y = L.xbx;
       M = L.mass;
@@ -667,16 +672,18 @@ struct MG : MGBase {
       h->pend(pi);
       return FDE_OK;
     }
+    // pre-smoothing from zero: x = W b (on structured-Galerkin levels l > 0
+    // with one sweep, inside the mass-term pass of the residual's products)
+    const bool fused_sweep = p.nu_pre == 1 && sg && l > 0;
     int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
-    if (p.nu_pre >= 1) LCHK(launch_mul<T>(L.N, L.W, L.b, L.x, st));
-    else CCHK(cudaMemsetAsync(L.x, 0, L.N * sizeof(T), st));
+    if (p.nu_pre >= 1 && !fused_sweep) LCHK(launch_mul<T>(L.N, L.W, L.b, L.x, st));
+    else if (p.nu_pre < 1) CCHK(cudaMemsetAsync(L.x, 0, L.N * sizeof(T), st));
     h->pend(pi);
     for (int s = 1; s < p.nu_pre; ++s) RCHK(smooth(h, l));
-    // residual r = b - K x (kept in kx), restriction
-    RCHK(products(h, l, L.x, L.kx));
+    // residual r = b - K x restricted without storing r
+    RCHK(products(h, l, L.x, L.kx, fused_sweep));
     pi = h->pbeg(FDE_KCLASS_MG_OTHER);
-    LCHK(launch_level_epilogue<T>(1, L.N, L.kx, L.b, L.x, L.W, L.kx, st));
-    LCHK(launch_restrict<T>(L.kx, L.n1, L.n2, rscale, lv[l + 1].b, st));
+    LCHK(launch_restrict_residual<T>(L.b, L.kx, L.n1, L.n2, rscale, lv[l + 1].b, st));
     h->pend(pi);
     RCHK(cycle(h, l + 1));
     pi = h->pbeg(FDE_KCLASS_MG_OTHER);
