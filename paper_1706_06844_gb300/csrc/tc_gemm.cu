@@ -37,7 +37,6 @@
 #include <cuda_fp16.h>
 #include <cstdint>
 #include <cstring>
-#include <type_traits>
 
 #include "tc_gemm.h"
 
@@ -78,18 +77,11 @@ struct Cfg {
   // + 1 KB alignment slack + 256 B barriers + one generator window per X slot and term
   static constexpr size_t FIXED = (size_t)RINGS + 1024 + 256 + (size_t)SA * NT * WIN_BYTES;
 };
-// epilogue staging per warp -- DIR 0: the transposed accumulators (2 x 32 x
-// 33 floats) and DEP operand buffers of EB rows; DIR 1: DEP operand buffers
-// of EB columns -- must fit in the pipeline stages it reuses
-template <int NT>
-struct Epi {
-  static constexpr int EB = NT == 2 ? 16 : 8;  // rows (DIR 0) / columns (DIR 1) per batch
-  static constexpr int BPB = 32 / EB;          // batches per 32-column block
-  static constexpr int STG = 2 * 32 * 33, OPD = 3 * EB * 32;  // floats
-  static constexpr int DEP = 2;                // operand buffers (batches in flight + 1)
-};
-static_assert(NSYN * (Epi<1>::STG + Epi<1>::DEP * Epi<1>::OPD) * 4 <= Cfg<1>::RINGS, "NT=1 epilogue");
-static_assert(NSYN * (Epi<2>::STG + Epi<2>::DEP * Epi<2>::OPD) * 4 <= Cfg<2>::RINGS, "NT=2 epilogue");
+// epilogue staging (DIR 0: transposed accumulators + operand batches; DIR 1:
+// operand blocks) must fit in the pipeline stages it reuses
+static_assert(8 * (2 * 32 * 33 + 3 * 16 * 32) * 4 <= Cfg<1>::RINGS, "NT=1 DIR0");
+static_assert(8 * (2 * 32 * 33 + 3 * 32 * 32) * 4 <= Cfg<2>::RINGS, "NT=2 DIR0");
+static_assert(8 * (3 * 32 * 32) * 4 <= Cfg<2>::RINGS, "DIR1");
 static_assert(BN % 16 == 0 && BN <= ACC_COLS && 2 * ACC_COLS <= 512, "accumulator layout");
 // padded generator length and the bytes of its forward + reversed copies
 __host__ __device__ constexpr int gen_len(int n) { return (n + GEN_PAD + 7) / 8 * 8; }
@@ -200,14 +192,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __device__ __forceinline__ void cp_async4(float* dst_smem, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst_smem)), "l"(src)
                : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-// wait until at most N committed groups are still in flight
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
@@ -568,135 +552,86 @@ toeplitz_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
       float* __restrict__ wsl =
           split ? kp.ws + ((size_t)DIR * kp.splits + blockIdx.z) * ((size_t)kp.n1 * kp.n2) : nullptr;
       // The freed pipeline stages hold the epilogue's operands: each lane
-      // copies its elements with 4-byte cp.async (rows of a length that is no
-      // multiple of 16 bytes rule out bulk copies) and reads them back itself.
+      // copies its elements of a block with 4-byte cp.async (rows of a length
+      // that is no multiple of 16 bytes rule out bulk copies), so all of a
+      // block's loads are in flight together, and reads them back itself.
       const float* __restrict__ c0 = kp.c0;
       const float* __restrict__ c1 = kp.c1;
       float* __restrict__ out = kp.out;
-      // Operands go through DEP buffers of EB rows (columns): while one batch
-      // is computed, the next DEP - 1 batches' copies are in flight (one
-      // commit group per batch, empty past the end).  Batch t covers part
-      // t % BPB of 32-column block t / BPB of this warp's range.
-      using E = Epi<NT>;
-      constexpr int EB = E::EB, BPB = E::BPB;
-      float* stg = reinterpret_cast<float*>(base) + w * (E::STG + E::DEP * E::OPD);
-      float* opdb = stg + E::STG;
-      const int nblk = (c_hi - c_lo + 31) / 32;
-      const int nbatch = BPB * nblk;
       if (DIR == 0) {
         // lanes are grid rows in TMEM: stage through shared memory so lane = column
+        float* stg = reinterpret_cast<float*>(base) + w * (2 * 32 * 33);
+        constexpr int RB = NT == 2 ? 32 : 16;  // rows per batch of copies (fits the stages)
+        float* opd = reinterpret_cast<float*>(base) + NSYN * (2 * 32 * 33) + w * (3 * RB * 32);
         const float* __restrict__ Mm = split ? nullptr : kp.M;
         float* __restrict__ dst = split ? wsl : out;
         const int rbase = m0 + g * 32;
         const int nr = kp.n2 - rbase < 32 ? kp.n2 - rbase : 32;
-        auto issue = [&](int t) {
-          const int cb = c_lo + (t / BPB) * 32, h = (t % BPB) * EB;
-          const int col = out0 + cb + lane;
-          float* opd = opdb + (t % E::DEP) * E::OPD;
-          if (col < kp.n1 && cb + lane < BN)
-            for (int rr = 0; rr < EB && h + rr < nr; ++rr) {
-              const size_t idx = (size_t)(rbase + h + rr) * kp.n1 + col;
-              cp_async4(opd + (0 * EB + rr) * 32 + lane, c0 + idx);
-              cp_async4(opd + (1 * EB + rr) * 32 + lane, c1 + idx);
-              if (Mm) cp_async4(opd + (2 * EB + rr) * 32 + lane, Mm + idx);
-            }
-          cp_async_commit();
-        };
-        for (int t0 = 0; t0 < E::DEP - 1; ++t0) {
-          if (t0 < nbatch) issue(t0);
-          else cp_async_commit();
-        }
-        for (int t = 0; t < nbatch; ++t) {
-          const int cb = c_lo + (t / BPB) * 32, h = (t % BPB) * EB;
+        for (int cb = c_lo; cb < c_hi; cb += 32) {
           const int col = out0 + cb + lane;
           const bool live = col < kp.n1 && cb + lane < BN;
-          if (t % BPB == 0) {
-            __syncwarp();  // the previous block's reads of stg are done
 #pragma unroll
-            for (int a = 0; a < 2; ++a) {
-              float v[32];
-              tmem_ld32(tl + a * ACC_COLS + cb, v);
-              tmem_wait_ld();
+          for (int a = 0; a < 2; ++a) {
+            float v[32];
+            tmem_ld32(tl + a * ACC_COLS + cb, v);
+            tmem_wait_ld();
 #pragma unroll
-              for (int q = 0; q < 32; ++q) stg[(a * 32 + lane) * 33 + q] = on[a] * v[q];
-            }
-            __syncwarp();
+            for (int q = 0; q < 32; ++q) stg[(a * 32 + lane) * 33 + q] = on[a] * v[q];
           }
-          if (t + E::DEP - 1 < nbatch) issue(t + E::DEP - 1);
-          else cp_async_commit();
-          cp_async_wait_group<E::DEP - 1>();
-          const float* opd = opdb + (t % E::DEP) * E::OPD;
-          if (live)
-            for (int rr = 0; rr < EB && h + rr < nr; ++rr) {
-              const size_t idx = (size_t)(rbase + h + rr) * kp.n1 + col;
-              const float m = Mm ? opd[(2 * EB + rr) * 32 + lane] : 0.f;
-              dst[idx] = kp.inv_scale * (opd[(0 * EB + rr) * 32 + lane] * stg[(h + rr) * 33 + lane] +
-                                         opd[(1 * EB + rr) * 32 + lane] *
-                                             stg[(32 + h + rr) * 33 + lane]) +
-                         kp.cm * m;
-            }
+          __syncwarp();
+#pragma unroll
+          for (int h = 0; h < 32; h += RB) {
+            if (live)
+              for (int rr = 0; rr < RB && h + rr < nr; ++rr) {
+                const size_t idx = (size_t)(rbase + h + rr) * kp.n1 + col;
+                cp_async4(opd + (0 * RB + rr) * 32 + lane, c0 + idx);
+                cp_async4(opd + (1 * RB + rr) * 32 + lane, c1 + idx);
+                if (Mm) cp_async4(opd + (2 * RB + rr) * 32 + lane, Mm + idx);
+              }
+            cp_async_wait_all();
+            if (live)
+              for (int rr = 0; rr < RB && h + rr < nr; ++rr) {
+                const size_t idx = (size_t)(rbase + h + rr) * kp.n1 + col;
+                const float m = Mm ? opd[(2 * RB + rr) * 32 + lane] : 0.f;
+                dst[idx] = kp.inv_scale * (opd[(0 * RB + rr) * 32 + lane] * stg[(h + rr) * 33 + lane] +
+                                           opd[(1 * RB + rr) * 32 + lane] *
+                                               stg[(32 + h + rr) * 33 + lane]) +
+                           kp.cm * m;
+              }
+          }
+          __syncwarp();
         }
-        __syncwarp();
       } else {
         // lanes are grid columns i; TMEM columns are grid rows j
+        float* opd = reinterpret_cast<float*>(base) + w * (3 * 32 * 32);
         const int col = m0 + g * 32 + lane;
         const bool live = col < kp.n1;
-        auto rows_of = [&](int cb) {
+        for (int cb = c_lo; cb < c_hi; cb += 32) {
           int nr = kp.n2 - (out0 + cb) < 32 ? kp.n2 - (out0 + cb) : 32;
-          return nr > BN - cb ? BN - cb : nr;
-        };
-        auto issue = [&](int t) {
-          const int cb = c_lo + (t / BPB) * 32, h = (t % BPB) * EB;
-          const int nr = rows_of(cb);
-          float* opd = opdb + (t % E::DEP) * E::OPD;
+          if (nr > BN - cb) nr = BN - cb;
           if (live)
-            for (int q = h; q < h + EB && q < nr; ++q) {
+            for (int q = 0; q < nr; ++q) {
               const size_t idx = (size_t)(out0 + cb + q) * kp.n1 + col;
-              cp_async4(opd + (0 * EB + q - h) * 32 + lane, c0 + idx);
-              cp_async4(opd + (1 * EB + q - h) * 32 + lane, c1 + idx);
-              if (!split) cp_async4(opd + (2 * EB + q - h) * 32 + lane, out + idx);
+              cp_async4(opd + (0 * 32 + q) * 32 + lane, c0 + idx);
+              cp_async4(opd + (1 * 32 + q) * 32 + lane, c1 + idx);
+              if (!split) cp_async4(opd + (2 * 32 + q) * 32 + lane, out + idx);
             }
-          cp_async_commit();
-        };
-        // one half of block cb from registers a0, a1 (H: compile-time row offset)
-        auto finish = [&](auto Hc, int cb, const float* a0, const float* a1, const float* opd) {
-          constexpr int H = decltype(Hc)::value;
-          const int nr = rows_of(cb);
-          if (!live) return;
+          float a0[32], a1[32];
+          tmem_ld32(tl + cb, a0);
+          tmem_ld32(tl + ACC_COLS + cb, a1);
+          tmem_wait_ld();
+          cp_async_wait_all();
+          if (live) {
 #pragma unroll
-          for (int qq = 0; qq < EB; ++qq) {
-            const int q = H + qq;
-            if (q < nr) {
-              const size_t idx = (size_t)(out0 + cb + q) * kp.n1 + col;
-              const float prod = kp.inv_scale * (opd[(0 * EB + qq) * 32 + lane] * on[0] * a0[q] +
-                                                 opd[(1 * EB + qq) * 32 + lane] * on[1] * a1[q]);
-              if (split) wsl[idx] = prod;
-              else out[idx] = opd[(2 * EB + qq) * 32 + lane] + prod;
+            for (int q = 0; q < 32; ++q) {
+              if (q < nr) {
+                const size_t idx = (size_t)(out0 + cb + q) * kp.n1 + col;
+                const float prod = kp.inv_scale * (opd[(0 * 32 + q) * 32 + lane] * on[0] * a0[q] +
+                                                   opd[(1 * 32 + q) * 32 + lane] * on[1] * a1[q]);
+                if (split) wsl[idx] = prod;
+                else out[idx] = opd[(2 * 32 + q) * 32 + lane] + prod;
+              }
             }
-          }
-        };
-        for (int t0 = 0; t0 < E::DEP - 1; ++t0) {
-          if (t0 < nbatch) issue(t0);
-          else cp_async_commit();
-        }
-        float a0[32], a1[32];
-        for (int t = 0; t < nbatch; ++t) {
-          const int cb = c_lo + (t / BPB) * 32;
-          if (t % BPB == 0) {
-            tmem_ld32(tl + cb, a0);
-            tmem_ld32(tl + ACC_COLS + cb, a1);
-            tmem_wait_ld();
-          }
-          if (t + E::DEP - 1 < nbatch) issue(t + E::DEP - 1);
-          else cp_async_commit();
-          cp_async_wait_group<E::DEP - 1>();
-          const float* opd = opdb + (t % E::DEP) * E::OPD;
-          // the register index q = H + qq must be a compile-time constant
-          switch (t % BPB) {
-            case 0: finish(std::integral_constant<int, 0>{}, cb, a0, a1, opd); break;
-            case 1: finish(std::integral_constant<int, EB>{}, cb, a0, a1, opd); break;
-            case 2: finish(std::integral_constant<int, (2 * EB) % 32>{}, cb, a0, a1, opd); break;
-            default: finish(std::integral_constant<int, (3 * EB) % 32>{}, cb, a0, a1, opd); break;
           }
         }
       }
