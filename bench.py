@@ -258,21 +258,24 @@ def time_steps(w, steps, warmup, dist, keep=False):
     return ms, wall, its, w.fde.fde_launch_count(w.h) - l0, hist
 
 
-def e2e_steps(w, steps):
-    """Same steps through fde_step_host: pinned host arrays in, host array out."""
+def e2e_steps(w, steps, warmup=1):
+    """Same steps through fde_step_host: pinned host arrays in, host array out
+    (the first `warmup` of them untimed)."""
     import torch
     n = w.n
     u_host = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
     u_host.copy_(w.u.cpu())
     out = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
     srcs = []
-    for m in range(w.m + 1, w.m + steps + 1):
+    for m in range(w.m + 1, w.m + warmup + steps + 1):
         s = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
         s.copy_(torch.from_numpy(w.prob.source(w.X, w.Y, (m - 0.5) * w.dt)))
         srcs.append(s)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s in srcs:
+    for i, s in enumerate(srcs):
+        if i == warmup:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
         w.fde.fde_step_host(w.h, u_host.data_ptr(), s.data_ptr(), out.data_ptr())
         u_host, out = out, u_host
     torch.cuda.synchronize()
@@ -978,7 +981,7 @@ def main():
                       "(set_coefficients), first step with CUDA-graph capture")
     ms = shard.max_over_ranks(ms, dist)
     value = world * args.steps / (ms * 1e-3)
-    e2e_v, h2d, d2h = e2e_steps(w, max(2, min(args.steps, 4)))
+    e2e_v, h2d, d2h = e2e_steps(w, max(2, min(args.steps, 8)))
     paths = level_paths(w)
     prof, pits, prel = profile_step_classes(w, 3)
     roof, classes, step_roof = roofline(w, prof, pits, prel, ms / args.steps, paths)

@@ -223,7 +223,12 @@ int fde_step(fde_handle* h, const double* u_prev, const double* v_half, double* 
              fde_stats* st);
 
 /* fde_step with HOST arrays: copies u_prev and v_half host->device, runs the
- * step and copies u_next device->host (pageable or pinned host memory). */
+ * step and copies u_next device->host (pageable or page-locked host memory).
+ * With page-locked arrays the copies overlap the computation on a second
+ * stream of the handle (created on the first call): v_half uploads while the
+ * right-hand side's operator apply of u_prev runs, and every FGMRES cycle's
+ * solution is copied to u_next while its true residual is checked (the last
+ * copy is the result).  All copies are complete when the call returns. */
 int fde_step_host(fde_handle* h, const double* u_prev_host, const double* v_half_host,
                   double* u_next_host, fde_stats* st);
 

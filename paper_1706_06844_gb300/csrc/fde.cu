@@ -288,9 +288,21 @@ static int solve_impl(fde_handle* h, const double* b, double* x, fde_stats* st_o
     // y = R^{-1} g, x += Z y (on the device)
     int pi = h->pbeg(FDE_KCLASS_KRYLOV);
     LCHK(launch_arnoldi_lsq(h->ast, k, h->ydev, h->st));
+    // an earlier cycle's copy of x to the host must have read x first
+    if (h->early_issued) CCHK(cudaStreamWaitEvent(h->st, h->x_copied, 0));
     LCHK(dfk ? launch_update_df(h->Z, ldv, k, h->ydev, x, N, h->st)
              : launch_update(h->Z, ldv, k, h->ydev, x, N, h->st));
     h->pend(pi);
+    if (h->early_out) {
+      // fde_step_host: copy this x to the host while the true residual is
+      // formed; if the cycle converges it is the result
+      CCHK(cudaEventRecord(h->x_ready, h->st));
+      CCHK(cudaStreamWaitEvent(h->copy_st, h->x_ready, 0));
+      CCHK(cudaMemcpyAsync(h->early_out, x, N * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->copy_st));
+      CCHK(cudaEventRecord(h->x_copied, h->copy_st));
+      h->early_issued = true;
+    }
     // true residual in FP64
     RCHK(outer_apply(h, x, h->tmp, false));
     LCHK(launch_sub(N, b, h->tmp, h->tmp, h->st));
@@ -549,6 +561,10 @@ void fde_destroy(fde_handle* h) {
   else cudaDeviceSynchronize();
   h->mg.reset();
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  if (h->copy_st) cudaStreamSynchronize(h->copy_st), cudaStreamDestroy(h->copy_st);
+  if (h->v_ready) cudaEventDestroy(h->v_ready);
+  if (h->x_ready) cudaEventDestroy(h->x_ready);
+  if (h->x_copied) cudaEventDestroy(h->x_copied);
   for (void* q : h->allocs) cudaFree(q);
   for (auto& pe : h->pending) {
     cudaEventDestroy(pe.a);
@@ -614,14 +630,21 @@ int fde_set_coefficients(fde_handle* h, int which, const double* dp, const doubl
   return FDE_OK;
 }
 
+// b = c u - A^(m-1) u + 2 h^a v = 2c u - M^(m-1) u + 2 h^a v; v_ready (may be
+// null): an event the stream waits for before v is first read
+static int rhs_impl(fde_handle* h, const double* u_prev, const double* v_half, double* b,
+                    cudaEvent_t v_ready) {
+  if (!h->have_old) return h->fail(FDE_ERR_ARG, "FDE_COEF_OLD coefficients not set");
+  RCHK(outer_apply(h, u_prev, h->tmp, true));
+  if (v_ready) CCHK(cudaStreamWaitEvent(h->st, v_ready, 0));
+  LCHK(launch_lincomb(h->N, 2.0 * h->c, u_prev, -1.0, h->tmp, h->two_h_alpha, v_half, b, h->st));
+  return FDE_OK;
+}
+
 int fde_rhs(fde_handle* h, const double* u_prev, const double* v_half, double* b) {
   if (!h) return FDE_ERR_ARG;
   if (!u_prev || !v_half || !b) return h->fail(FDE_ERR_ARG, "null pointer");
-  if (!h->have_old) return h->fail(FDE_ERR_ARG, "FDE_COEF_OLD coefficients not set");
-  // b = c u - A^(m-1) u + 2 h^a v = 2c u - M^(m-1) u + 2 h^a v
-  RCHK(outer_apply(h, u_prev, h->tmp, true));
-  LCHK(launch_lincomb(h->N, 2.0 * h->c, u_prev, -1.0, h->tmp, h->two_h_alpha, v_half, b, h->st));
-  return FDE_OK;
+  return rhs_impl(h, u_prev, v_half, b, nullptr);
 }
 
 int fde_apply(fde_handle* h, const double* x, double* y) {
@@ -702,12 +725,9 @@ int fde_wait_selftest(fde_handle* h, int complete) {
   return FDE_OK;
 }
 
-int fde_step(fde_handle* h, const double* u_prev, const double* v_half, double* u_next,
-             fde_stats* st) {
-  if (!h) return FDE_ERR_ARG;
-  if (!u_prev || !v_half || !u_next || u_prev == u_next)
-    return h->fail(FDE_ERR_ARG, "null or aliased pointer");
-  RCHK(fde_rhs(h, u_prev, v_half, h->bwork));
+static int step_impl(fde_handle* h, const double* u_prev, const double* v_half, double* u_next,
+                     fde_stats* st, cudaEvent_t v_ready) {
+  RCHK(rhs_impl(h, u_prev, v_half, h->bwork, v_ready));
   if (!h->have_new) return h->fail(FDE_ERR_ARG, "FDE_COEF_NEW coefficients not set");
   const double* x0 = h->p.warm ? u_prev : nullptr;
   NvtxRange range("fde_step");
@@ -723,16 +743,60 @@ int fde_step(fde_handle* h, const double* u_prev, const double* v_half, double* 
   return r;
 }
 
+int fde_step(fde_handle* h, const double* u_prev, const double* v_half, double* u_next,
+             fde_stats* st) {
+  if (!h) return FDE_ERR_ARG;
+  if (!u_prev || !v_half || !u_next || u_prev == u_next)
+    return h->fail(FDE_ERR_ARG, "null or aliased pointer");
+  return step_impl(h, u_prev, v_half, u_next, st, nullptr);
+}
+
 int fde_step_host(fde_handle* h, const double* u_prev_host, const double* v_half_host,
                   double* u_next_host, fde_stats* st) {
   if (!h) return FDE_ERR_ARG;
   if (!u_prev_host || !v_half_host || !u_next_host)
     return h->fail(FDE_ERR_ARG, "null pointer");
+  if (!h->copy_st) {
+    CCHK(cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking));
+    CCHK(cudaEventCreateWithFlags(&h->v_ready, cudaEventDisableTiming));
+    CCHK(cudaEventCreateWithFlags(&h->x_ready, cudaEventDisableTiming));
+    CCHK(cudaEventCreateWithFlags(&h->x_copied, cudaEventDisableTiming));
+  }
+  // copies run beside the computation only from page-locked host memory (from
+  // pageable memory an asynchronous copy blocks the host until it is done)
+  auto pinned = [](const void* p) {
+    cudaPointerAttributes a{};
+    const bool ok = cudaPointerGetAttributes(&a, p) == cudaSuccess && a.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    return ok;
+  };
   CCHK(cudaMemcpyAsync(h->hu, u_prev_host, h->N * 8, cudaMemcpyHostToDevice, h->st));
-  CCHK(cudaMemcpyAsync(h->hv, v_half_host, h->N * 8, cudaMemcpyHostToDevice, h->st));
-  int r = fde_step(h, h->hu, h->hv, h->hx_out, st);
-  if (r != FDE_OK && r != FDE_ERR_NOT_CONVERGED) return r;
-  CCHK(cudaMemcpyAsync(u_next_host, h->hx_out, h->N * 8, cudaMemcpyDeviceToHost, h->st));
+  // the source is first read after the right-hand side's operator apply of
+  // u: its upload overlaps that apply (the previous call ended with a stream
+  // synchronisation, so nothing still reads h->hv)
+  cudaEvent_t v_ready = nullptr;
+  if (pinned(v_half_host)) {
+    CCHK(cudaMemcpyAsync(h->hv, v_half_host, h->N * 8, cudaMemcpyHostToDevice, h->copy_st));
+    CCHK(cudaEventRecord(h->v_ready, h->copy_st));
+    v_ready = h->v_ready;
+  } else {
+    CCHK(cudaMemcpyAsync(h->hv, v_half_host, h->N * 8, cudaMemcpyHostToDevice, h->st));
+  }
+  // the FGMRES solve copies each cycle's x to u_next_host while it checks the
+  // true residual; the copy of the last cycle's x is the result
+  const bool early = h->p.solver == FDE_SOLVER_FGMRES && pinned(u_next_host);
+  h->early_out = early ? u_next_host : nullptr;
+  h->early_issued = false;
+  int r = step_impl(h, h->hu, h->hv, h->hx_out, st, v_ready);
+  h->early_out = nullptr;
+  const bool copied = h->early_issued;
+  h->early_issued = false;
+  if (r != FDE_OK && r != FDE_ERR_NOT_CONVERGED) {
+    cudaStreamSynchronize(h->copy_st);
+    return r;
+  }
+  if (copied) CCHK(cudaStreamSynchronize(h->copy_st));
+  else CCHK(cudaMemcpyAsync(u_next_host, h->hx_out, h->N * 8, cudaMemcpyDeviceToHost, h->st));
   CCHK(cudaStreamSynchronize(h->st));
   return r;
 }

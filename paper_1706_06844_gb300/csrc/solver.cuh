@@ -51,6 +51,16 @@ struct fde_handle {
   fde_params p{};
   cudaStream_t st = nullptr;
   cudaStream_t cap_st = nullptr;  // private stream on which V-cycles are captured into graphs
+  // fde_step_host: the source's upload runs on copy_st, beside the right-hand
+  // side's operator apply, and v_ready orders it before its first use
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t v_ready = nullptr;
+  // ... and each FGMRES cycle's x is copied to early_out (page-locked host
+  // memory) beside the true-residual check: x_ready orders the copy after
+  // the update, x_copied a later update after the copy
+  double* early_out = nullptr;
+  bool early_issued = false;
+  cudaEvent_t x_ready = nullptr, x_copied = nullptr;
   std::string err;
   long long launches = 0;
   int n1 = 0, n2 = 0;

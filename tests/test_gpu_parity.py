@@ -311,6 +311,35 @@ def test_step_host_matches_device_step():
         fde.fde_destroy(h)
 
 
+@pytest.mark.parametrize("restart", [30, 4])
+def test_step_host_pinned_two_steps_match_device_steps(restart):
+    # pinned host arrays: the source's upload overlaps the right-hand side's
+    # operator apply and every restart cycle's solution is copied out while
+    # its true residual is checked (restart 4: several cycles, so later
+    # updates wait for earlier copies); two steps in a row with different
+    # sources give the device path's bits
+    import torch
+    case = Case(inputs.perturbed_power_law(), 127, restart=restart, precision=fde.FDE_PREC_FP32,
+                outer=fde.FDE_OUTER_DF32, relax=1)
+    X, Y, _, _ = case.problem.grid(127, 127)
+    v2 = case.problem.source(X, Y, 1.5 * case.dt)
+    h = case.handle()
+    try:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        u0, s1, s2 = pin(case.u0), pin(case.v), pin(v2)
+        u1, u2 = torch.empty_like(u0).pin_memory(), torch.empty_like(u0).pin_memory()
+        fde.fde_step_host(h, u0.data_ptr(), s1.data_ptr(), u1.data_ptr())
+        fde.fde_step_host(h, u1.data_ptr(), s2.data_ptr(), u2.data_ptr())
+        d0 = dev(case.u0)
+        d1, d2 = torch.empty_like(d0), torch.empty_like(d0)
+        fde.fde_step(h, d0, dev(case.v), d1)
+        fde.fde_step(h, d1, dev(v2), d2)
+        np.testing.assert_array_equal(u1.numpy(), host(d1))
+        np.testing.assert_array_equal(u2.numpy(), host(d2))
+    finally:
+        fde.fde_destroy(h)
+
+
 def test_error_paths():
     # host-side failure injection: bad arguments, non-finite data, too few iterations
     import torch
