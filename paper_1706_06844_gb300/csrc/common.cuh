@@ -82,6 +82,25 @@ cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int log
                             size_t ws_elems = 0);
 // shared-memory bytes a pass of length 2^logL in cx<R> needs with two buffers
 size_t fft_pass_two_buffer_bytes(int logL, size_t cx_bytes);
+// the arguments of one pass (as launch_fft_pass's)
+template <typename T, typename R, typename C>
+struct FftPass {
+  const T* X;
+  int es, vs, nvec, n;
+  const cx<R>*S1, *S2, *tw;
+  const C *cp, *cm;
+  const T* M;
+  double cmass;
+  T* Y;
+  int accumulate;
+};
+// two independent passes of the same length 2^logL in one launch (their row
+// pairs share the grid, so each pass's latency hides behind the other's);
+// results are those of two launch_fft_pass calls.  Falls back to two launches
+// where the one-buffer pass would be needed.
+template <typename T, typename R, typename C>
+cudaError_t launch_fft_pass2(const FftPass<T, R, C>& a, const FftPass<T, R, C>& b, int logL,
+                             cudaStream_t st, cx<R>* ws = nullptr, size_t ws_elems = 0);
 
 // Spectra of the circulant embeddings (length L = 2^logL >= 2n - 1) of A and A^T,
 // A = [t_{i-k}], generator t_d at t[d+1] for d = -1..n-1, scaled by scale/L and

@@ -16,37 +16,46 @@ void set_global_error(const char* msg) { g_create_error = msg; }
 // ============================================================================
 // FP64-accurate outer operator
 
+// The two passes of an outer apply -- the rows of x (with the c x term) and
+// the rows of the transposed grid -- then y += yT^T.  When both FFT lengths
+// agree the passes share one launch (the transpose of x goes first).
+template <typename T, typename R, typename C>
+static int outer_passes(fde_handle* h, const T* x, T* y, T* xT, T* yT, int logLx, int logLy,
+                        const cx<R>* S1x, const cx<R>* S2x, const cx<R>* twx, const C* cpx,
+                        const C* cmx, const cx<R>* S1y, const cx<R>* S2y, const cx<R>* twy,
+                        const C* cpy, const C* cmy, cx<R>* ws, size_t wse) {
+  const FftPass<T, R, C> px{x, 1, h->n1, h->n2, h->n1, S1x, S2x, twx, cpx, cmx, x, h->c, y, 0};
+  const FftPass<T, R, C> py{xT, 1, h->n2, h->n1, h->n2, S1y, S2y, twy, cpy, cmy, nullptr, 0.0,
+                            yT, 0};
+  LCHK(launch_transpose<T>(x, h->n2, h->n1, xT, 0, h->st));
+  if (logLx == logLy) {
+    LCHK((launch_fft_pass2<T, R, C>(px, py, logLx, h->st, ws, wse)));
+  } else {
+    LCHK((launch_fft_pass<T, R, C>(px.X, px.es, px.vs, px.nvec, px.n, logLx, px.S1, px.S2, px.tw,
+                                   px.cp, px.cm, px.M, px.cmass, px.Y, 0, h->st, ws, wse)));
+    LCHK((launch_fft_pass<T, R, C>(py.X, py.es, py.vs, py.nvec, py.n, logLy, py.S1, py.S2, py.tw,
+                                   py.cp, py.cm, nullptr, 0.0, py.Y, 0, h->st, ws, wse)));
+  }
+  LCHK(launch_transpose<T>(yT, h->n1, h->n2, y, 1, h->st));
+  return FDE_OK;
+}
+
 static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
   NvtxRange range("matvec");
+  const int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
   if (h->p.outer == FDE_OUTER_DF32) {
     df* const* cf = old ? h->cfO : h->cfN;
-    const int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
-    cx<df>* ws = reinterpret_cast<cx<df>*>(h->fft_ws);
-    LCHK((launch_fft_pass<double, df, df>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1xd, h->S2xd,
-                                          h->twxd, cf[0], cf[1], x, h->c, y, 0, h->st, ws,
-                                          h->fft_ws_elems)));
     df* const* cfT = old ? h->cfOT : h->cfNT;
-    LCHK(launch_transpose<double>(x, h->n2, h->n1, h->xT, 0, h->st));
-    LCHK((launch_fft_pass<double, df, df>(h->xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1yd,
-                                          h->S2yd, h->twyd, cfT[0], cfT[1], nullptr, 0.0, h->yT, 0,
-                                          h->st, ws, h->fft_ws_elems)));
-    LCHK(launch_transpose<double>(h->yT, h->n1, h->n2, y, 1, h->st));
-    h->pend(pi);
-    return FDE_OK;
+    RCHK((outer_passes<double, df, df>(h, x, y, h->xT, h->yT, h->logLx, h->logLy, h->S1xd,
+                                       h->S2xd, h->twxd, cf[0], cf[1], h->S1yd, h->S2yd, h->twyd,
+                                       cfT[0], cfT[1], reinterpret_cast<cx<df>*>(h->fft_ws),
+                                       h->fft_ws_elems)));
+  } else {
+    RCHK((outer_passes<double, double, double>(
+        h, x, y, h->xT, h->yT, h->logLx, h->logLy, h->S1x, h->S2x, h->twx, old ? h->dpO : h->dpN,
+        old ? h->dmO : h->dmN, h->S1y, h->S2y, h->twy, old ? h->epOsT : h->epNsT,
+        old ? h->emOsT : h->emNsT, h->fft_ws, h->fft_ws_elems)));
   }
-  const double* dp = old ? h->dpO : h->dpN;
-  const double* dm = old ? h->dmO : h->dmN;
-  const int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
-  LCHK((launch_fft_pass<double, double, double>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x, h->S2x,
-                                        h->twx, dp, dm, x, h->c, y, 0, h->st, h->fft_ws,
-                                        h->fft_ws_elems)));
-  const double* epT = old ? h->epOsT : h->epNsT;
-  const double* emT = old ? h->emOsT : h->emNsT;
-  LCHK(launch_transpose<double>(x, h->n2, h->n1, h->xT, 0, h->st));
-  LCHK((launch_fft_pass<double, double, double>(h->xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1y,
-                                                h->S2y, h->twy, epT, emT, nullptr, 0.0, h->yT, 0,
-                                                h->st, h->fft_ws, h->fft_ws_elems)));
-  LCHK(launch_transpose<double>(h->yT, h->n1, h->n2, y, 1, h->st));
   h->pend(pi);
   return FDE_OK;
 }
@@ -55,20 +64,12 @@ static int outer_apply(fde_handle* h, const double* x, double* y, bool old) {
 // double-float outer operator without conversions at its ends
 static int outer_apply_df(fde_handle* h, const double* x_, double* y_) {
   NvtxRange range("matvec");
-  const df* x = reinterpret_cast<const df*>(x_);
-  df* y = reinterpret_cast<df*>(y_);
-  df* xT = reinterpret_cast<df*>(h->xT);
-  df* yT = reinterpret_cast<df*>(h->yT);
   const int pi = h->pbeg(FDE_KCLASS_OUTER_APPLY);
-  cx<df>* ws = reinterpret_cast<cx<df>*>(h->fft_ws);
-  LCHK((launch_fft_pass<df, df, df>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1xd, h->S2xd,
-                                    h->twxd, h->cfN[0], h->cfN[1], x, h->c, y, 0, h->st, ws,
-                                    h->fft_ws_elems)));
-  LCHK(launch_transpose<df>(x, h->n2, h->n1, xT, 0, h->st));
-  LCHK((launch_fft_pass<df, df, df>(xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1yd, h->S2yd,
-                                    h->twyd, h->cfNT[0], h->cfNT[1], nullptr, 0.0, yT, 0, h->st,
-                                    ws, h->fft_ws_elems)));
-  LCHK(launch_transpose<df>(yT, h->n1, h->n2, y, 1, h->st));  // y += yT^T in double-float
+  RCHK((outer_passes<df, df, df>(h, reinterpret_cast<const df*>(x_), reinterpret_cast<df*>(y_),
+                                 reinterpret_cast<df*>(h->xT), reinterpret_cast<df*>(h->yT),
+                                 h->logLx, h->logLy, h->S1xd, h->S2xd, h->twxd, h->cfN[0],
+                                 h->cfN[1], h->S1yd, h->S2yd, h->twyd, h->cfNT[0], h->cfNT[1],
+                                 reinterpret_cast<cx<df>*>(h->fft_ws), h->fft_ws_elems)));
   h->pend(pi);
   return FDE_OK;
 }
@@ -77,21 +78,12 @@ static int outer_apply_df(fde_handle* h, const double* x_, double* y_) {
 // widened)
 static int outer_apply32_df(fde_handle* h, const double* x_, double* y_) {
   NvtxRange range("matvec_fp32");
-  const df* x = reinterpret_cast<const df*>(x_);
-  df* y = reinterpret_cast<df*>(y_);
-  cx<float>* ws = reinterpret_cast<cx<float>*>(h->fft_ws);
-  const size_t wse = h->fft_ws_elems * 2;
-  int pi = h->pbeg(FDE_KCLASS_OUTER_FP32);
-  LCHK((launch_fft_pass<df, float, float>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x32,
-                                          h->S2x32, h->twx32, h->cf32[0], h->cf32[1], x, h->c,
-                                          y, 0, h->st, ws, wse)));
-  df* xT = reinterpret_cast<df*>(h->xT);
-  df* yT = reinterpret_cast<df*>(h->yT);
-  LCHK(launch_transpose<df>(x, h->n2, h->n1, xT, 0, h->st));
-  LCHK((launch_fft_pass<df, float, float>(xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1y32,
-                                          h->S2y32, h->twy32, h->cf32T[0], h->cf32T[1], nullptr,
-                                          0.0, yT, 0, h->st, ws, wse)));
-  LCHK(launch_transpose<df>(yT, h->n1, h->n2, y, 1, h->st));
+  const int pi = h->pbeg(FDE_KCLASS_OUTER_FP32);
+  RCHK((outer_passes<df, float, float>(
+      h, reinterpret_cast<const df*>(x_), reinterpret_cast<df*>(y_), reinterpret_cast<df*>(h->xT),
+      reinterpret_cast<df*>(h->yT), h->logLx, h->logLy, h->S1x32, h->S2x32, h->twx32, h->cf32[0],
+      h->cf32[1], h->S1y32, h->S2y32, h->twy32, h->cf32T[0], h->cf32T[1],
+      reinterpret_cast<cx<float>*>(h->fft_ws), h->fft_ws_elems * 2)));
   h->pend(pi);
   return FDE_OK;
 }
@@ -99,17 +91,11 @@ static int outer_apply32_df(fde_handle* h, const double* x_, double* y_) {
 // y = M^(m) x with FP32 arithmetic on FP64 data (relaxed Krylov matvec)
 static int outer_apply32(fde_handle* h, const double* x, double* y) {
   NvtxRange range("matvec_fp32");
-  cx<float>* ws = reinterpret_cast<cx<float>*>(h->fft_ws);
-  const size_t wse = h->fft_ws_elems * 2;
-  int pi = h->pbeg(FDE_KCLASS_OUTER_FP32);
-  LCHK((launch_fft_pass<double, float, float>(x, 1, h->n1, h->n2, h->n1, h->logLx, h->S1x32,
-                                              h->S2x32, h->twx32, h->cf32[0], h->cf32[1], x,
-                                              h->c, y, 0, h->st, ws, wse)));
-  LCHK(launch_transpose<double>(x, h->n2, h->n1, h->xT, 0, h->st));
-  LCHK((launch_fft_pass<double, float, float>(h->xT, 1, h->n2, h->n1, h->n2, h->logLy, h->S1y32,
-                                              h->S2y32, h->twy32, h->cf32T[0], h->cf32T[1],
-                                              nullptr, 0.0, h->yT, 0, h->st, ws, wse)));
-  LCHK(launch_transpose<double>(h->yT, h->n1, h->n2, y, 1, h->st));
+  const int pi = h->pbeg(FDE_KCLASS_OUTER_FP32);
+  RCHK((outer_passes<double, float, float>(
+      h, x, y, h->xT, h->yT, h->logLx, h->logLy, h->S1x32, h->S2x32, h->twx32, h->cf32[0],
+      h->cf32[1], h->S1y32, h->S2y32, h->twy32, h->cf32T[0], h->cf32T[1],
+      reinterpret_cast<cx<float>*>(h->fft_ws), h->fft_ws_elems * 2)));
   h->pend(pi);
   return FDE_OK;
 }

@@ -283,6 +283,25 @@ fft_pass_kernel(const T* __restrict__ X, int es, int vs, int nvec, int n, int lo
                            accumulate, pair, a, c);
 }
 
+// two passes of the same length in one launch: pairs 0 .. npa-1 of a, then b's
+template <typename T, typename R, typename C>
+__global__ void __launch_bounds__(FftBlock<R>::threads, FftBlock<R>::min_blocks)
+fft_pass2_kernel(const FftPass<T, R, C> pa, const FftPass<T, R, C> pb, int logL) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = 1 << logL;
+  cx<R>* a = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* c = a + padded_len(L);
+  const int npa = (pa.nvec + 1) >> 1, npb = (pb.nvec + 1) >> 1;
+  for (int pair = blockIdx.x; pair < npa + npb; pair += gridDim.x) {
+    if (pair < npa)
+      fft_pass_pair<T, R, C>(pa.X, pa.es, pa.vs, pa.nvec, pa.n, logL, pa.S1, pa.S2, pa.tw, pa.cp,
+                             pa.cm, pa.M, R(pa.cmass), pa.Y, pa.accumulate, pair, a, c);
+    else
+      fft_pass_pair<T, R, C>(pb.X, pb.es, pb.vs, pb.nvec, pb.n, logL, pb.S1, pb.S2, pb.tw, pb.cp,
+                             pb.cm, pb.M, R(pb.cmass), pb.Y, pb.accumulate, pair - npa, a, c);
+  }
+}
+
 // grouped: item (entry, pair) of many problems' passes in one launch
 template <typename T, typename R, typename C>
 __global__ void __launch_bounds__(256)
@@ -423,6 +442,32 @@ cudaError_t launch_fft_pass(const T* X, int es, int vs, int nvec, int n, int log
   const int threads2 = L / 2 < FftBlock<R>::threads ? L / 2 : FftBlock<R>::threads;
   fft_pass_kernel<T, R, C><<<grid, threads2, smem, st>>>(X, es, vs, nvec, n, logL, S1, S2, tw,
                                                          cp, cm, M, cmass, Y, accumulate);
+  return cudaGetLastError();
+}
+
+template <typename T, typename R, typename C>
+cudaError_t launch_fft_pass2(const FftPass<T, R, C>& a, const FftPass<T, R, C>& b, int logL,
+                             cudaStream_t st, cx<R>* ws, size_t ws_elems) {
+  const int L = 1 << logL;
+  const size_t smem = 2 * (size_t)padded_len(L) * sizeof(cx<R>);
+  if (smem > 227 * 1024) {
+    cudaError_t e = launch_fft_pass<T, R, C>(a.X, a.es, a.vs, a.nvec, a.n, logL, a.S1, a.S2, a.tw,
+                                             a.cp, a.cm, a.M, a.cmass, a.Y, a.accumulate, st, ws,
+                                             ws_elems);
+    if (e != cudaSuccess) return e;
+    return launch_fft_pass<T, R, C>(b.X, b.es, b.vs, b.nvec, b.n, logL, b.S1, b.S2, b.tw, b.cp,
+                                    b.cm, b.M, b.cmass, b.Y, b.accumulate, st, ws, ws_elems);
+  }
+  if (smem > 48 * 1024) {
+    cudaError_t e = ensure_max_smem((const void*)fft_pass2_kernel<T, R, C>);
+    if (e != cudaSuccess) return e;
+  }
+  const int npairs = (a.nvec + 1) / 2 + (b.nvec + 1) / 2;
+  const int per_sm = (int)((227 * 1024) / (smem + 1024));
+  int grid = 152 * (per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm));
+  if (grid > npairs) grid = npairs;
+  const int threads = L / 2 < FftBlock<R>::threads ? L / 2 : FftBlock<R>::threads;
+  fft_pass2_kernel<T, R, C><<<grid, threads, smem, st>>>(a, b, logL);
   return cudaGetLastError();
 }
 
@@ -606,6 +651,24 @@ template cudaError_t launch_fft_pass<double, df, df>(const double*, int, int, in
                                                      const cx<df>*, const cx<df>*,
                                                      const cx<df>*, const df*, const df*,
                                                      const double*, double, double*, int,
+                                                     cudaStream_t, cx<df>*, size_t);
+template cudaError_t launch_fft_pass2<float, float, float>(const FftPass<float, float, float>&,
+                                                           const FftPass<float, float, float>&,
+                                                           int, cudaStream_t, cx<float>*, size_t);
+template cudaError_t launch_fft_pass2<double, double, double>(
+    const FftPass<double, double, double>&, const FftPass<double, double, double>&, int,
+    cudaStream_t, cx<double>*, size_t);
+template cudaError_t launch_fft_pass2<df, float, float>(const FftPass<df, float, float>&,
+                                                       const FftPass<df, float, float>&, int,
+                                                       cudaStream_t, cx<float>*, size_t);
+template cudaError_t launch_fft_pass2<df, df, df>(const FftPass<df, df, df>&,
+                                                 const FftPass<df, df, df>&, int, cudaStream_t,
+                                                 cx<df>*, size_t);
+template cudaError_t launch_fft_pass2<double, float, float>(const FftPass<double, float, float>&,
+                                                            const FftPass<double, float, float>&,
+                                                            int, cudaStream_t, cx<float>*, size_t);
+template cudaError_t launch_fft_pass2<double, df, df>(const FftPass<double, df, df>&,
+                                                     const FftPass<double, df, df>&, int,
                                                      cudaStream_t, cx<df>*, size_t);
 template cudaError_t launch_fft_pass<df, float, float>(
     const df*, int, int, int, int, int, const cx<float>*, const cx<float>*, const cx<float>*,

@@ -627,11 +627,21 @@ struct MG : MGBase {
     if (L.path == FDE_PATH_FFT) {
       cx<T>* ws = reinterpret_cast<cx<T>*>(h->fft_ws);
       const size_t wse = h->fft_ws_elems * sizeof(cx<double>) / sizeof(cx<T>);
-      LCHK((launch_fft_pass<T, T, T>(xin_x, 1, L.n1, L.n2, L.n1, L.logLx, L.S1x, L.S2x, L.twx, L.dp,
-                                  L.dm, M, cm, kx, 0, st, ws, wse)));
-      LCHK(launch_transpose<T>(xin_y, L.n2, L.n1, L.xT, 0, st));
-      LCHK((launch_fft_pass<T, T, T>(L.xT, 1, L.n2, L.n1, L.n2, L.logLy, L.S1y, L.S2y, L.twy,
-                                     L.epT, L.emT, nullptr, 0.0, L.yT, 0, st, ws, wse)));
+      if (L.logLx == L.logLy) {
+        // both directions' passes in one launch (the y pass on the transposed grid)
+        LCHK(launch_transpose<T>(xin_y, L.n2, L.n1, L.xT, 0, st));
+        const FftPass<T, T, T> px{xin_x, 1, L.n1, L.n2, L.n1, L.S1x, L.S2x, L.twx, L.dp, L.dm,
+                                  M,     cm, kx,   0};
+        const FftPass<T, T, T> py{L.xT, 1,   L.n2,    L.n1, L.n2, L.S1y, L.S2y, L.twy, L.epT,
+                                  L.emT, nullptr, 0.0, L.yT, 0};
+        LCHK((launch_fft_pass2<T, T, T>(px, py, L.logLx, st, ws, wse)));
+      } else {
+        LCHK((launch_fft_pass<T, T, T>(xin_x, 1, L.n1, L.n2, L.n1, L.logLx, L.S1x, L.S2x, L.twx,
+                                       L.dp, L.dm, M, cm, kx, 0, st, ws, wse)));
+        LCHK(launch_transpose<T>(xin_y, L.n2, L.n1, L.xT, 0, st));
+        LCHK((launch_fft_pass<T, T, T>(L.xT, 1, L.n2, L.n1, L.n2, L.logLy, L.S1y, L.S2y, L.twy,
+                                       L.epT, L.emT, nullptr, 0.0, L.yT, 0, st, ws, wse)));
+      }
       LCHK(launch_transpose<T>(L.yT, L.n1, L.n2, kx, 1, st));
     } else if (L.path == FDE_PATH_DIRECT) {
       LCHK(launch_direct_pass<T>(xin_x, 1, L.n1, L.n2, L.n1, L.txT, L.dp, L.dm, M, cm, kx, 0, st));
