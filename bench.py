@@ -431,6 +431,19 @@ def roofline(w, prof, its, relaxed, ms_per_step, level_paths):
                              "products per block, ~3.5x this on the tensor pipe)",
                 "launches": int(gl), "avg_launch_us": round(avg_s * 1e6, 2),
                 "share_of_step": round(gms / steps / prof_total, 4) if prof_total else None}
+    if roof is None:
+        # no tensor-core level in this run (the tuner kept FFT products on every
+        # level): the class with the largest measured time stands in
+        name = max(classes, key=lambda c: classes[c]["measured_ms_per_step"])
+        cl = classes[name]
+        roof = {"bound": "tensor" if cl["work_unit"] == "flop" else "hbm",
+                "kernel": f"kernel class '{name}' (no tensor-core level in this run)",
+                "achieved": cl["achieved"], "peak": cl["peak"], "unit": cl["unit"],
+                "frac": None if cl["achieved"] is None else round(cl["achieved"] / cl["peak"], 4),
+                "traffic": None, "traffic_note": "null: a class of several kernels",
+                "work_per_launch": None, "launches": None, "avg_launch_us": None,
+                "share_of_step": (round(cl["measured_ms_per_step"] / prof_total, 4)
+                                  if prof_total else None)}
     step = {"t_min_ms": round(t_min, 4), "ms_per_step": round(ms_per_step, 4),
             "frac": round(t_min / ms_per_step, 4),
             "note": "T_min = product flops / BF16 burst peak + all other bytes / HBM copy peak "

@@ -78,7 +78,8 @@ extern "C" {
 #define FDE_PATH_TUNE          4  /* on the first coefficient set-up every level times its
                                      candidate paths on the device -- tensor cores (BF16/FP16/
                                      BF16X3, n >= 127), FFT, direct summation (n <= 1023) -- and
-                                     keeps the fastest */
+                                     keeps the fastest (a later path in that order only when
+                                     faster by more than 3 %) */
 
 /* arithmetic of the FP64-accurate outer apply (Krylov matvec, true residual, rhs) */
 #define FDE_OUTER_FP64         0  /* FFT in FP64; FGMRES vectors and Gram-Schmidt in FP64 */

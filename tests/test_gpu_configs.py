@@ -67,6 +67,9 @@ def test_bench_configuration_n2047():
     its = {}
     for name, kw in [("mixed", dict(precision=fde.FDE_PREC_BF16X3, toeplitz_path=fde.FDE_PATH_TUNE,
                                     outer=fde.FDE_OUTER_DF32, relax=1)),
+                     ("mixed_gemm", dict(precision=fde.FDE_PREC_BF16X3,
+                                         toeplitz_path=fde.FDE_PATH_GEMM,
+                                         outer=fde.FDE_OUTER_DF32, relax=1)),
                      ("fp64", dict(precision=fde.FDE_PREC_FP64))]:
         case = Case(prob, n, rtol=1e-8, maxit=2000, **kw)
         h = case.handle()
@@ -81,9 +84,13 @@ def test_bench_configuration_n2047():
             assert st.converged == 1 and res <= 1.05e-8, (name, res)
             its[name] = st.iterations
             if name == "mixed":
-                # the tuner keeps the tensor cores for the bench grid's level 0
-                assert fde.fde_level_path(h, 0) == fde.FDE_PATH_GEMM
+                # the tuner's choice for level 0: tensor cores or FFT products
+                assert fde.fde_level_path(h, 0) in (fde.FDE_PATH_GEMM, fde.FDE_PATH_FFT)
                 assert st.relaxed > 0
+            if name == "mixed_gemm":
+                # the same solve with level 0 on the tensor cores
+                assert fde.fde_level_path(h, 0) == fde.FDE_PATH_GEMM
         finally:
             fde.fde_destroy(h)
     assert abs(its["mixed"] - its["fp64"]) <= 1, its
+    assert abs(its["mixed_gemm"] - its["fp64"]) <= 1, its
