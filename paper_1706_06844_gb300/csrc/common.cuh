@@ -144,6 +144,10 @@ cudaError_t launch_mul(size_t N, const T* W, const T* B, T* Y, cudaStream_t st);
 // coarse b_c = rscale * P^T r (bilinear P of the transfer above, any fine sizes)
 template <typename T>
 cudaError_t launch_restrict(const T* R, int n1, int n2, double rscale, T* BC, cudaStream_t st);
+// out = transpose(in) added to KX, then X <- X + W (B - out) (out not stored)
+template <typename T>
+cudaError_t launch_transpose_smooth(const T* in, int rows, int cols, const T* KX, const T* B,
+                                    const T* W, T* X, cudaStream_t st);
 // restriction of the residual B - KX without storing it
 template <typename T>
 cudaError_t launch_restrict_residual(const T* B, const T* KX, int n1, int n2, double rscale,

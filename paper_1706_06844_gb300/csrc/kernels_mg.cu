@@ -103,6 +103,38 @@ __global__ void transpose_kernel(const T* __restrict__ in, int rows, int cols, T
   }
 }
 
+// the last step of a level's smoothing sweep on the FFT path: the transposed
+// y products are added to the x products KX and the damped-Jacobi update
+// X <- X + W (B - KX) is applied in the same pass (KX itself is not stored)
+template <typename T>
+__global__ void transpose_smooth_kernel(const T* __restrict__ in, int rows, int cols,
+                                        const T* __restrict__ KX, const T* __restrict__ B,
+                                        const T* __restrict__ W, T* X) {
+  __shared__ T tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;  // out row c, column r
+    if (r < rows && c < cols) {
+      const size_t o = (size_t)c * rows + r;
+      const T kx = KX[o] + tile[threadIdx.x][k];
+      X[o] = X[o] + W[o] * (B[o] - kx);
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_transpose_smooth(const T* in, int rows, int cols, const T* KX, const T* B,
+                                    const T* W, T* X, cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+  transpose_smooth_kernel<T><<<grid, block, 0, st>>>(in, rows, cols, KX, B, W, X);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_transpose(const T* in, int rows, int cols, T* out, int add, cudaStream_t st) {
   dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
@@ -672,6 +704,8 @@ template cudaError_t launch_g_level_op<float>(int, const GLevelOp<float>*, const
                                                 const T*, T*, cudaStream_t);                      \
   template cudaError_t launch_mul<T>(size_t, const T*, const T*, T*, cudaStream_t);               \
   template cudaError_t launch_restrict<T>(const T*, int, int, double, T*, cudaStream_t);          \
+  template cudaError_t launch_transpose_smooth<T>(const T*, int, int, const T*, const T*,         \
+                                                  const T*, T*, cudaStream_t);                    \
   template cudaError_t launch_restrict_residual<T>(const T*, const T*, int, int, double, T*,      \
                                                    cudaStream_t);                                 \
   template cudaError_t launch_jacobi_mass_prepass<T>(const T*, const T*, int, int, double, double,\

@@ -608,8 +608,12 @@ struct MG : MGBase {
   }
 
   // kx = K_l x (products + mass term); jacobi_from_zero (structured-Galerkin
-  // levels l > 0 only): x is first set to W b in the same pass as the mass terms
-  int products(fde_handle* h, size_t l, const T* x, T* kx, bool jacobi_from_zero = false) {
+  // levels l > 0 only): x is first set to W b in the same pass as the mass terms;
+  // smoothed (non-null, x = L.x): on the FFT path the damped-Jacobi update
+  // x <- x + W (b - K x) is applied in the products' last pass instead of
+  // storing kx, and *smoothed is set
+  int products(fde_handle* h, size_t l, const T* x, T* kx, bool jacobi_from_zero = false,
+               bool* smoothed = nullptr) {
     Lv& L = lv[l];
     cudaStream_t st = h->st;
     const T *xin_x = x, *xin_y = x, *M = x;
@@ -645,7 +649,12 @@ struct MG : MGBase {
         LCHK((launch_fft_pass<T, T, T>(L.xT, 1, L.n2, L.n1, L.n2, L.logLy, L.S1y, L.S2y, L.twy,
                                        L.epT, L.emT, nullptr, 0.0, L.yT, 0, st, ws, wse)));
       }
-      LCHK(launch_transpose<T>(L.yT, L.n1, L.n2, kx, 1, st));
+      if (smoothed) {
+        LCHK(launch_transpose_smooth<T>(L.yT, L.n1, L.n2, kx, L.b, L.W, L.x, st));
+        *smoothed = true;
+      } else {
+        LCHK(launch_transpose<T>(L.yT, L.n1, L.n2, kx, 1, st));
+      }
     } else if (L.path == FDE_PATH_DIRECT) {
       LCHK(launch_direct_pass<T>(xin_x, 1, L.n1, L.n2, L.n1, L.txT, L.dp, L.dm, M, cm, kx, 0, st));
       LCHK(launch_direct_pass<T>(xin_y, L.n1, 1, L.n1, L.n2, L.tyT, L.ep, L.em, nullptr, 0.0, kx,
@@ -677,7 +686,9 @@ struct MG : MGBase {
 
   int smooth(fde_handle* h, size_t l) {  // x <- x + W (b - K x)
     Lv& L = lv[l];
-    RCHK(products(h, l, L.x, L.kx));
+    bool done = false;
+    RCHK(products(h, l, L.x, L.kx, false, &done));
+    if (done) return FDE_OK;
     const int pi = h->pbeg(FDE_KCLASS_MG_OTHER);
     LCHK(launch_level_epilogue<T>(2, L.N, L.kx, L.b, L.x, L.W, L.x, h->st));
     h->pend(pi);
