@@ -144,6 +144,12 @@ cudaError_t launch_mul(size_t N, const T* W, const T* B, T* Y, cudaStream_t st);
 // coarse b_c = rscale * P^T r (bilinear P of the transfer above, any fine sizes)
 template <typename T>
 cudaError_t launch_restrict(const T* R, int n1, int n2, double rscale, T* BC, cudaStream_t st);
+// mass-term pre-pass with (I (x) B_x) x written transposed (XBXT, n1 x n2);
+// W, B non-null: X = W B first (as launch_jacobi_mass_prepass), else X is read
+template <typename T>
+cudaError_t launch_mass_prepass_t(const T* W, const T* B, int n1, int n2, double bx0, double bx1,
+                                  double by0, double by1, double c, T* X, T* XBY, T* XBXT,
+                                  T* MASS, cudaStream_t st);
 // out = transpose(in) added to KX, then X <- X + W (B - out) (out not stored)
 template <typename T>
 cudaError_t launch_transpose_smooth(const T* in, int rows, int cols, const T* KX, const T* B,

@@ -43,6 +43,62 @@ __global__ void mass_prepass_kernel(T* X, int n1, int n2, T bx0, T bx1, T by0, T
   }
 }
 
+// The same pre-pass over 32 x 32 tiles (x and its one-point halo staged in
+// shared memory) that writes (I (x) B_x) x TRANSPOSED (n1 x n2, XBXT) for
+// the FFT path's column pass, saving that pass's separate transpose.
+template <typename T>
+__global__ void mass_prepass_t_kernel(T* X, int n1, int n2, T bx0, T bx1, T by0, T by1, T c,
+                                      T* __restrict__ XBY, T* __restrict__ XBXT,
+                                      T* __restrict__ MASS, const T* __restrict__ W,
+                                      const T* __restrict__ B) {
+  __shared__ T xs[34][35];
+  __shared__ T tb[32][33];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int k = tid; k < 34 * 34; k += 32 * blockDim.y) {
+    const int jj = j0 - 1 + k / 34, ii = i0 - 1 + k % 34;
+    T v = T(0);
+    if (ii >= 0 && ii < n1 && jj >= 0 && jj < n2) {
+      const size_t q = (size_t)jj * n1 + ii;
+      v = W ? W[q] * B[q] : X[q];
+    }
+    xs[k / 34][k % 34] = v;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, i = i0 + tx;
+    if (i < n1 && j < n2) {
+      const size_t idx = (size_t)j * n1 + i;
+      const T xc = xs[r + 1][tx + 1];
+      const T up = xs[r][tx + 1], dn = xs[r + 2][tx + 1], lf = xs[r + 1][tx],
+              rt = xs[r + 1][tx + 2];
+      if (W) X[idx] = xc;
+      XBY[idx] = by1 * up + by0 * xc + by1 * dn;
+      tb[r][tx] = bx1 * lf + bx0 * xc + bx1 * rt;
+      const T rowm = bx1 * xs[r][tx] + bx0 * up + bx1 * xs[r][tx + 2];
+      const T row0 = bx1 * lf + bx0 * xc + bx1 * rt;
+      const T rowp = bx1 * xs[r + 2][tx] + bx0 * dn + bx1 * xs[r + 2][tx + 2];
+      MASS[idx] = c * (by1 * rowm + by0 * row0 + by1 * rowp);
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, j = j0 + tx;
+    if (i < n1 && j < n2) XBXT[(size_t)i * n2 + j] = tb[tx][r];
+  }
+}
+
+template <typename T>
+cudaError_t launch_mass_prepass_t(const T* W, const T* B, int n1, int n2, double bx0, double bx1,
+                                  double by0, double by1, double c, T* X, T* XBY, T* XBXT,
+                                  T* MASS, cudaStream_t st) {
+  dim3 grid((n1 + 31) / 32, (n2 + 31) / 32), block(32, 8);
+  mass_prepass_t_kernel<T><<<grid, block, 0, st>>>(X, n1, n2, T(bx0), T(bx1), T(by0), T(by1),
+                                                   T(c), XBY, XBXT, MASS, W, B);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_mass_prepass(const T* X, int n1, int n2, double bx0, double bx1, double by0,
                                 double by1, double c, T* XBY, T* XBX, T* MASS, cudaStream_t st) {
@@ -704,6 +760,9 @@ template cudaError_t launch_g_level_op<float>(int, const GLevelOp<float>*, const
                                                 const T*, T*, cudaStream_t);                      \
   template cudaError_t launch_mul<T>(size_t, const T*, const T*, T*, cudaStream_t);               \
   template cudaError_t launch_restrict<T>(const T*, int, int, double, T*, cudaStream_t);          \
+  template cudaError_t launch_mass_prepass_t<T>(const T*, const T*, int, int, double, double,     \
+                                                double, double, double, T*, T*, T*, T*,           \
+                                                cudaStream_t);                                    \
   template cudaError_t launch_transpose_smooth<T>(const T*, int, int, const T*, const T*,         \
                                                   const T*, T*, cudaStream_t);                    \
   template cudaError_t launch_restrict_residual<T>(const T*, const T*, int, int, double, T*,      \

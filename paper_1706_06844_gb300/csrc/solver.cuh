@@ -618,7 +618,19 @@ struct MG : MGBase {
     cudaStream_t st = h->st;
     const T *xin_x = x, *xin_y = x, *M = x;
     double cm = h->c;
-    if (sg && l > 0) {
+    // structured-Galerkin level on the two-pass FFT path: the pre-pass writes
+    // the column pass's operand already transposed
+    const bool xT_ready = sg && l > 0 && L.path == FDE_PATH_FFT && L.logLx == L.logLy;
+    if (xT_ready) {
+      LCHK(launch_mass_prepass_t<T>(jacobi_from_zero ? L.W : nullptr,
+                                    jacobi_from_zero ? L.b : nullptr, L.n1, L.n2, L.bx0, L.bx1,
+                                    L.by0, L.by1, h->c, const_cast<T*>(x), L.xby, L.xT, L.mass,
+                                    st));
+      xin_x = L.xby;
+      xin_y = nullptr;
+      M = L.mass;
+      cm = 1.0;
+    } else if (sg && l > 0) {
       if (jacobi_from_zero)
         LCHK(launch_jacobi_mass_prepass<T>(L.W, L.b, L.n1, L.n2, L.bx0, L.bx1, L.by0, L.by1, h->c,
                                            const_cast<T*>(x), L.xby, L.xbx, L.mass, st));
@@ -636,7 +648,7 @@ struct MG : MGBase {
       const size_t wse = h->fft_ws_elems * sizeof(cx<double>) / sizeof(cx<T>);
       if (L.logLx == L.logLy) {
         // both directions' passes in one launch (the y pass on the transposed grid)
-        LCHK(launch_transpose<T>(xin_y, L.n2, L.n1, L.xT, 0, st));
+        if (!xT_ready) LCHK(launch_transpose<T>(xin_y, L.n2, L.n1, L.xT, 0, st));
         const FftPass<T, T, T> px{xin_x, 1, L.n1, L.n2, L.n1, L.S1x, L.S2x, L.twx, L.dp, L.dm,
                                   M,     cm, kx,   0};
         const FftPass<T, T, T> py{L.xT, 1,   L.n2,    L.n1, L.n2, L.S1y, L.S2y, L.twy, L.epT,
